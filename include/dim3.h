@@ -1,0 +1,216 @@
+/*
+ * dim3.h -- C ABI of the GB300 (sm_103a) DIM^3 Join-Project library.
+ *
+ * The library computes the Join-Project of Eq. 1 (Section 1),
+ *     Pi_{x,z}( R(x,y) join_y S(z,y) ),
+ * and the Join-Aggregate COUNT of Section 4.1, on one GPU, with every step
+ * of Algorithm 1 (mapping, CSR construction, intersection-free partitioning,
+ * SparseBMM, DenseEC, union of the disjoint results) in CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Tables are int32 column pairs in DEVICE memory: R is (r_key = y,
+ *   r_val = x), S is (s_key = y, s_val = z), each of n rows. Rows may repeat
+ *   and come in any order: tables are sets (duplicates collapse).
+ * - Output pairs are the original int32 values, distinct, in canonical order:
+ *   x ascending, then z ascending, comparing signed 32-bit integers.
+ * - The caller owns every input and output buffer. The library owns its
+ *   context, its plans and the scratch memory they allocate (stream-ordered
+ *   cudaMallocAsync on the call's stream).
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream). Work is enqueued on it. Calls that return sizes in host memory
+ *   (counts, distinct counts, plan info) synchronise that stream before they
+ *   return.
+ * - Every call returns a dim3_status. No C++ exception crosses the ABI.
+ *   On failure dim3_last_error() returns a message for the calling thread.
+ * - Sizes are int64. Null pointers with a nonzero size, or negative sizes,
+ *   give DIM3_ERR_ARG. n = 0 is legal and yields an empty result.
+ * - A context is bound to one device and may be used by one host thread at
+ *   a time.
+ */
+#ifndef DIM3_H
+#define DIM3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DIM3_OK = 0,
+    DIM3_ERR_ARG = -1,         /* bad argument (null pointer, negative size, bad range) */
+    DIM3_ERR_CUDA = -2,        /* a CUDA runtime/driver call failed */
+    DIM3_ERR_NOMEM = -3,       /* device allocation failed */
+    DIM3_ERR_CAPACITY = -4,    /* output capacity smaller than the result; count is set */
+    DIM3_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    DIM3_ERR_OVERFLOW = -6,    /* a size exceeds what the library supports */
+    DIM3_ERR_UNSUPPORTED = -7  /* option or device not supported */
+} dim3_status;
+
+typedef struct dim3_ctx dim3_ctx;
+typedef struct dim3_plan dim3_plan;
+
+/* Sizes of a partitioned input, returned by dim3_partition (host struct). */
+typedef struct {
+    int64_t n_r;          /* input R rows */
+    int64_t n_s;          /* input S rows */
+    int64_t n_r_kept;     /* distinct R tuples whose y occurs in S.y (Section 2.2, Opt. 2) */
+    int64_t n_s_distinct; /* distinct S tuples */
+    int64_t n_x;          /* |X|: distinct x of the kept R tuples */
+    int64_t n_y;          /* |Y|: distinct S.y */
+    int64_t n_z;          /* |Z|: distinct S.z */
+    int64_t n_z_dense;    /* |Z_d|: z columns judged dense (Section 2.3) */
+    int64_t n_y_dense;    /* distinct y of the dense S tuples (K of the DenseEC contraction) */
+    int64_t n_s_sparse;   /* S tuples in S_sparse */
+    int64_t n_y_bitmap;   /* S_sparse rows held as z-bitmaps (SparseBMM's wide rows) */
+    int64_t out_j;        /* |OUT_J| = sum over y of deg_R(y) * deg_S(y) */
+    int32_t theta_z;      /* degree threshold used: z dense iff m_z >= theta_z */
+    int32_t dense_variant;/* DenseEC variant that will run (dim3_dense_variant) */
+} dim3_plan_info;
+
+/* DenseEC bitmap-intersection variants (Algorithm 3; the choice is the role
+ * of f3 in Section 2.6). All give identical results. */
+typedef enum {
+    DIM3_DENSE_AUTO = 0,   /* tuned choice */
+    DIM3_DENSE_TC = 1,     /* 0/1 tile product on tcgen05 tensor cores, then > 0 */
+    DIM3_DENSE_POPC = 2,   /* bit-packed AND + popc on CUDA cores */
+    DIM3_DENSE_PROBE = 3   /* per x, probe each y of R[x] in S_dense (non-SIMD method) */
+} dim3_dense_variant;
+
+/* Context options (dim3_ctx_set_option). */
+typedef enum {
+    DIM3_OPT_THETA_Z = 1,       /* z dense iff m_z >= value; <0: tuned (default) */
+    DIM3_OPT_DENSE_VARIANT = 2, /* a dim3_dense_variant (default AUTO) */
+    DIM3_OPT_BITMAP_ROW_MIN = 3,/* S_sparse rows with at least this many z are held as bitmaps; <0: |Z|/32 */
+    DIM3_OPT_LIGHT_ROW_MAX = 4  /* x rows with at most this many join tuples dedup in shared memory by sort; <0: default */
+} dim3_option;
+
+/* Library version as major*10000 + minor*100 + patch. */
+int dim3_version(void);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *dim3_last_error(void);
+
+/* Create a context on CUDA device `device`. *out receives the handle. */
+int dim3_ctx_create(dim3_ctx **out, int device);
+
+/* Destroy a context. Plans made with it must be destroyed first. */
+int dim3_ctx_destroy(dim3_ctx *ctx);
+
+/* Set a dim3_option. Returns DIM3_ERR_ARG for an unknown option. */
+int dim3_ctx_set_option(dim3_ctx *ctx, int option, int64_t value);
+
+/*
+ * dim3_map -- order-preserving mapping of one column to dense ids.
+ * Section 2.2 maps every distinct value of a column to a natural number; this
+ * library gives each value its rank among the column's distinct values, so id
+ * order is value order (the reason canonical output order needs no sort).
+ *   d_vals     [n] int32 device, the column.
+ *   d_ids      [n] int32 device, out: d_ids[i] = #distinct values < d_vals[i].
+ *   d_dict     [n] int32 device, out: the first *n_distinct entries are the
+ *              distinct values ascending (d_dict[d_ids[i]] == d_vals[i]).
+ *   n_distinct host, out.
+ * Synchronises the stream.
+ */
+int dim3_map(dim3_ctx *ctx, const int32_t *d_vals, int64_t n, int32_t *d_ids,
+             int32_t *d_dict, int64_t *n_distinct, void *stream);
+
+/*
+ * dim3_partition -- Algorithm 1 up to the compute steps: map y from S.y and
+ * drop R tuples whose y is not in S.y (Section 2.2, Opt. 2); map x and z;
+ * build R_CSR by x (Section 2.5); split S by z into S_sparse (CSR by y) and
+ * S_dense (bitmaps / 0-1 tiles) so that the two results are disjoint
+ * (Section 2.3). z is dense iff m_z >= theta_z (theta_z < 0: the context's
+ * option, else tuned).
+ *   *plan_out  receives a plan that owns the device-resident tables.
+ *   info       host, out (may be NULL).
+ * Inputs may be freed or reused once the call returns. Synchronises the stream.
+ */
+int dim3_partition(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
+                   const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns,
+                   int32_t theta_z, dim3_plan **plan_out, dim3_plan_info *info, void *stream);
+
+/* Copy of the plan's sizes. */
+int dim3_plan_get_info(const dim3_plan *plan, dim3_plan_info *info);
+
+/*
+ * dim3_plan_row_counts -- per-x output sizes for the x-id range
+ * [x_begin, x_end): d_counts[i] = |{z : (x_begin + i, z) in result}|
+ * (int64 device, x_end - x_begin entries). Useful to size x-range chunks.
+ */
+int dim3_plan_row_counts(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
+                         int64_t *d_counts, void *stream);
+
+/*
+ * dim3_plan_join_project -- SparseBMM (Algorithm 2) and DenseEC (Algorithm 3)
+ * over the x-id range [x_begin, x_end) of a plan, and their union
+ * (Algorithm 1, last step: disjoint, so no dedup), compacted into
+ *   d_out_x, d_out_z  [capacity] int32 device, out: pairs of the range in
+ *                     canonical order (x ids are rank-ordered, so ranges
+ *                     concatenate into the full canonical result).
+ *   count             host, out: pairs of the range; always set.
+ * If capacity < count nothing is written and DIM3_ERR_CAPACITY is returned.
+ * x_begin = 0, x_end = n_x covers everything. Synchronises the stream.
+ */
+int dim3_plan_join_project(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
+                           int32_t *d_out_x, int32_t *d_out_z, int64_t capacity,
+                           int64_t *count, void *stream);
+
+/*
+ * dim3_plan_join_count -- as dim3_plan_join_project, plus
+ *   d_out_cnt [capacity] int32 device, out: COUNT(x,z) = number of distinct y
+ *             joining x and z (Join-Aggregate, Section 4.1, with COUNT).
+ */
+int dim3_plan_join_count(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
+                         int32_t *d_out_x, int32_t *d_out_z, int32_t *d_out_cnt,
+                         int64_t capacity, int64_t *count, void *stream);
+
+/* Tables a plan can export (dim3_plan_export), for inspection and tests. */
+typedef enum {
+    DIM3_TABLE_DICT_X = 1,    /* int32 [n_x]   distinct x ascending */
+    DIM3_TABLE_DICT_Y = 2,    /* int32 [n_y]   distinct S.y ascending */
+    DIM3_TABLE_DICT_Z = 3,    /* int32 [n_z]   distinct S.z ascending */
+    DIM3_TABLE_R_ROWPTR = 4,  /* int64 [n_x+1] R_CSR row pointers */
+    DIM3_TABLE_R_COL = 5,     /* int32 [n_r_kept] R_CSR y ids, ascending per row */
+    DIM3_TABLE_M_Z = 6,       /* int32 [n_z]   m_z */
+    DIM3_TABLE_DENSE_Z = 7,   /* uint8 [n_z]   1 if z is dense */
+    DIM3_TABLE_SS_ROWPTR = 8, /* int64 [n_y+1] S_sparse row pointers by y id */
+    DIM3_TABLE_SS_COL = 9,    /* int32 [n_s_sparse] S_sparse z ids, ascending per row */
+    DIM3_TABLE_DEG_S = 10,    /* int32 [n_y]   deg_S(y) */
+    DIM3_TABLE_OUTJ_X = 11    /* int64 [n_x]   join tuples per x: sum over y in R[x] of deg_S(y) */
+} dim3_table;
+
+/* Copy table `which` into d_dst (device), which holds `bytes` bytes. */
+int dim3_plan_export(dim3_plan *plan, int which, void *d_dst, int64_t bytes, void *stream);
+
+/* Free a plan's device tables (stream-ordered on the plan's stream). */
+int dim3_plan_destroy(dim3_plan *plan);
+
+/*
+ * dim3_join_project -- the whole hot path of Eq. 1 in one call: partition,
+ * SparseBMM + DenseEC, union, compaction.
+ *   d_out_x, d_out_z [capacity] int32 device, out.
+ *   count            host, out: |OUT_P|; always set, also on DIM3_ERR_CAPACITY
+ *                    (then nothing is written).
+ * Synchronises the stream.
+ */
+int dim3_join_project(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
+                      const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns,
+                      int32_t *d_out_x, int32_t *d_out_z, int64_t capacity, int64_t *count,
+                      void *stream);
+
+/*
+ * dim3_join_count -- Join-Aggregate COUNT (Section 4.1): as dim3_join_project
+ * plus d_out_cnt [capacity] int32 device, COUNT(x,z) for every output pair.
+ */
+int dim3_join_count(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
+                    const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns,
+                    int32_t *d_out_x, int32_t *d_out_z, int32_t *d_out_cnt, int64_t capacity,
+                    int64_t *count, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIM3_H */
