@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 DIM^3 Join-Project hot path.
+
+One step = one call of the C ABI's dim3_join_project on the two-table
+workload (|R| = |S| = 10^6 distinct int32 tuples, 100,000 x, 80,000 z, Zipf(1.0)
+y over 50,000 ids): mapping, partition, SparseBMM + DenseEC, union and
+compaction of ~5e9 deduplicated (x, z) pairs into HBM. Inputs are resident in
+HBM when the timed region starts.
+
+Prints one JSON line (rank 0). With --impl reference it times the CPU oracle
+instead (bounded samples of the same workload on the host cores).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "dedup (x,z) pairs/s on 1 GB300 vs plain path; served p50/p99 latency"
+UNIT = "pairs/s"
+WORKLOADS = ("two_table_1m_zipf1", "self_20k", "chung_lu_1m_4m")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=WORKLOADS, default="two_table_1m_zipf1")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name: str, rank: int = 0):
+    import gen
+
+    if name == "two_table_1m_zipf1":
+        return gen.config2_two_table(seed=1 + 1000 * rank)
+    if name == "self_20k":
+        return gen.config1_self(seed=0 + 1000 * rank)
+    return gen.config3_chung_lu(seed=2 + 1000 * rank)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current source of that kernel."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d[kernel]
+        import hashlib
+
+        src = os.path.join(ROOT, "paper_2206_04995_gb300", "csrc", e["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != e["source_sha"]:
+            return None, e
+        return float(e["dram_bytes_per_launch_full"]), e
+    except Exception:  # noqa: BLE001
+        return None, None
+
+
+def cpu_baseline(inst, target_s: float, rng_seed: int = 5):
+    """The oracle as it stands, single-threaded, on the rows of a random x
+    sample sized to take about target_s seconds."""
+    import oracle
+
+    oracle.build()
+    xs = np.unique(inst.r_val)
+    rng = np.random.default_rng(rng_seed)
+    k = 4
+    while True:
+        pick = rng.choice(xs, size=min(k, xs.size), replace=False)
+        t0 = time.perf_counter()
+        x, _, _ = oracle.join_project(inst.r_key, inst.r_val, inst.s_key, inst.s_val, x_filter=pick)
+        dt = time.perf_counter() - t0
+        if dt >= target_s * 0.5 or pick.size == xs.size:
+            break
+        k = int(min(xs.size, max(k * 2, k * target_s / max(dt, 1e-3) * 0.9)))
+    return {"value": x.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"rows of {pick.size} random x of {xs.size} (R restricted to them, S whole); "
+                      f"{x.size} pairs in {dt:.2f} s"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    inst = make_workload(args.workload)
+    import oracle
+
+    oracle.build()
+    xs = np.unique(inst.r_val)
+    rng = np.random.default_rng(17)
+    per_step = max(1, min(xs.size, 200))
+    pairs = 0
+    t_total = 0.0
+    for s in range(args.warmup + args.steps):
+        pick = rng.choice(xs, size=per_step, replace=False)
+        t0 = time.perf_counter()
+        x, _, _ = oracle.join_project(inst.r_key, inst.r_val, inst.s_key, inst.s_val, x_filter=pick)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            pairs += x.size
+            t_total += dt
+    value = pairs / t_total
+    sample = f"each step: rows of {per_step} random x of {xs.size} (R restricted, S whole), single-threaded"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": inst.name},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    assert args.warmup >= 3 or os.environ.get("DIM3_BENCH_ALLOW_SHORT"), "at least 3 warm-up steps"
+
+    import torch
+
+    import paper_2206_04995_gb300 as dim3
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    inst = make_workload(args.workload, rank)
+    dev = torch.device("cuda", local_rank)
+    cols = [torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(dev)
+            for a in (inst.r_key, inst.r_val, inst.s_key, inst.s_val)]
+    ctx = dim3.Context(local_rank)
+
+    # size the output once (plan path), then time the one-call path
+    plan = ctx.partition(*cols)
+    info = plan.info
+    out_p = int(plan.row_counts().sum().item())
+    plan.close()
+    out_x = torch.empty(out_p, dtype=torch.int32, device=dev)
+    out_z = torch.empty(out_p, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > 129 MB L2
+
+    def step():
+        x, _ = ctx.join_project(*cols, out_x=out_x, out_z=out_z)
+        return x.numel()
+
+    for _ in range(args.warmup):
+        assert step() == out_p
+    torch.cuda.synchronize()
+
+    ctx.set_option(dim3.OPT_TIMING, 1)
+    ctx.timing(reset=True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = dim3.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    evs = []
+    for k in range(args.steps):
+        flush.fill_(k)  # evict the previous step's lines from L2 (outside the step's events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        n = step()
+        e1.record()
+        evs.append((e0, e1))
+        assert n == out_p
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = dim3.launch_count() - l0
+    clocks = sampler.stop()
+    tm = ctx.timing()
+    ctx.set_option(dim3.OPT_TIMING, 0)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    busy_s = sum(step_ms) / 1e3
+
+    total_pairs = out_p * args.steps
+    if dist:
+        t = torch.tensor([busy_s, float(total_pairs)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        busy_max, pairs_all = float(mx[0]), float(t[1])
+    else:
+        busy_max, pairs_all = busy_s, float(total_pairs)
+    value = pairs_all / busy_max
+
+    # roofline of the dominant kernel: SparseBMM + union + compaction (emitting pass)
+    hbm_peak, peak_src = measured_peaks()
+    emit_ms, emit_n = tm["sparse_emit"]
+    emit_s = emit_ms / 1e3 / max(emit_n, 1)
+    alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
+    achieved = alg_bytes / emit_s / 1e9
+    traffic, _ = traffic_for("k_xrow_bits_emit")
+    phases = {k: round(v[0] / max(v[1], 1), 4) for k, v in tm.items() if v[1]}
+
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        e2e = run_e2e(torch, ctx, inst, dev, out_p, args.e2e_steps)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(inst, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * busy_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": inst.name, "n_r": inst.nr, "n_s": inst.ns, "n_x": info["n_x"],
+                       "n_y": info["n_y"], "n_z": info["n_z"], "n_z_dense": info["n_z_dense"],
+                       "out_p": out_p, "out_j": info["out_j"], "theta_z": info["theta_z"],
+                       "l2": "flushed between steps (256 MiB write outside the step events)",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "join_tuples_per_s": info["out_j"] * args.steps * (pairs_all / total_pairs) / busy_max},
+            "roofline": {"bound": "hbm", "kernel": "k_xrow_bits<emit> (SparseBMM+union+compaction)",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "peak_source": peak_src, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                         "launch_ms": emit_s * 1e3},
+            "phase_ms": phases,
+            "wall_s": t_wall,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    ctx.close()
+
+
+def run_e2e(torch, ctx, inst, dev, out_p, steps):
+    """Same metric through the public call with HOST buffers: pinned host
+    inputs copied in, dim3_join_project, both output columns copied out."""
+    pin = True
+    try:
+        h_in = [torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
+                for a in (inst.r_key, inst.r_val, inst.s_key, inst.s_val)]
+        h_x = torch.empty(out_p, dtype=torch.int32, pin_memory=True)
+        h_z = torch.empty(out_p, dtype=torch.int32, pin_memory=True)
+    except Exception:  # noqa: BLE001
+        pin = False
+        h_in = [torch.from_numpy(np.ascontiguousarray(a, np.int32)) for a in
+                (inst.r_key, inst.r_val, inst.s_key, inst.s_val)]
+        h_x = torch.empty(out_p, dtype=torch.int32)
+        h_z = torch.empty(out_p, dtype=torch.int32)
+    d_in = [torch.empty_like(h, device=dev) for h in h_in]
+    d_x = torch.empty(out_p, dtype=torch.int32, device=dev)
+    d_z = torch.empty(out_p, dtype=torch.int32, device=dev)
+    h2d = sum(h.numel() * 4 for h in h_in)
+    d2h = 2 * out_p * 4
+
+    def one():
+        for d, h in zip(d_in, h_in):
+            d.copy_(h, non_blocking=pin)
+        x, z = ctx.join_project(*d_in, out_x=d_x, out_z=d_z)
+        h_x.copy_(x, non_blocking=pin)
+        h_z.copy_(z, non_blocking=pin)
+
+    one()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        one()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    del d_in, d_x, d_z
+    return {"value": out_p * steps / sum(times), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "host_memory": "pinned" if pin else "pageable",
+            "ms_per_step": 1e3 * sum(times) / steps}
+
+
+if __name__ == "__main__":
+    main()

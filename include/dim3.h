@@ -33,6 +33,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define DIM3_API __attribute__((visibility("default")))
+#else
+#define DIM3_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -83,23 +89,42 @@ typedef enum {
     DIM3_OPT_THETA_Z = 1,       /* z dense iff m_z >= value; <0: tuned (default) */
     DIM3_OPT_DENSE_VARIANT = 2, /* a dim3_dense_variant (default AUTO) */
     DIM3_OPT_BITMAP_ROW_MIN = 3,/* S_sparse rows with at least this many z are held as bitmaps; <0: |Z|/32 */
-    DIM3_OPT_LIGHT_ROW_MAX = 4  /* x rows with at most this many join tuples dedup in shared memory by sort; <0: default */
+    DIM3_OPT_LIGHT_ROW_MAX = 4, /* x rows with at most this many join tuples dedup in shared memory by sort; <0: default */
+    DIM3_OPT_TIMING = 5         /* nonzero: record CUDA events around each phase (dim3_ctx_timing) */
 } dim3_option;
 
+/* Phases timed under DIM3_OPT_TIMING. */
+typedef enum {
+    DIM3_PHASE_MAP = 0,          /* dim3_map */
+    DIM3_PHASE_PARTITION = 1,    /* mapping + CSR + split of dim3_partition / dim3_join_* */
+    DIM3_PHASE_DENSE_EC = 2,     /* DenseEC kernels */
+    DIM3_PHASE_SPARSE_COUNT = 3, /* SparseBMM + union, counting pass */
+    DIM3_PHASE_SPARSE_EMIT = 4   /* SparseBMM + union + compaction, emitting pass */
+} dim3_phase;
+
 /* Library version as major*10000 + minor*100 + patch. */
-int dim3_version(void);
+DIM3_API int dim3_version(void);
 
 /* Message of the last failed call on this host thread ("" if none). */
-const char *dim3_last_error(void);
+DIM3_API const char *dim3_last_error(void);
 
 /* Create a context on CUDA device `device`. *out receives the handle. */
-int dim3_ctx_create(dim3_ctx **out, int device);
+DIM3_API int dim3_ctx_create(dim3_ctx **out, int device);
 
 /* Destroy a context. Plans made with it must be destroyed first. */
-int dim3_ctx_destroy(dim3_ctx *ctx);
+DIM3_API int dim3_ctx_destroy(dim3_ctx *ctx);
 
 /* Set a dim3_option. Returns DIM3_ERR_ARG for an unknown option. */
-int dim3_ctx_set_option(dim3_ctx *ctx, int option, int64_t value);
+DIM3_API int dim3_ctx_set_option(dim3_ctx *ctx, int option, int64_t value);
+
+/* Accumulated device time (CUDA events on the launching stream) and number of
+ * timed intervals of a dim3_phase since the last reset, while DIM3_OPT_TIMING
+ * is on. Waits for the recorded events. reset != 0 clears all phases after
+ * reading. Not a paper operation: instrumentation for roofline measurement. */
+DIM3_API int dim3_ctx_timing(dim3_ctx *ctx, int phase, double *total_ms, int64_t *launches, int reset);
+
+/* Number of CUDA kernels this library has launched in this process. */
+DIM3_API int dim3_launch_count(int64_t *out);
 
 /*
  * dim3_map -- order-preserving mapping of one column to dense ids.
@@ -113,7 +138,7 @@ int dim3_ctx_set_option(dim3_ctx *ctx, int option, int64_t value);
  *   n_distinct host, out.
  * Synchronises the stream.
  */
-int dim3_map(dim3_ctx *ctx, const int32_t *d_vals, int64_t n, int32_t *d_ids,
+DIM3_API int dim3_map(dim3_ctx *ctx, const int32_t *d_vals, int64_t n, int32_t *d_ids,
              int32_t *d_dict, int64_t *n_distinct, void *stream);
 
 /*
@@ -127,19 +152,19 @@ int dim3_map(dim3_ctx *ctx, const int32_t *d_vals, int64_t n, int32_t *d_ids,
  *   info       host, out (may be NULL).
  * Inputs may be freed or reused once the call returns. Synchronises the stream.
  */
-int dim3_partition(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
+DIM3_API int dim3_partition(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
                    const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns,
                    int32_t theta_z, dim3_plan **plan_out, dim3_plan_info *info, void *stream);
 
 /* Copy of the plan's sizes. */
-int dim3_plan_get_info(const dim3_plan *plan, dim3_plan_info *info);
+DIM3_API int dim3_plan_get_info(const dim3_plan *plan, dim3_plan_info *info);
 
 /*
  * dim3_plan_row_counts -- per-x output sizes for the x-id range
  * [x_begin, x_end): d_counts[i] = |{z : (x_begin + i, z) in result}|
  * (int64 device, x_end - x_begin entries). Useful to size x-range chunks.
  */
-int dim3_plan_row_counts(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
+DIM3_API int dim3_plan_row_counts(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
                          int64_t *d_counts, void *stream);
 
 /*
@@ -153,7 +178,7 @@ int dim3_plan_row_counts(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_
  * If capacity < count nothing is written and DIM3_ERR_CAPACITY is returned.
  * x_begin = 0, x_end = n_x covers everything. Synchronises the stream.
  */
-int dim3_plan_join_project(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
+DIM3_API int dim3_plan_join_project(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
                            int32_t *d_out_x, int32_t *d_out_z, int64_t capacity,
                            int64_t *count, void *stream);
 
@@ -162,7 +187,7 @@ int dim3_plan_join_project(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int6
  *   d_out_cnt [capacity] int32 device, out: COUNT(x,z) = number of distinct y
  *             joining x and z (Join-Aggregate, Section 4.1, with COUNT).
  */
-int dim3_plan_join_count(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
+DIM3_API int dim3_plan_join_count(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
                          int32_t *d_out_x, int32_t *d_out_z, int32_t *d_out_cnt,
                          int64_t capacity, int64_t *count, void *stream);
 
@@ -182,10 +207,10 @@ typedef enum {
 } dim3_table;
 
 /* Copy table `which` into d_dst (device), which holds `bytes` bytes. */
-int dim3_plan_export(dim3_plan *plan, int which, void *d_dst, int64_t bytes, void *stream);
+DIM3_API int dim3_plan_export(dim3_plan *plan, int which, void *d_dst, int64_t bytes, void *stream);
 
 /* Free a plan's device tables (stream-ordered on the plan's stream). */
-int dim3_plan_destroy(dim3_plan *plan);
+DIM3_API int dim3_plan_destroy(dim3_plan *plan);
 
 /*
  * dim3_join_project -- the whole hot path of Eq. 1 in one call: partition,
@@ -195,7 +220,7 @@ int dim3_plan_destroy(dim3_plan *plan);
  *                    (then nothing is written).
  * Synchronises the stream.
  */
-int dim3_join_project(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
+DIM3_API int dim3_join_project(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
                       const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns,
                       int32_t *d_out_x, int32_t *d_out_z, int64_t capacity, int64_t *count,
                       void *stream);
@@ -204,7 +229,7 @@ int dim3_join_project(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_
  * dim3_join_count -- Join-Aggregate COUNT (Section 4.1): as dim3_join_project
  * plus d_out_cnt [capacity] int32 device, COUNT(x,z) for every output pair.
  */
-int dim3_join_count(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
+DIM3_API int dim3_join_count(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
                     const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns,
                     int32_t *d_out_x, int32_t *d_out_z, int32_t *d_out_cnt, int64_t capacity,
                     int64_t *count, void *stream);

@@ -1,0 +1,27 @@
+"""GB300-native (sm_103a) DIM^3 Join-Project.
+
+The hot path of DIM^3 (value mapping, intersection-free dense/sparse split,
+SparseBMM, DenseEC, compaction of the deduplicated (x, z) output) runs in the
+CUDA library ``libdim3.so`` behind the C ABI of ``include/dim3.h``; this
+package is its thin binding (``dim3``), plus the batch runner, the serving
+loop and the autotuner built on that ABI.
+"""
+
+from .dim3 import (  # noqa: F401
+    DENSE_AUTO,
+    DENSE_POPC,
+    DENSE_PROBE,
+    DENSE_TC,
+    OPT_BITMAP_ROW_MIN,
+    OPT_DENSE_VARIANT,
+    OPT_LIGHT_ROW_MAX,
+    OPT_THETA_Z,
+    OPT_TIMING,
+    PHASES,
+    Context,
+    Dim3Error,
+    Plan,
+    launch_count,
+    lib_path,
+    load,
+)

@@ -1,0 +1,354 @@
+// The C ABI (include/dim3.h): argument checks, device selection, error
+// reporting, and the order of the steps of Algorithm 1.
+#include <atomic>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "internal.cuh"
+
+struct dim3_ctx {
+    dimcube::Ctx c;
+    dimcube::Stats stats;
+    ~dim3_ctx() {
+        stats.resolve();
+    }
+};
+
+namespace dimcube {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void Stats::resolve() {
+    for (auto& e : pending) {
+        float ms_f = 0.f;
+        if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&ms_f, e.a, e.b) == cudaSuccess) {
+            ms[e.ph] += ms_f;
+            n[e.ph] += 1;
+        }
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    pending.clear();
+}
+
+void Stats::reset() {
+    resolve();
+    for (int i = 0; i < PH_N; ++i) {
+        ms[i] = 0.0;
+        n[i] = 0;
+    }
+}
+
+PhaseScope::PhaseScope(Stats* stats, int phase, cudaStream_t stream)
+    : st(stats && stats->on ? stats : nullptr), ph(phase), s(stream) {
+    if (!st) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess || cudaEventRecord(a, s) != cudaSuccess) {
+        cudaGetLastError();
+        st = nullptr;
+    }
+}
+
+PhaseScope::~PhaseScope() {
+    if (!st) return;
+    if (cudaEventRecord(b, s) == cudaSuccess) {
+        st->pending.push_back({ph, a, b});
+    } else {
+        cudaGetLastError();
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+}
+
+}  // namespace dimcube
+struct dim3_plan {
+    std::unique_ptr<dimcube::Plan> p;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+int guarded(F&& f) {
+    try {
+        f();
+        g_last_error.clear();
+        return DIM3_OK;
+    } catch (const dimcube::Error& e) {
+        g_last_error = e.what();
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return DIM3_ERR_NOMEM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return DIM3_ERR_CUDA;
+    } catch (...) {
+        g_last_error = "unknown error";
+        return DIM3_ERR_CUDA;
+    }
+}
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        DIM3_CUDA(cudaGetDevice(&prev));
+        if (prev != dev) DIM3_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+void check_table(const int32_t* k, const int32_t* v, int64_t n, const char* name) {
+    DIM3_REQUIRE(n >= 0, DIM3_ERR_ARG, std::string(name) + ": negative row count");
+    DIM3_REQUIRE(n == 0 || (k && v), DIM3_ERR_ARG, std::string(name) + ": null column pointer");
+    DIM3_REQUIRE(n < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, std::string(name) + ": more than 2^31 - 1 rows");
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+int dim3_version(void) { return 100; }
+
+const char* dim3_last_error(void) { return g_last_error.c_str(); }
+
+int dim3_ctx_create(dim3_ctx** out, int device) {
+    return guarded([&] {
+        DIM3_REQUIRE(out != nullptr, DIM3_ERR_ARG, "out is null");
+        *out = nullptr;
+        int n = 0;
+        DIM3_CUDA(cudaGetDeviceCount(&n));
+        DIM3_REQUIRE(device >= 0 && device < n, DIM3_ERR_ARG, "no such CUDA device");
+        std::unique_ptr<dim3_ctx> c(new dim3_ctx());
+        c->c.stats = &c->stats;
+        c->c.device = device;
+        cudaDeviceProp prop;
+        DIM3_CUDA(cudaGetDeviceProperties(&prop, device));
+        c->c.sm_count = prop.multiProcessorCount;
+        c->c.smem_optin = (int)prop.sharedMemPerBlockOptin;
+        c->c.cc_major = prop.major;
+        c->c.cc_minor = prop.minor;
+        DIM3_REQUIRE(prop.major == 10 && prop.minor == 3, DIM3_ERR_UNSUPPORTED,
+                     "this library is built for sm_103a (GB300) only; device is sm_" + std::to_string(prop.major) +
+                         std::to_string(prop.minor));
+        // keep freed stream-ordered memory in the pool between calls
+        DeviceGuard g(device);
+        cudaMemPool_t pool;
+        DIM3_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+        uint64_t thr = UINT64_MAX;
+        DIM3_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        *out = c.release();
+    });
+}
+
+int dim3_ctx_destroy(dim3_ctx* ctx) {
+    return guarded([&] { delete ctx; });
+}
+
+int dim3_ctx_set_option(dim3_ctx* ctx, int option, int64_t value) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx, DIM3_ERR_ARG, "ctx is null");
+        switch (option) {
+            case DIM3_OPT_THETA_Z: ctx->c.opt.theta_z = value; break;
+            case DIM3_OPT_DENSE_VARIANT:
+                DIM3_REQUIRE(value >= DIM3_DENSE_AUTO && value <= DIM3_DENSE_PROBE, DIM3_ERR_ARG, "bad DenseEC variant");
+                ctx->c.opt.dense_variant = value;
+                break;
+            case DIM3_OPT_BITMAP_ROW_MIN: ctx->c.opt.bitmap_row_min = value; break;
+            case DIM3_OPT_LIGHT_ROW_MAX: ctx->c.opt.light_row_max = value; break;
+            case DIM3_OPT_TIMING: ctx->stats.on = value != 0; break;
+            default: throw dimcube::Error(DIM3_ERR_ARG, "unknown option " + std::to_string(option));
+        }
+    });
+}
+
+int dim3_map(dim3_ctx* ctx, const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,
+             void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && n_distinct, DIM3_ERR_ARG, "null ctx or n_distinct");
+        DIM3_REQUIRE(n >= 0 && (n == 0 || (d_vals && d_ids && d_dict)), DIM3_ERR_ARG, "bad column arguments");
+        DIM3_REQUIRE(n < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "more than 2^31 - 1 rows");
+        DeviceGuard g(ctx->c.device);
+        cudaStream_t s = as_stream(stream);
+        dimcube::ValueMap vm;
+        {
+            dimcube::PhaseScope ps(ctx->c.stats, dimcube::PH_MAP, s);
+            dimcube::build_value_map(d_vals, nullptr, n, vm, d_ids, d_dict, s);
+        }
+        DIM3_CUDA(cudaStreamSynchronize(s));
+        *n_distinct = vm.n_distinct;
+    });
+}
+
+int dim3_ctx_timing(dim3_ctx* ctx, int phase, double* total_ms, int64_t* launches, int reset) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx, DIM3_ERR_ARG, "ctx is null");
+        DIM3_REQUIRE(phase >= 0 && phase < dimcube::PH_N, DIM3_ERR_ARG, "unknown phase");
+        DeviceGuard g(ctx->c.device);
+        ctx->stats.resolve();
+        if (total_ms) *total_ms = ctx->stats.ms[phase];
+        if (launches) *launches = ctx->stats.n[phase];
+        if (reset) ctx->stats.reset();
+    });
+}
+
+int dim3_launch_count(int64_t* out) {
+    return guarded([&] {
+        DIM3_REQUIRE(out, DIM3_ERR_ARG, "out is null");
+        *out = dimcube::g_launches.load();
+    });
+}
+
+static int64_t resolve_theta(const dim3_ctx* ctx, int32_t theta_z) {
+    if (theta_z >= 0) return theta_z;
+    return ctx->c.opt.theta_z;  // < 0 means the tuned default inside the plan builder
+}
+
+int dim3_partition(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val, int64_t nr, const int32_t* d_s_key,
+                   const int32_t* d_s_val, int64_t ns, int32_t theta_z, dim3_plan** plan_out, dim3_plan_info* info,
+                   void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && plan_out, DIM3_ERR_ARG, "null ctx or plan_out");
+        *plan_out = nullptr;
+        check_table(d_r_key, d_r_val, nr, "R");
+        check_table(d_s_key, d_s_val, ns, "S");
+        DeviceGuard g(ctx->c.device);
+        std::unique_ptr<dim3_plan> pl(new dim3_plan());
+        pl->p.reset(dimcube::build_plan(ctx->c, d_r_key, d_r_val, nr, d_s_key, d_s_val, ns, resolve_theta(ctx, theta_z),
+                                        as_stream(stream)));
+        if (info) *info = pl->p->info;
+        *plan_out = pl.release();
+    });
+}
+
+int dim3_plan_get_info(const dim3_plan* plan, dim3_plan_info* info) {
+    return guarded([&] {
+        DIM3_REQUIRE(plan && info, DIM3_ERR_ARG, "null plan or info");
+        *info = plan->p->info;
+    });
+}
+
+int dim3_plan_row_counts(dim3_ctx* ctx, dim3_plan* plan, int64_t x_begin, int64_t x_end, int64_t* d_counts,
+                         void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && plan, DIM3_ERR_ARG, "null ctx or plan");
+        DIM3_REQUIRE(x_end == x_begin || d_counts, DIM3_ERR_ARG, "null d_counts");
+        DeviceGuard g(ctx->c.device);
+        dimcube::plan_row_counts(ctx->c, *plan->p, x_begin, x_end, d_counts, as_stream(stream));
+        DIM3_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    });
+}
+
+int dim3_plan_join_project(dim3_ctx* ctx, dim3_plan* plan, int64_t x_begin, int64_t x_end, int32_t* d_out_x,
+                           int32_t* d_out_z, int64_t capacity, int64_t* count, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && plan && count, DIM3_ERR_ARG, "null ctx, plan or count");
+        DIM3_REQUIRE(capacity >= 0, DIM3_ERR_ARG, "negative capacity");
+        *count = 0;
+        DeviceGuard g(ctx->c.device);
+        dimcube::plan_join(ctx->c, *plan->p, x_begin, x_end, 0, d_out_x, d_out_z, nullptr, capacity, count,
+                           as_stream(stream));
+    });
+}
+
+int dim3_plan_join_count(dim3_ctx* ctx, dim3_plan* plan, int64_t x_begin, int64_t x_end, int32_t* d_out_x,
+                         int32_t* d_out_z, int32_t* d_out_cnt, int64_t capacity, int64_t* count, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && plan && count, DIM3_ERR_ARG, "null ctx, plan or count");
+        DIM3_REQUIRE(capacity >= 0, DIM3_ERR_ARG, "negative capacity");
+        *count = 0;
+        DeviceGuard g(ctx->c.device);
+        dimcube::plan_join(ctx->c, *plan->p, x_begin, x_end, 1, d_out_x, d_out_z, d_out_cnt, capacity, count,
+                           as_stream(stream));
+    });
+}
+
+int dim3_plan_export(dim3_plan* plan, int which, void* d_dst, int64_t bytes, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(plan, DIM3_ERR_ARG, "null plan");
+        const dimcube::Plan& p = *plan->p;
+        const dim3_plan_info& in = p.info;
+        const void* src = nullptr;
+        int64_t need = 0;
+        switch (which) {
+            case DIM3_TABLE_DICT_X: src = p.dict_x.p; need = in.n_x * 4; break;
+            case DIM3_TABLE_DICT_Y: src = p.dict_y.p; need = in.n_y * 4; break;
+            case DIM3_TABLE_DICT_Z: src = p.dict_z.p; need = in.n_z * 4; break;
+            case DIM3_TABLE_R_ROWPTR: src = p.r_rowptr.p; need = (in.n_x + 1) * 8; break;
+            case DIM3_TABLE_R_COL: src = p.r_col.p; need = in.n_r_kept * 4; break;
+            case DIM3_TABLE_M_Z: src = p.m_z.p; need = in.n_z * 4; break;
+            case DIM3_TABLE_DENSE_Z: src = p.dense_z.p; need = in.n_z; break;
+            case DIM3_TABLE_SS_ROWPTR: src = p.ss_rowptr.p; need = (in.n_y + 1) * 8; break;
+            case DIM3_TABLE_SS_COL: src = p.ss_col.p; need = in.n_s_sparse * 4; break;
+            case DIM3_TABLE_DEG_S: src = p.deg_s.p; need = in.n_y * 4; break;
+            case DIM3_TABLE_OUTJ_X: src = p.outj_x.p; need = in.n_x * 8; break;
+            default: throw dimcube::Error(DIM3_ERR_ARG, "unknown table " + std::to_string(which));
+        }
+        DIM3_REQUIRE(bytes >= need, DIM3_ERR_CAPACITY, "destination smaller than the table");
+        if (need == 0) return;
+        DIM3_REQUIRE(d_dst, DIM3_ERR_ARG, "null destination");
+        DeviceGuard g(p.device);
+        DIM3_CUDA(cudaMemcpyAsync(d_dst, src, (size_t)need, cudaMemcpyDeviceToDevice, as_stream(stream)));
+        DIM3_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    });
+}
+
+int dim3_plan_destroy(dim3_plan* plan) {
+    return guarded([&] {
+        if (!plan) return;
+        DeviceGuard g(plan->p->device);
+        cudaStream_t s = plan->p->stream;
+        delete plan;
+        DIM3_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+static int join_common(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val, int64_t nr,
+                       const int32_t* d_s_key, const int32_t* d_s_val, int64_t ns, int32_t* d_out_x, int32_t* d_out_z,
+                       int32_t* d_out_cnt, int64_t capacity, int64_t* count, void* stream, int kind) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && count, DIM3_ERR_ARG, "null ctx or count");
+        DIM3_REQUIRE(capacity >= 0, DIM3_ERR_ARG, "negative capacity");
+        *count = 0;
+        check_table(d_r_key, d_r_val, nr, "R");
+        check_table(d_s_key, d_s_val, ns, "S");
+        DeviceGuard g(ctx->c.device);
+        cudaStream_t s = as_stream(stream);
+        std::unique_ptr<dimcube::Plan> p(
+            dimcube::build_plan(ctx->c, d_r_key, d_r_val, nr, d_s_key, d_s_val, ns, resolve_theta(ctx, -1), s));
+        try {
+            dimcube::plan_join(ctx->c, *p, 0, p->info.n_x, kind, d_out_x, d_out_z, d_out_cnt, capacity, count, s);
+        } catch (...) {
+            p.reset();
+            cudaStreamSynchronize(s);
+            throw;
+        }
+        p.reset();
+        DIM3_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int dim3_join_project(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val, int64_t nr, const int32_t* d_s_key,
+                      const int32_t* d_s_val, int64_t ns, int32_t* d_out_x, int32_t* d_out_z, int64_t capacity,
+                      int64_t* count, void* stream) {
+    return join_common(ctx, d_r_key, d_r_val, nr, d_s_key, d_s_val, ns, d_out_x, d_out_z, nullptr, capacity, count,
+                       stream, 0);
+}
+
+int dim3_join_count(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val, int64_t nr, const int32_t* d_s_key,
+                    const int32_t* d_s_val, int64_t ns, int32_t* d_out_x, int32_t* d_out_z, int32_t* d_out_cnt,
+                    int64_t capacity, int64_t* count, void* stream) {
+    return join_common(ctx, d_r_key, d_r_val, nr, d_s_key, d_s_val, ns, d_out_x, d_out_z, d_out_cnt, capacity, count,
+                       stream, 1);
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Internal helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/dim3.h"
+
+namespace dimcube {
+
+// Error carried from deep inside the library to the C ABI boundary.
+struct Error : std::runtime_error {
+    int status;
+    Error(int s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define DIM3_CUDA(call)                                                                    \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            int st_ = (e_ == cudaErrorMemoryAllocation) ? DIM3_ERR_NOMEM : DIM3_ERR_CUDA;  \
+            throw ::dimcube::Error(st_, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                  \
+    } while (0)
+
+// Every kernel launch of the library is followed by DIM3_LAUNCHED(): it checks
+// the launch and counts it (dim3_launch_count).
+void count_launch();
+#define DIM3_LAUNCHED()                 \
+    do {                                \
+        ::dimcube::count_launch();      \
+        DIM3_CUDA(cudaGetLastError());  \
+    } while (0)
+
+#define DIM3_REQUIRE(cond, status, msg)                 \
+    do {                                                \
+        if (!(cond)) throw ::dimcube::Error((status), (msg)); \
+    } while (0)
+
+constexpr int kThreads = 256;
+constexpr int kSms = 152;  // GB300; the real count is queried at context creation
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int bits_for(int64_t n) {  // bits needed to store values 0..n-1 (at least 1)
+    int b = 1;
+    while (b < 62 && (int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; o.bytes = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; bytes = o.bytes; s = o.s;
+            o.p = nullptr; o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t n, cudaStream_t st) {
+        release();
+        s = st;
+        bytes = n;
+        if (n == 0) return;
+        cudaError_t e = cudaMallocAsync(&p, n, st);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            throw Error(DIM3_ERR_NOMEM, "device allocation of " + std::to_string(n) +
+                                            " bytes failed: " + cudaGetErrorString(e));
+        }
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------- launchers
+// primitives (prims.cu)
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);  // out[n+1]
+void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s);
+int64_t read_i64(const int64_t* d, cudaStream_t s);  // synchronising read of one device value
+// LSD radix sort of n keys (32- or 64-bit) on their low `bits` bits, with an
+// optional uint32 payload. Results end in keys/vals (the alt buffers are scratch).
+void radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                    int64_t n, int bits, cudaStream_t s);
+void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                    int64_t n, int bits, cudaStream_t s);
+// Drop adjacent duplicates of sorted keys; returns the count (synchronising).
+int64_t unique_sorted_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+int64_t unique_sorted_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s);
+// rowptr[r] = first index i with (keys[i] >> shift) >= r, for r = 0..n_rows
+void rowptr_from_sorted_u32(const uint32_t* keys, int64_t n, int shift, int64_t n_rows,
+                            int64_t* rowptr, cudaStream_t s);
+void rowptr_from_sorted_u64(const uint64_t* keys, int64_t n, int shift, int64_t n_rows,
+                            int64_t* rowptr, cudaStream_t s);
+
+}  // namespace dimcube

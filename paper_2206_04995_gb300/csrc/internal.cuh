@@ -1,0 +1,123 @@
+// Internal plan structures and step launchers.
+#pragma once
+
+#include "common.cuh"
+
+namespace dimcube {
+
+// ----------------------------------------------------------------- mapping
+// An order-preserving map of one column's values to dense ids (ranks among
+// the distinct values). The hash table stays alive so other columns can be
+// probed against it (semi-join of Section 2.2, Optimization 2).
+struct ValueMap {
+    DevBuf table;  // uint64 slots: 0 = empty, else (1 << 32) | uint32(value)
+    DevBuf rank;   // uint32 per slot: rank of the slot's value
+    uint32_t mask = 0;
+    int64_t n_distinct = 0;
+};
+
+// Map vals[0..n) (rows with pred[i] < 0 are skipped and get id -1).
+// ids_out [n]; dict_out [n] capacity, first n_distinct ascending.
+void build_value_map(const int32_t* vals, const int32_t* pred, int64_t n, ValueMap& vm,
+                     int32_t* ids_out, int32_t* dict_out, cudaStream_t s);
+// ids_out[i] = id of vals[i] in vm, or -1 if absent.
+void probe_value_map(const ValueMap& vm, const int32_t* vals, int64_t n, int32_t* ids_out,
+                     cudaStream_t s);
+
+// -------------------------------------------------------------------- plan
+struct Options {
+    int64_t theta_z = -1;
+    int64_t dense_variant = DIM3_DENSE_AUTO;
+    int64_t bitmap_row_min = -1;
+    int64_t light_row_max = -1;
+};
+
+struct Plan {
+    dim3_plan_info info{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    Options opt;
+    // mapping
+    DevBuf dict_x, dict_y, dict_z;  // int32
+    // R_CSR by x id
+    DevBuf r_rowptr;  // int64 [n_x + 1]
+    DevBuf r_col;     // int32 [n_r_kept], y ids ascending per row
+    DevBuf outj_x;    // int64 [n_x], join tuples per x
+    // degrees
+    DevBuf m_z;       // int32 [n_z]
+    DevBuf deg_s;     // int32 [n_y]
+    DevBuf dense_z;   // uint8 [n_z]
+    // S_sparse CSR by y id
+    DevBuf ss_rowptr;   // int64 [n_y + 1]
+    DevBuf ss_col;      // int32 [n_s_sparse], z ids ascending per row
+    DevBuf bm_row_of_y; // int32 [n_y], bitmap row or -1
+    DevBuf ss_bits;     // uint32 [n_y_bitmap][zw]
+    int64_t zw = 0;     // words per z bitmap
+    // S_dense
+    DevBuf zd_list;     // int32 [n_zd]: dense index -> z id (ascending)
+    DevBuf kidx_of_y;   // int32 [n_y]: y id -> K index or -1
+    DevBuf b_tc;        // uint8 [n_zd_pad][k_pad]: e4m3 0/1, K-major (tensor-core operand)
+    DevBuf b_bits;      // uint32 [n_zd][kw]: Bitmap_z over K (AND+popc operand)
+    DevBuf sdt_bits;    // uint32 [n_yd][zdw]: S_dense rows by y over dense index (probe operand)
+    int64_t k_pad = 0, kw = 0, zdw = 0, n_zd_pad = 0;
+    // cached row offsets of the last counting pass
+    int64_t cache_begin = -1, cache_end = -1;
+    int cache_kind = -1;
+    DevBuf cache_off;  // int64 [rows + 1]
+    DevBuf cache_dbits; // dense bits of the cached range
+    DevBuf cache_dcnt;  // dense counts of the cached range
+};
+
+// Per-phase CUDA-event timing (DIM3_OPT_TIMING). Events are recorded on the
+// launching stream around a phase and resolved when the caller asks.
+enum Phase { PH_MAP = 0, PH_PARTITION = 1, PH_DENSE = 2, PH_COUNT = 3, PH_EMIT = 4, PH_N = 5 };
+struct Stats {
+    bool on = false;
+    double ms[PH_N] = {};
+    int64_t n[PH_N] = {};
+    struct Pending {
+        int ph;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    void resolve();
+    void reset();
+};
+struct PhaseScope {
+    Stats* st = nullptr;
+    int ph = 0;
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    PhaseScope(Stats* stats, int phase, cudaStream_t stream);
+    ~PhaseScope();
+};
+
+struct Ctx {
+    Stats* stats = nullptr;  // owned by the ABI context
+    int device = 0;
+    int sm_count = 152;
+    int smem_optin = 227 * 1024;
+    int cc_major = 0, cc_minor = 0;
+    Options opt;
+};
+
+Plan* build_plan(const Ctx& ctx, const int32_t* r_key, const int32_t* r_val, int64_t nr,
+                 const int32_t* s_key, const int32_t* s_val, int64_t ns, int64_t theta_z,
+                 cudaStream_t s);
+
+// Output of a join over an x-id range: counts pass + scan + emit pass.
+// kind 0 = project, 1 = count. Returns the number of pairs; writes only when
+// capacity >= pairs (else throws DIM3_ERR_CAPACITY after setting *count).
+int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int kind, int32_t* out_x,
+                  int32_t* out_z, int32_t* out_cnt, int64_t capacity, int64_t* count, cudaStream_t s);
+void plan_row_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int64_t* d_counts,
+                     cudaStream_t s);
+
+// DenseEC over rows [x_begin, x_begin + rows): dense result bits [rows][zdw]
+// (kind 0) or dense counts [rows][n_zd] int32 (kind 1).
+void dense_ec(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int kind, uint32_t* d_bits,
+              int32_t* d_cnt, cudaStream_t s);
+void dense_build_operands(const Ctx& ctx, Plan& p, const uint64_t* s_keys_u64, const uint32_t* s_keys_u32,
+                          int64_t n_s, int bz, const int32_t* zd_index, cudaStream_t s);
+
+}  // namespace dimcube

@@ -1,0 +1,160 @@
+// Step 1 of Algorithm 1: mapping column values to consecutive natural
+// numbers (Section 2.2).
+//
+// GPU form: an open-addressing linear-probing hash table (the paper's
+// Optimization 3 uses linear probing too) is filled by all threads at once;
+// the distinct keys are collected and radix-sorted, and each distinct value's
+// id is its rank. Ranks, unlike first-seen numbering, do not depend on the
+// order in which threads reach the table, so the mapping is deterministic and
+// order-preserving (id order = signed value order).
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace dimcube {
+
+constexpr uint32_t kNoSlot = 0xffffffffu;
+
+__device__ __forceinline__ uint64_t table_key(int32_t v) {
+    return (uint64_t(1) << 32) | (uint64_t)(uint32_t)v;
+}
+
+// Insert every value (rows with pred < 0 skipped); slot_out[i] = its slot.
+__global__ void k_hash_insert(const int32_t* __restrict__ vals, const int32_t* __restrict__ pred,
+                              int64_t n, unsigned long long* table, uint32_t mask,
+                              uint32_t* __restrict__ slot_out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (pred && pred[i] < 0) {
+            slot_out[i] = kNoSlot;
+            continue;
+        }
+        const int32_t v = vals[i];
+        const unsigned long long key = table_key(v);
+        uint32_t h = fmix32((uint32_t)v) & mask;
+        // The table holds at least twice as many slots as rows, so the probe
+        // sequence always reaches the key or an empty slot within mask+1 steps.
+        for (uint32_t step = 0; step <= mask; ++step) {
+            unsigned long long cur = table[h];
+            if (cur == key) break;
+            if (cur == 0ull) {
+                unsigned long long old = atomicCAS(&table[h], 0ull, key);
+                if (old == 0ull || old == key) break;
+            }
+            h = (h + 1) & mask;
+        }
+        slot_out[i] = h;
+    }
+}
+
+// Append every occupied slot's (order key, slot) to the output arrays.
+__global__ void k_hash_collect(const unsigned long long* table, int64_t cap, uint32_t* okeys,
+                               uint32_t* oslots, unsigned long long* counter) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t iters = (cap + stride - 1) / stride;
+    const unsigned lane = lane_id();
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t s = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const bool occ = s < cap && table[s] != 0ull;
+        const unsigned b = __ballot_sync(kFull, occ);
+        unsigned long long base = 0;
+        if (lane == 0 && b) base = atomicAdd(counter, (unsigned long long)__popc(b));
+        base = __shfl_sync(kFull, base, 0);
+        if (occ) {
+            const unsigned long long pos = base + __popc(b & lanemask_lt());
+            okeys[pos] = ((uint32_t)table[s]) ^ 0x80000000u;  // signed order as unsigned
+            oslots[pos] = (uint32_t)s;
+        }
+    }
+}
+
+__global__ void k_hash_rank(const uint32_t* skeys, const uint32_t* sslots, int64_t d, uint32_t* rank,
+                            int32_t* dict_out) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        rank[sslots[p]] = (uint32_t)p;
+        dict_out[p] = (int32_t)(skeys[p] ^ 0x80000000u);
+    }
+}
+
+__global__ void k_gather_rank(const uint32_t* slot, int64_t n, const uint32_t* rank, int32_t* ids) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = slot[i];
+        ids[i] = s == kNoSlot ? -1 : (int32_t)rank[s];
+    }
+}
+
+__global__ void k_hash_probe(const int32_t* __restrict__ vals, int64_t n, const unsigned long long* table,
+                             uint32_t mask, const uint32_t* __restrict__ rank, int32_t* __restrict__ ids) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = vals[i];
+        const unsigned long long key = table_key(v);
+        uint32_t h = fmix32((uint32_t)v) & mask;
+        int32_t id = -1;
+        for (uint32_t step = 0; step <= mask; ++step) {
+            const unsigned long long cur = table[h];
+            if (cur == key) {
+                id = (int32_t)rank[h];
+                break;
+            }
+            if (cur == 0ull) break;
+            h = (h + 1) & mask;
+        }
+        ids[i] = id;
+    }
+}
+
+static unsigned grid_for(int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kThreads), 152 * 16));
+}
+
+void build_value_map(const int32_t* vals, const int32_t* pred, int64_t n, ValueMap& vm, int32_t* ids_out,
+                     int32_t* dict_out, cudaStream_t s) {
+    int64_t cap = 64;
+    while (cap < 2 * n) cap <<= 1;
+    DIM3_REQUIRE(cap <= (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "column too long for the value map");
+    vm.mask = (uint32_t)(cap - 1);
+    vm.table.alloc((size_t)cap * 8, s);
+    vm.rank.alloc((size_t)cap * 4, s);
+    DIM3_CUDA(cudaMemsetAsync(vm.table.p, 0, (size_t)cap * 8, s));
+    vm.n_distinct = 0;
+    if (n == 0) return;
+    DevBuf slots;
+    slots.alloc((size_t)n * 4, s);
+    k_hash_insert<<<grid_for(n), kThreads, 0, s>>>(vals, pred, n, vm.table.as<unsigned long long>(),
+                                                    vm.mask, slots.as<uint32_t>());
+    DIM3_LAUNCHED();
+    DevBuf counter, keys, sl, keys_alt, sl_alt;
+    counter.alloc(8, s);
+    DIM3_CUDA(cudaMemsetAsync(counter.p, 0, 8, s));
+    keys.alloc((size_t)n * 4, s);
+    sl.alloc((size_t)n * 4, s);
+    k_hash_collect<<<grid_for(cap), kThreads, 0, s>>>(vm.table.as<unsigned long long>(), cap,
+                                                       keys.as<uint32_t>(), sl.as<uint32_t>(),
+                                                       counter.as<unsigned long long>());
+    DIM3_LAUNCHED();
+    const int64_t d = read_i64(counter.as<int64_t>(), s);
+    DIM3_REQUIRE(d >= 0 && d <= n, DIM3_ERR_CUDA, "value map: inconsistent distinct count");
+    vm.n_distinct = d;
+    keys_alt.alloc((size_t)d * 4, s);
+    sl_alt.alloc((size_t)d * 4, s);
+    radix_sort_u32(keys.as<uint32_t>(), sl.as<uint32_t>(), keys_alt.as<uint32_t>(), sl_alt.as<uint32_t>(), d,
+                   32, s);
+    k_hash_rank<<<grid_for(d), kThreads, 0, s>>>(keys.as<uint32_t>(), sl.as<uint32_t>(), d,
+                                                  vm.rank.as<uint32_t>(), dict_out);
+    DIM3_LAUNCHED();
+    k_gather_rank<<<grid_for(n), kThreads, 0, s>>>(slots.as<uint32_t>(), n, vm.rank.as<uint32_t>(), ids_out);
+    DIM3_LAUNCHED();
+}
+
+void probe_value_map(const ValueMap& vm, const int32_t* vals, int64_t n, int32_t* ids_out, cudaStream_t s) {
+    if (n == 0) return;
+    k_hash_probe<<<grid_for(n), kThreads, 0, s>>>(vals, n, vm.table.as<unsigned long long>(), vm.mask,
+                                                   vm.rank.as<uint32_t>(), ids_out);
+    DIM3_LAUNCHED();
+}
+
+}  // namespace dimcube

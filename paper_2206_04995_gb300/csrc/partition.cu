@@ -1,0 +1,391 @@
+// Steps 2-3 of Algorithm 1: R_CSR by x, degrees, and the intersection-free
+// partition of S by z (Section 2.3) into S_sparse (CSR by y, Section 2.4) and
+// S_dense (Section 2.5).
+//
+// Tuples are packed into one integer key (row id in the high bits, column id
+// in the low bits) and radix-sorted; adjacent duplicates are dropped, which
+// applies set semantics, and CSR row pointers come from binary searches over
+// the sorted keys. Every z is judged once (dense iff m_z >= theta_z), so all
+// tuples of one z land on the same side and the two results are disjoint.
+#include <algorithm>
+#include <climits>
+#include <memory>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace dimcube {
+
+static unsigned grid_for(int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kThreads), 152 * 16));
+}
+
+#define GRID_STRIDE(i, n)                                                        \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
+         i += (int64_t)gridDim.x * blockDim.x)
+
+// Append key = (a << shift) | b for rows with a >= 0 and b >= 0 (unordered;
+// a sort follows).
+template <typename K>
+__global__ void k_pack_pairs(const int32_t* a, const int32_t* b, int64_t n, int shift, K* keys,
+                             unsigned long long* counter) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t iters = (n + stride - 1) / stride;
+    const unsigned lane = lane_id();
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        int32_t av = -1, bv = -1;
+        if (i < n) {
+            av = a[i];
+            bv = b[i];
+        }
+        const bool ok = av >= 0 && bv >= 0;
+        const unsigned bal = __ballot_sync(kFull, ok);
+        unsigned long long base = 0;
+        if (lane == 0 && bal) base = atomicAdd(counter, (unsigned long long)__popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        if (ok) keys[base + __popc(bal & lanemask_lt())] = ((K)(uint32_t)av << shift) | (K)(uint32_t)bv;
+    }
+}
+
+template <typename K>
+__global__ void k_split_low(const K* keys, int64_t n, K mask, int32_t* col) {
+    GRID_STRIDE(i, n) col[i] = (int32_t)(keys[i] & mask);
+}
+
+template <typename K>
+__global__ void k_hist_low(const K* keys, int64_t n, K mask, int32_t* hist) {
+    GRID_STRIDE(i, n) atomicAdd(&hist[(int64_t)(keys[i] & mask)], 1);
+}
+
+__global__ void k_row_len(const int64_t* rowptr, int64_t n_rows, int32_t* len) {
+    GRID_STRIDE(r, n_rows) len[r] = (int32_t)(rowptr[r + 1] - rowptr[r]);
+}
+
+// join tuples per x: sum of deg_S(y) over y in R[x]
+__global__ void k_outj_x(const int64_t* r_rowptr, const int32_t* r_col, int64_t n_x, const int32_t* deg_s,
+                         int64_t* outj_x) {
+    GRID_STRIDE(x, n_x) {
+        int64_t acc = 0;
+        for (int64_t p = r_rowptr[x]; p < r_rowptr[x + 1]; ++p) acc += deg_s[r_col[p]];
+        outj_x[x] = acc;
+    }
+}
+
+__global__ void k_dense_flags(const int32_t* m_z, int64_t n_z, int64_t theta, uint8_t* dense_u8, int32_t* flag) {
+    GRID_STRIDE(z, n_z) {
+        const bool d = (int64_t)m_z[z] >= theta;
+        dense_u8[z] = d ? 1 : 0;
+        flag[z] = d ? 1 : 0;
+    }
+}
+
+// dense index of every dense z (order-preserving compaction of the flags)
+__global__ void k_zd_list(const int32_t* flag, const int64_t* pos, int64_t n_z, int32_t* zd_list, int32_t* zd_index) {
+    GRID_STRIDE(z, n_z) {
+        if (flag[z]) {
+            zd_list[pos[z]] = (int32_t)z;
+            zd_index[z] = (int32_t)pos[z];
+        } else {
+            zd_index[z] = -1;
+        }
+    }
+}
+
+template <typename K>
+__global__ void k_sparse_flags(const K* keys, int64_t n, K zmask, const uint8_t* dense_u8, int32_t* flag) {
+    GRID_STRIDE(i, n) flag[i] = dense_u8[(int64_t)(keys[i] & zmask)] ? 0 : 1;
+}
+
+template <typename K>
+__global__ void k_compact(const K* in, int64_t n, const int32_t* flag, const int64_t* pos, K* out) {
+    GRID_STRIDE(i, n) if (flag[i]) out[pos[i]] = in[i];
+}
+
+__global__ void k_wide_flags(const int64_t* rowptr, int64_t n_rows, int64_t min_len, int32_t* flag) {
+    GRID_STRIDE(r, n_rows) flag[r] = (rowptr[r + 1] - rowptr[r]) >= min_len ? 1 : 0;
+}
+
+__global__ void k_index_from_flags(const int32_t* flag, const int64_t* pos, int64_t n, int32_t* idx) {
+    GRID_STRIDE(i, n) idx[i] = flag[i] ? (int32_t)pos[i] : -1;
+}
+
+// bitmap rows of the wide S_sparse rows
+template <typename K>
+__global__ void k_fill_row_bits(const K* keys, int64_t n, int bz, K zmask, const int32_t* row_of_y,
+                                uint32_t* bits, int64_t zw) {
+    GRID_STRIDE(i, n) {
+        const K k = keys[i];
+        const int32_t b = row_of_y[(int64_t)(k >> bz)];
+        if (b >= 0) {
+            const int64_t z = (int64_t)(k & zmask);
+            atomicOr(&bits[(int64_t)b * zw + (z >> 5)], 1u << (z & 31));
+        }
+    }
+}
+
+template <typename K>
+__global__ void k_mark_dense_y(const K* keys, int64_t n, int bz, K zmask, const uint8_t* dense_u8, int32_t* flag_y) {
+    GRID_STRIDE(i, n) {
+        const K k = keys[i];
+        if (dense_u8[(int64_t)(k & zmask)]) flag_y[(int64_t)(k >> bz)] = 1;
+    }
+}
+
+// ------------------------------------------------------------------------
+template <typename K>
+struct SortedPairs {
+    DevBuf keys;  // sorted unique
+    int64_t n = 0;
+};
+
+template <typename K>
+static void sort_unique_pairs(const int32_t* a, const int32_t* b, int64_t n, int shift, int bits,
+                              SortedPairs<K>& out, cudaStream_t s) {
+    DevBuf keys, alt, counter;
+    keys.alloc((size_t)std::max<int64_t>(n, 1) * sizeof(K), s);
+    counter.alloc(8, s);
+    DIM3_CUDA(cudaMemsetAsync(counter.p, 0, 8, s));
+    if (n > 0) {
+        k_pack_pairs<K><<<grid_for(n), kThreads, 0, s>>>(a, b, n, shift, keys.as<K>(),
+                                                          counter.as<unsigned long long>());
+        DIM3_LAUNCHED();
+    }
+    const int64_t m = read_i64(counter.as<int64_t>(), s);
+    alt.alloc((size_t)std::max<int64_t>(m, 1) * sizeof(K), s);
+    if constexpr (sizeof(K) == 4)
+        radix_sort_u32(keys.as<uint32_t>(), nullptr, alt.as<uint32_t>(), nullptr, m, bits, s);
+    else
+        radix_sort_u64(keys.as<uint64_t>(), nullptr, alt.as<uint64_t>(), nullptr, m, bits, s);
+    // unique into alt, then keep alt
+    int64_t u;
+    if constexpr (sizeof(K) == 4)
+        u = unique_sorted_u32(keys.as<uint32_t>(), alt.as<uint32_t>(), m, s);
+    else
+        u = unique_sorted_u64(keys.as<uint64_t>(), alt.as<uint64_t>(), m, s);
+    out.keys = std::move(alt);
+    out.n = u;
+}
+
+template <typename K>
+static void rowptr_sorted(const K* keys, int64_t n, int shift, int64_t n_rows, int64_t* rowptr, cudaStream_t s) {
+    if constexpr (sizeof(K) == 4)
+        rowptr_from_sorted_u32(keys, n, shift, n_rows, rowptr, s);
+    else
+        rowptr_from_sorted_u64(keys, n, shift, n_rows, rowptr, s);
+}
+
+// R side: CSR of the kept distinct R tuples by x id.
+template <typename K>
+static void build_r_side(Plan& p, const int32_t* rx_id, const int32_t* ry_id, int64_t nr, int bx, int by,
+                         cudaStream_t s) {
+    SortedPairs<K> r;
+    sort_unique_pairs<K>(rx_id, ry_id, nr, by, bx + by, r, s);
+    const int64_t n_x = p.info.n_x;
+    p.info.n_r_kept = r.n;
+    p.r_col.alloc((size_t)std::max<int64_t>(r.n, 1) * 4, s);
+    p.r_rowptr.alloc((size_t)(n_x + 1) * 8, s);
+    if (r.n > 0) {
+        k_split_low<K><<<grid_for(r.n), kThreads, 0, s>>>(r.keys.template as<K>(), r.n, (K)((K(1) << by) - 1),
+                                                           p.r_col.as<int32_t>());
+        DIM3_LAUNCHED();
+    }
+    rowptr_sorted<K>(r.keys.template as<K>(), r.n, by, n_x, p.r_rowptr.as<int64_t>(), s);
+}
+
+// S side: everything that depends on the distinct S tuples sorted by (y, z).
+template <typename K>
+static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const int32_t* sz_id, int64_t ns,
+                         int by, int bz, int64_t theta, cudaStream_t s) {
+    const int64_t n_y = p.info.n_y, n_z = p.info.n_z, n_x = p.info.n_x;
+    const K zmask = (K)((K(1) << bz) - 1);
+    SortedPairs<K> sp;
+    sort_unique_pairs<K>(sy_id, sz_id, ns, bz, by + bz, sp, s);
+    p.info.n_s_distinct = sp.n;
+    const K* keys = sp.keys.template as<K>();
+
+    // deg_S(y) and m_z
+    DevBuf s_rowptr;
+    s_rowptr.alloc((size_t)(n_y + 1) * 8, s);
+    rowptr_sorted<K>(keys, sp.n, bz, n_y, s_rowptr.as<int64_t>(), s);
+    p.deg_s.alloc((size_t)std::max<int64_t>(n_y, 1) * 4, s);
+    if (n_y > 0) {
+        k_row_len<<<grid_for(n_y), kThreads, 0, s>>>(s_rowptr.as<int64_t>(), n_y, p.deg_s.as<int32_t>());
+        DIM3_LAUNCHED();
+    }
+    p.m_z.alloc((size_t)std::max<int64_t>(n_z, 1) * 4, s);
+    DIM3_CUDA(cudaMemsetAsync(p.m_z.p, 0, (size_t)std::max<int64_t>(n_z, 1) * 4, s));
+    if (sp.n > 0) {
+        k_hist_low<K><<<grid_for(sp.n), kThreads, 0, s>>>(keys, sp.n, zmask, p.m_z.as<int32_t>());
+        DIM3_LAUNCHED();
+    }
+
+    // join tuples per x and |OUT_J|
+    p.outj_x.alloc((size_t)std::max<int64_t>(n_x, 1) * 8, s);
+    if (n_x > 0) {
+        k_outj_x<<<grid_for(n_x), kThreads, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(), n_x,
+                                                     p.deg_s.as<int32_t>(), p.outj_x.as<int64_t>());
+        DIM3_LAUNCHED();
+        DevBuf sc;
+        sc.alloc((size_t)(n_x + 1) * 8, s);
+        exclusive_scan_i64(p.outj_x.as<int64_t>(), sc.as<int64_t>(), n_x, s);
+        p.info.out_j = read_i64(sc.as<int64_t>() + n_x, s);
+    } else {
+        p.info.out_j = 0;
+    }
+
+    // intersection-free split: z dense iff m_z >= theta
+    if (theta < 0) theta = INT32_MAX;  // tuned choice made by the caller; default all sparse
+    p.info.theta_z = (int32_t)std::min<int64_t>(theta, INT32_MAX);
+    p.dense_z.alloc((size_t)std::max<int64_t>(n_z, 1), s);
+    DevBuf zflag, zpos, zd_index;
+    zflag.alloc((size_t)std::max<int64_t>(n_z, 1) * 4, s);
+    zpos.alloc((size_t)(n_z + 1) * 8, s);
+    zd_index.alloc((size_t)std::max<int64_t>(n_z, 1) * 4, s);
+    int64_t n_zd = 0;
+    if (n_z > 0) {
+        k_dense_flags<<<grid_for(n_z), kThreads, 0, s>>>(p.m_z.as<int32_t>(), n_z, theta, p.dense_z.as<uint8_t>(),
+                                                          zflag.as<int32_t>());
+        DIM3_LAUNCHED();
+        exclusive_scan_i32_to_i64(zflag.as<int32_t>(), zpos.as<int64_t>(), n_z, s);
+        n_zd = read_i64(zpos.as<int64_t>() + n_z, s);
+        p.zd_list.alloc((size_t)std::max<int64_t>(n_zd, 1) * 4, s);
+        k_zd_list<<<grid_for(n_z), kThreads, 0, s>>>(zflag.as<int32_t>(), zpos.as<int64_t>(), n_z,
+                                                      p.zd_list.as<int32_t>(), zd_index.as<int32_t>());
+        DIM3_LAUNCHED();
+    }
+    p.info.n_z_dense = n_zd;
+
+    // S_sparse: the distinct tuples of sparse z, still sorted by (y, z)
+    DevBuf sflag, spos, skeys;
+    int64_t n_ss = 0;
+    if (sp.n > 0) {
+        sflag.alloc((size_t)sp.n * 4, s);
+        spos.alloc((size_t)(sp.n + 1) * 8, s);
+        k_sparse_flags<K><<<grid_for(sp.n), kThreads, 0, s>>>(keys, sp.n, zmask, p.dense_z.as<uint8_t>(),
+                                                               sflag.as<int32_t>());
+        DIM3_LAUNCHED();
+        exclusive_scan_i32_to_i64(sflag.as<int32_t>(), spos.as<int64_t>(), sp.n, s);
+        n_ss = read_i64(spos.as<int64_t>() + sp.n, s);
+    }
+    p.info.n_s_sparse = n_ss;
+    skeys.alloc((size_t)std::max<int64_t>(n_ss, 1) * sizeof(K), s);
+    if (n_ss > 0) {
+        k_compact<K><<<grid_for(sp.n), kThreads, 0, s>>>(keys, sp.n, sflag.as<int32_t>(), spos.as<int64_t>(),
+                                                          skeys.as<K>());
+        DIM3_LAUNCHED();
+    }
+    p.ss_col.alloc((size_t)std::max<int64_t>(n_ss, 1) * 4, s);
+    p.ss_rowptr.alloc((size_t)(n_y + 1) * 8, s);
+    if (n_ss > 0) {
+        k_split_low<K><<<grid_for(n_ss), kThreads, 0, s>>>(skeys.as<K>(), n_ss, zmask, p.ss_col.as<int32_t>());
+        DIM3_LAUNCHED();
+    }
+    rowptr_sorted<K>(skeys.as<K>(), n_ss, bz, n_y, p.ss_rowptr.as<int64_t>(), s);
+
+    // wide S_sparse rows held as z-bitmaps (|Z|/32 words per row)
+    p.zw = ceil_div(std::max<int64_t>(n_z, 1), 32);
+    int64_t min_len = p.opt.bitmap_row_min >= 0 ? p.opt.bitmap_row_min : std::max<int64_t>(p.zw, 8);
+    p.bm_row_of_y.alloc((size_t)std::max<int64_t>(n_y, 1) * 4, s);
+    int64_t n_bm = 0;
+    if (n_y > 0) {
+        DevBuf yflag, ypos;
+        yflag.alloc((size_t)n_y * 4, s);
+        ypos.alloc((size_t)(n_y + 1) * 8, s);
+        // bound the bitmap memory: raise the threshold until the rows fit 4 GiB
+        const int64_t budget_words = (int64_t(4) << 30) / 4;
+        for (;;) {
+            k_wide_flags<<<grid_for(n_y), kThreads, 0, s>>>(p.ss_rowptr.as<int64_t>(), n_y, std::max<int64_t>(min_len, 1),
+                                                             yflag.as<int32_t>());
+            DIM3_LAUNCHED();
+            exclusive_scan_i32_to_i64(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y, s);
+            n_bm = read_i64(ypos.as<int64_t>() + n_y, s);
+            if (n_bm * p.zw <= budget_words) break;
+            min_len = std::max<int64_t>(min_len * 2, 1);
+        }
+        k_index_from_flags<<<grid_for(n_y), kThreads, 0, s>>>(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y,
+                                                               p.bm_row_of_y.as<int32_t>());
+        DIM3_LAUNCHED();
+    }
+    p.info.n_y_bitmap = n_bm;
+    p.ss_bits.alloc((size_t)std::max<int64_t>(n_bm * p.zw, 1) * 4, s);
+    if (n_bm > 0) {
+        DIM3_CUDA(cudaMemsetAsync(p.ss_bits.p, 0, (size_t)(n_bm * p.zw) * 4, s));
+        k_fill_row_bits<K><<<grid_for(n_ss), kThreads, 0, s>>>(skeys.as<K>(), n_ss, bz, zmask,
+                                                                p.bm_row_of_y.as<int32_t>(), p.ss_bits.as<uint32_t>(),
+                                                                p.zw);
+        DIM3_LAUNCHED();
+    }
+
+    // S_dense: K = distinct y of the dense tuples
+    p.kidx_of_y.alloc((size_t)std::max<int64_t>(n_y, 1) * 4, s);
+    p.info.n_y_dense = 0;
+    if (n_zd > 0 && sp.n > 0) {
+        DevBuf yflag, ypos;
+        yflag.alloc((size_t)n_y * 4, s);
+        ypos.alloc((size_t)(n_y + 1) * 8, s);
+        DIM3_CUDA(cudaMemsetAsync(yflag.p, 0, (size_t)n_y * 4, s));
+        k_mark_dense_y<K><<<grid_for(sp.n), kThreads, 0, s>>>(keys, sp.n, bz, zmask, p.dense_z.as<uint8_t>(),
+                                                               yflag.as<int32_t>());
+        DIM3_LAUNCHED();
+        exclusive_scan_i32_to_i64(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y, s);
+        p.info.n_y_dense = read_i64(ypos.as<int64_t>() + n_y, s);
+        k_index_from_flags<<<grid_for(n_y), kThreads, 0, s>>>(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y,
+                                                               p.kidx_of_y.as<int32_t>());
+        DIM3_LAUNCHED();
+        if constexpr (sizeof(K) == 8)
+            dense_build_operands(ctx, p, keys, nullptr, sp.n, bz, zd_index.as<int32_t>(), s);
+        else
+            dense_build_operands(ctx, p, nullptr, keys, sp.n, bz, zd_index.as<int32_t>(), s);
+    }
+}
+
+Plan* build_plan(const Ctx& ctx, const int32_t* r_key, const int32_t* r_val, int64_t nr, const int32_t* s_key,
+                 const int32_t* s_val, int64_t ns, int64_t theta_z, cudaStream_t s) {
+    PhaseScope phase(ctx.stats, PH_PARTITION, s);
+    std::unique_ptr<Plan> p(new Plan());
+    p->stream = s;
+    p->device = ctx.device;
+    p->opt = ctx.opt;
+    p->info.n_r = nr;
+    p->info.n_s = ns;
+
+    DevBuf sy_id, sz_id, ry_id, rx_id;
+    sy_id.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+    sz_id.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+    ry_id.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+    rx_id.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+    {
+        // y from S.y; R tuples whose y is absent from S.y get id -1 (dropped)
+        ValueMap ymap;
+        p->dict_y.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+        build_value_map(s_key, nullptr, ns, ymap, sy_id.as<int32_t>(), p->dict_y.as<int32_t>(), s);
+        p->info.n_y = ymap.n_distinct;
+        probe_value_map(ymap, r_key, nr, ry_id.as<int32_t>(), s);
+    }
+    {
+        ValueMap xmap;
+        p->dict_x.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+        build_value_map(r_val, ry_id.as<int32_t>(), nr, xmap, rx_id.as<int32_t>(), p->dict_x.as<int32_t>(), s);
+        p->info.n_x = xmap.n_distinct;
+    }
+    {
+        ValueMap zmap;
+        p->dict_z.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+        build_value_map(s_val, nullptr, ns, zmap, sz_id.as<int32_t>(), p->dict_z.as<int32_t>(), s);
+        p->info.n_z = zmap.n_distinct;
+    }
+    const int bx = bits_for(p->info.n_x), by = bits_for(p->info.n_y), bz = bits_for(p->info.n_z);
+    if (bx + by <= 32)
+        build_r_side<uint32_t>(*p, rx_id.as<int32_t>(), ry_id.as<int32_t>(), nr, bx, by, s);
+    else
+        build_r_side<uint64_t>(*p, rx_id.as<int32_t>(), ry_id.as<int32_t>(), nr, bx, by, s);
+    if (by + bz <= 32)
+        build_s_side<uint32_t>(ctx, *p, sy_id.as<int32_t>(), sz_id.as<int32_t>(), ns, by, bz, theta_z, s);
+    else
+        build_s_side<uint64_t>(ctx, *p, sy_id.as<int32_t>(), sz_id.as<int32_t>(), ns, by, bz, theta_z, s);
+    DIM3_CUDA(cudaStreamSynchronize(s));
+    return p.release();
+}
+
+}  // namespace dimcube

@@ -1,0 +1,437 @@
+// SparseBMM (Algorithm 2), the union with DenseEC's result (Algorithm 1, last
+// step) and compaction into canonical order.
+//
+// GPU form. One CTA owns one x. Its SPA (Algorithm 2's z-vector) is a
+// shared-memory bitmap over the z ids of a z tile: the paper's monotone
+// "SPA[z] = x" tag avoids re-initialising a |Z|-long array per x; a bitmap of
+// |Z|/8 bytes in shared memory is cheap to clear instead.
+//   * Narrow S_sparse rows: a warp walks the row and sets bits (atomicOr).
+//   * Wide S_sparse rows (held as z-bitmaps): the row is OR-ed in word by word,
+//     |Z|/32 words instead of deg_S(y) bit updates.
+//   * DenseEC's result bits (over the dense z index) are OR-ed in; the dense
+//     and sparse z sets are disjoint (Section 2.3), so no dedup is needed.
+// Because ids are ranks, scanning the bitmap in word order yields z ascending,
+// and x ids processed in order yield the canonical (x, z) order. A counting
+// pass gives per-x sizes, a scan gives offsets, an emitting pass rebuilds the
+// bitmap and writes the pairs through a shared-memory staging buffer with
+// 16-byte stores.
+//
+// Join-Count (Section 4.1): the SPA holds a 32-bit counter per z of the tile
+// instead of a bit, every S_sparse row is walked as a list, and DenseEC's
+// counts are added in.
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace dimcube {
+
+constexpr int kStage = 8192;            // staged output values per chunk
+constexpr int kChunkWords = kThreads;   // bitmap words compacted per chunk
+constexpr int64_t kMaxTileWords = 24 * 1024;   // 96 KiB bitmap tile = 786,432 z
+constexpr int kCntChunk = 4096;         // z per compaction chunk (count mode)
+constexpr int64_t kMaxCntTile = 16 * 1024;     // counters per tile (64 KiB)
+
+struct XRowArgs {
+    int64_t x_begin, n_rows;
+    int64_t n_z, zw, tile_bits;
+    const int64_t* r_rowptr;
+    const int32_t* r_col;
+    const int64_t* ss_rowptr;
+    const int32_t* ss_col;
+    const int32_t* bm_row_of_y;
+    const uint32_t* ss_bits;
+    const uint32_t* d_bits;  // [n_rows][zdw] or null
+    const int32_t* d_cnt;    // [n_rows][n_zd] or null
+    int64_t zdw, n_zd;
+    const int32_t* zd_list;
+    const int32_t* dict_x;
+    const int32_t* dict_z;
+    int64_t* cnt;            // counting pass out
+    const int64_t* off;      // emitting pass: [n_rows + 1]
+    int32_t* out_x;
+    int32_t* out_z;
+    int32_t* out_c;
+    int vec_ok;
+};
+
+// Fill out[o0, o1) with v using 16-byte stores where aligned.
+__device__ __forceinline__ void fill_range(int32_t* out, int64_t o0, int64_t o1, int32_t v, bool vec_ok) {
+    if (!vec_ok) {
+        for (int64_t i = o0 + threadIdx.x; i < o1; i += blockDim.x) out[i] = v;
+        return;
+    }
+    int64_t a = min64(o1, (o0 + 3) & ~int64_t(3));
+    int64_t b = max64(a, o1 & ~int64_t(3));
+    for (int64_t i = o0 + threadIdx.x; i < a; i += blockDim.x) out[i] = v;
+    const int4 v4 = make_int4(v, v, v, v);
+    for (int64_t i = a + 4 * (int64_t)threadIdx.x; i < b; i += 4 * (int64_t)blockDim.x)
+        *reinterpret_cast<int4*>(out + i) = v4;
+    for (int64_t i = b + threadIdx.x; i < o1; i += blockDim.x) out[i] = v;
+}
+
+// Copy stage[sh, sh + cnt) to dst[sh, sh + cnt) where dst + 0 is 16-byte
+// aligned when vec_ok (the caller offsets dst by the global misalignment).
+__device__ __forceinline__ void flush_stage(int32_t* dst, const int32_t* stage, int sh, int cnt, bool vec_ok) {
+    const int end = sh + cnt;
+    const int nv = (end + 3) >> 2;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        const int s = v << 2;
+        if (vec_ok && s >= sh && s + 4 <= end) {
+            *reinterpret_cast<int4*>(dst + s) = *reinterpret_cast<const int4*>(stage + s);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int t = s + j;
+                if (t >= sh && t < end) dst[t] = stage[t];
+            }
+        }
+    }
+}
+
+template <bool kEmit>
+__global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);  // kStage + 8
+    uint32_t* bm = smem + kStage + 8;                   // tile words
+    __shared__ int64_t s_scan[kThreads / 32 + 1];
+    __shared__ int32_t s_list[kThreads];
+    __shared__ int32_t s_wc[kThreads / 32 + 1];
+
+    const int64_t xr = blockIdx.x;
+    if (xr >= a.n_rows) return;
+    const int64_t x = a.x_begin + xr;
+    const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool tiled = a.tile_bits < a.n_z;
+    int64_t total = 0;
+    int64_t out_pos = 0;
+    if (kEmit) {
+        out_pos = a.off[xr];
+        fill_range(a.out_x, out_pos, a.off[xr + 1], a.dict_x[x], a.vec_ok);
+    }
+    for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += a.tile_bits) {
+        const int64_t zt1 = min64(zt0 + a.tile_bits, a.n_z);
+        const int tw = (int)((zt1 - zt0 + 31) >> 5);
+        for (int w = tid; w < tw; w += kThreads) bm[w] = 0u;
+        __syncthreads();
+        // narrow S_sparse rows: one warp per y of R[x]
+        for (int64_t p = r0 + warp; p < r1; p += kThreads / 32) {
+            const int32_t y = a.r_col[p];
+            if (a.bm_row_of_y[y] >= 0) continue;
+            int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+            if (tiled) {
+                s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
+                s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
+            }
+            for (int64_t q = s0 + lane; q < s1; q += 32) {
+                const int32_t z = a.ss_col[q] - (int32_t)zt0;
+                atomicOr(&bm[z >> 5], 1u << (z & 31));
+            }
+        }
+        // wide S_sparse rows: gather up to kThreads bitmap rows, OR them word-wise
+        for (int64_t base = r0; base < r1; base += kThreads) {
+            const int64_t p = base + tid;
+            const int32_t b = p < r1 ? a.bm_row_of_y[a.r_col[p]] : -1;
+            const unsigned bal = __ballot_sync(kFull, b >= 0);
+            if (lane == 0) s_wc[warp] = __popc(bal);
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int w = 0; w < kThreads / 32; ++w) {
+                    const int c = s_wc[w];
+                    s_wc[w] = run;
+                    run += c;
+                }
+                s_wc[kThreads / 32] = run;
+            }
+            __syncthreads();
+            if (b >= 0) s_list[s_wc[warp] + __popc(bal & lanemask_lt())] = b;
+            __syncthreads();
+            const int nl = s_wc[kThreads / 32];
+            if (nl > 0) {
+                const uint32_t* bits = a.ss_bits + (zt0 >> 5);
+                for (int w = tid; w < tw; w += kThreads) {
+                    uint32_t acc = 0u;
+                    for (int i = 0; i < nl; ++i) acc |= __ldg(bits + (int64_t)s_list[i] * a.zw + w);
+                    if (acc) bm[w] |= acc;
+                }
+            }
+            __syncthreads();
+        }
+        // DenseEC result of this x (disjoint from the sparse z set)
+        if (a.n_zd > 0) {
+            const uint32_t* drow = a.d_bits + xr * a.zdw;
+            for (int64_t w = tid; w < a.zdw; w += kThreads) {
+                uint32_t word = drow[w];
+                while (word) {
+                    const int b = __ffs(word) - 1;
+                    word &= word - 1;
+                    int32_t z = a.zd_list[w * 32 + b];
+                    if (z >= zt0 && z < zt1) {
+                        z -= (int32_t)zt0;
+                        atomicOr(&bm[z >> 5], 1u << (z & 31));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (!kEmit) {
+            int64_t c = 0;
+            for (int w = tid; w < tw; w += kThreads) c += __popc(bm[w]);
+            total += block_sum<int64_t, kThreads>(c, s_scan);
+        } else {
+            for (int cw = 0; cw < tw; cw += kChunkWords) {
+                const int w = cw + tid;
+                uint32_t word = w < tw ? bm[w] : 0u;
+                int64_t ctot;
+                const int64_t ex = block_exclusive_scan<int64_t, kThreads>(__popc(word), &ctot, s_scan);
+                const int sh = (int)(out_pos & 3);
+                int pos = sh + (int)ex;
+                const int32_t zb = (int32_t)zt0 + (w << 5);
+                while (word) {
+                    const int b = __ffs(word) - 1;
+                    word &= word - 1;
+                    stage[pos++] = a.dict_z[zb + b];
+                }
+                __syncthreads();
+                flush_stage(a.out_z + (out_pos - sh), stage, sh, (int)ctot, a.vec_ok);
+                out_pos += ctot;
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+    if (!kEmit && tid == 0) a.cnt[xr] = total;
+}
+
+// Join-Count: counters per z of a tile.
+template <bool kEmit>
+__global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    int32_t* stage_z = reinterpret_cast<int32_t*>(smem);          // kCntChunk + 8
+    int32_t* stage_c = stage_z + (kCntChunk + 8);                  // kCntChunk + 8
+    uint32_t* ctr = reinterpret_cast<uint32_t*>(stage_c + (kCntChunk + 8));  // tile counters
+    __shared__ int64_t s_scan[kThreads / 32 + 1];
+
+    const int64_t xr = blockIdx.x;
+    if (xr >= a.n_rows) return;
+    const int64_t x = a.x_begin + xr;
+    const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool tiled = a.tile_bits < a.n_z;
+    int64_t total = 0;
+    int64_t out_pos = 0;
+    if (kEmit) {
+        out_pos = a.off[xr];
+        fill_range(a.out_x, out_pos, a.off[xr + 1], a.dict_x[x], a.vec_ok);
+    }
+    for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += a.tile_bits) {
+        const int64_t zt1 = min64(zt0 + a.tile_bits, a.n_z);
+        const int tn = (int)(zt1 - zt0);
+        for (int i = tid; i < tn; i += kThreads) ctr[i] = 0u;
+        __syncthreads();
+        for (int64_t p = r0 + warp; p < r1; p += kThreads / 32) {
+            const int32_t y = a.r_col[p];
+            int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+            if (tiled) {
+                s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
+                s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
+            }
+            for (int64_t q = s0 + lane; q < s1; q += 32) atomicAdd(&ctr[a.ss_col[q] - (int32_t)zt0], 1u);
+        }
+        if (a.n_zd > 0) {
+            const int32_t* crow = a.d_cnt + xr * a.n_zd;
+            for (int64_t d = tid; d < a.n_zd; d += kThreads) {
+                const int32_t c = crow[d];
+                const int32_t z = a.zd_list[d];
+                if (c > 0 && z >= zt0 && z < zt1) atomicAdd(&ctr[z - (int32_t)zt0], (uint32_t)c);
+            }
+        }
+        __syncthreads();
+        if (!kEmit) {
+            int64_t c = 0;
+            for (int i = tid; i < tn; i += kThreads) c += ctr[i] != 0u;
+            total += block_sum<int64_t, kThreads>(c, s_scan);
+        } else {
+            constexpr int kPer = kCntChunk / kThreads;  // z per thread per chunk
+            for (int c0 = 0; c0 < tn; c0 += kCntChunk) {
+                const int i0 = c0 + tid * kPer;
+                int n = 0;
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) n += (i0 + j < tn && ctr[i0 + j] != 0u);
+                int64_t ctot;
+                const int64_t ex = block_exclusive_scan<int64_t, kThreads>(n, &ctot, s_scan);
+                const int sh = (int)(out_pos & 3);
+                int pos = sh + (int)ex;
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) {
+                    const int i = i0 + j;
+                    if (i < tn) {
+                        const uint32_t v = ctr[i];
+                        if (v) {
+                            stage_z[pos] = a.dict_z[zt0 + i];
+                            stage_c[pos] = (int32_t)v;
+                            ++pos;
+                        }
+                    }
+                }
+                __syncthreads();
+                flush_stage(a.out_z + (out_pos - sh), stage_z, sh, (int)ctot, a.vec_ok);
+                flush_stage(a.out_c + (out_pos - sh), stage_c, sh, (int)ctot, a.vec_ok);
+                out_pos += ctot;
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+    if (!kEmit && tid == 0) a.cnt[xr] = total;
+}
+
+// ----------------------------------------------------------------- host side
+static size_t bits_smem(int64_t tile_bits) { return (size_t)(kStage + 8) * 4 + (size_t)(tile_bits / 32) * 4; }
+static size_t cnt_smem(int64_t tile_bits) { return (size_t)(kCntChunk + 8) * 8 + (size_t)tile_bits * 4; }
+
+static void setup_attrs(const Ctx& ctx) {
+    static bool done[64] = {false};
+    const int d = ctx.device & 63;
+    if (done[d]) return;
+    const int lim = ctx.smem_optin;
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    done[d] = true;
+}
+
+static XRowArgs make_args(const Plan& p, int64_t x_begin, int64_t rows, int kind) {
+    XRowArgs a{};
+    a.x_begin = x_begin;
+    a.n_rows = rows;
+    a.n_z = p.info.n_z;
+    a.zw = p.zw;
+    if (kind == 0) {
+        const int64_t tw = std::min<int64_t>(p.zw, kMaxTileWords);
+        a.tile_bits = tw * 32;
+    } else {
+        a.tile_bits = std::min<int64_t>(std::max<int64_t>(p.info.n_z, 1), kMaxCntTile);
+    }
+    a.r_rowptr = p.r_rowptr.as<int64_t>();
+    a.r_col = p.r_col.as<int32_t>();
+    a.ss_rowptr = p.ss_rowptr.as<int64_t>();
+    a.ss_col = p.ss_col.as<int32_t>();
+    a.bm_row_of_y = p.bm_row_of_y.as<int32_t>();
+    a.ss_bits = p.ss_bits.as<uint32_t>();
+    a.zdw = p.zdw;
+    a.n_zd = p.info.n_z_dense;
+    a.zd_list = p.zd_list.as<int32_t>();
+    a.dict_x = p.dict_x.as<int32_t>();
+    a.dict_z = p.dict_z.as<int32_t>();
+    return a;
+}
+
+static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, cudaStream_t s) {
+    if (a.n_rows <= 0 || a.n_z <= 0) return;
+    setup_attrs(ctx);
+    DIM3_REQUIRE(a.n_rows < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long");
+    const unsigned g = (unsigned)a.n_rows;
+    PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
+    if (kind == 0) {
+        const size_t sm = bits_smem(a.tile_bits);
+        if (emit) k_xrow_bits<true><<<g, kThreads, sm, s>>>(a);
+        else k_xrow_bits<false><<<g, kThreads, sm, s>>>(a);
+    } else {
+        const size_t sm = cnt_smem(a.tile_bits);
+        if (emit) k_xrow_counts<true><<<g, kThreads, sm, s>>>(a);
+        else k_xrow_counts<false><<<g, kThreads, sm, s>>>(a);
+    }
+    DIM3_LAUNCHED();
+}
+
+// Dense results and per-row counts of a range, cached on the plan so that a
+// count query followed by the emitting call does the counting pass once.
+static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int kind, cudaStream_t s) {
+    if (p.cache_begin == x_begin && p.cache_end == x_end && p.cache_kind == kind) return;
+    p.cache_begin = p.cache_end = -1;
+    p.cache_kind = -1;
+    const int64_t rows = x_end - x_begin;
+    p.cache_dbits.release();
+    p.cache_dcnt.release();
+    if (p.info.n_z_dense > 0 && rows > 0) {
+        if (kind == 0) {
+            p.cache_dbits.alloc((size_t)(rows * p.zdw) * 4, s);
+            dense_ec(ctx, p, x_begin, rows, 0, p.cache_dbits.as<uint32_t>(), nullptr, s);
+        } else {
+            p.cache_dcnt.alloc((size_t)(rows * p.info.n_z_dense) * 4, s);
+            dense_ec(ctx, p, x_begin, rows, 1, nullptr, p.cache_dcnt.as<int32_t>(), s);
+        }
+    }
+    DevBuf cnt;
+    cnt.alloc((size_t)std::max<int64_t>(rows, 1) * 8, s);
+    p.cache_off.alloc((size_t)(rows + 1) * 8, s);
+    if (rows > 0) {
+        if (p.info.n_z <= 0 || p.info.n_r_kept == 0) {
+            DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
+        } else {
+            XRowArgs a = make_args(p, x_begin, rows, kind);
+            a.d_bits = p.cache_dbits.as<uint32_t>();
+            a.d_cnt = p.cache_dcnt.as<int32_t>();
+            a.cnt = cnt.as<int64_t>();
+            launch_rows(ctx, a, kind, false, s);
+        }
+    }
+    exclusive_scan_i64(cnt.as<int64_t>(), p.cache_off.as<int64_t>(), rows, s);
+    p.cache_begin = x_begin;
+    p.cache_end = x_end;
+    p.cache_kind = kind;
+}
+
+static void check_range(const Plan& p, int64_t x_begin, int64_t x_end) {
+    DIM3_REQUIRE(x_begin >= 0 && x_end >= x_begin && x_end <= p.info.n_x, DIM3_ERR_ARG,
+                 "x range outside [0, n_x]");
+}
+
+__global__ void k_diff_i64(const int64_t* off, int64_t n, int64_t* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = off[i + 1] - off[i];
+}
+
+void plan_row_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int64_t* d_counts, cudaStream_t s) {
+    check_range(p, x_begin, x_end);
+    ensure_counts(ctx, p, x_begin, x_end, 0, s);
+    const int64_t rows = x_end - x_begin;
+    if (rows > 0) {
+        const unsigned g = (unsigned)std::min<int64_t>(ceil_div(rows, kThreads), 4096);
+        k_diff_i64<<<g, kThreads, 0, s>>>(p.cache_off.as<int64_t>(), rows, d_counts);
+        DIM3_LAUNCHED();
+    }
+}
+
+int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int kind, int32_t* out_x, int32_t* out_z,
+                  int32_t* out_cnt, int64_t capacity, int64_t* count, cudaStream_t s) {
+    check_range(p, x_begin, x_end);
+    ensure_counts(ctx, p, x_begin, x_end, kind, s);
+    const int64_t rows = x_end - x_begin;
+    const int64_t total = read_i64(p.cache_off.as<int64_t>() + rows, s);
+    if (count) *count = total;
+    if (total > capacity) throw Error(DIM3_ERR_CAPACITY, "output capacity " + std::to_string(capacity) +
+                                                             " < result size " + std::to_string(total));
+    if (total > 0) {
+        DIM3_REQUIRE(out_x && out_z && (kind == 0 || out_cnt), DIM3_ERR_ARG, "null output buffer");
+        XRowArgs a = make_args(p, x_begin, rows, kind);
+        a.d_bits = p.cache_dbits.as<uint32_t>();
+        a.d_cnt = p.cache_dcnt.as<int32_t>();
+        a.off = p.cache_off.as<int64_t>();
+        a.out_x = out_x;
+        a.out_z = out_z;
+        a.out_c = out_cnt;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z) |
+                             (kind ? reinterpret_cast<uintptr_t>(out_cnt) : 0);
+        a.vec_ok = (al & 15u) == 0;
+        launch_rows(ctx, a, kind, true, s);
+    }
+    DIM3_CUDA(cudaStreamSynchronize(s));
+    return total;
+}
+
+}  // namespace dimcube

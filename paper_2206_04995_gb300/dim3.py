@@ -1,0 +1,321 @@
+"""Thin Python binding of the C ABI in ``include/dim3.h`` (ctypes).
+
+Argument marshalling only: torch supplies device memory and streams; every
+step of the Join-Project path runs in the CUDA kernels of ``libdim3.so``.
+There is no CPU fallback: without the library (or a GB300) calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+DIM3_OK = 0
+DIM3_ERR_ARG = -1
+DIM3_ERR_CUDA = -2
+DIM3_ERR_NOMEM = -3
+DIM3_ERR_CAPACITY = -4
+DIM3_ERR_TIMEOUT = -5
+DIM3_ERR_OVERFLOW = -6
+DIM3_ERR_UNSUPPORTED = -7
+
+DENSE_AUTO, DENSE_TC, DENSE_POPC, DENSE_PROBE = 0, 1, 2, 3
+OPT_THETA_Z, OPT_DENSE_VARIANT, OPT_BITMAP_ROW_MIN, OPT_LIGHT_ROW_MAX, OPT_TIMING = 1, 2, 3, 4, 5
+PHASES = {"map": 0, "partition": 1, "dense_ec": 2, "sparse_count": 3, "sparse_emit": 4}
+
+TABLES = {
+    "dict_x": (1, torch.int32), "dict_y": (2, torch.int32), "dict_z": (3, torch.int32),
+    "r_rowptr": (4, torch.int64), "r_col": (5, torch.int32), "m_z": (6, torch.int32),
+    "dense_z": (7, torch.uint8), "ss_rowptr": (8, torch.int64), "ss_col": (9, torch.int32),
+    "deg_s": (10, torch.int32), "outj_x": (11, torch.int64),
+}
+
+
+class Dim3Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dim3 error {status}: {msg}")
+        self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "n_r", "n_s", "n_r_kept", "n_s_distinct", "n_x", "n_y", "n_z", "n_z_dense", "n_y_dense",
+        "n_s_sparse", "n_y_bitmap", "out_j")] + [("theta_z", ctypes.c_int32), ("dense_variant", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libdim3.so (building it in-tree first if it is missing or stale
+    and nvcc is available). Raises if the library cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            try:
+                _build.build()
+            except Exception as e:  # noqa: BLE001
+                if not os.path.exists(_build.LIB):
+                    raise RuntimeError(f"libdim3.so is missing and could not be built: {e}") from e
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libdim3.so is missing; run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        P, I64, I32, INT = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        sig = {
+            "dim3_version": ([], INT),
+            "dim3_last_error": ([], ctypes.c_char_p),
+            "dim3_ctx_create": ([ctypes.POINTER(P), INT], INT),
+            "dim3_ctx_destroy": ([P], INT),
+            "dim3_ctx_set_option": ([P, INT, I64], INT),
+            "dim3_ctx_timing": ([P, INT, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), INT], INT),
+            "dim3_launch_count": ([ctypes.POINTER(I64)], INT),
+            "dim3_map": ([P, P, I64, P, P, ctypes.POINTER(I64), P], INT),
+            "dim3_partition": ([P, P, P, I64, P, P, I64, I32, ctypes.POINTER(P), ctypes.POINTER(PlanInfo), P], INT),
+            "dim3_plan_get_info": ([P, ctypes.POINTER(PlanInfo)], INT),
+            "dim3_plan_row_counts": ([P, P, I64, I64, P, P], INT),
+            "dim3_plan_join_project": ([P, P, I64, I64, P, P, I64, ctypes.POINTER(I64), P], INT),
+            "dim3_plan_join_count": ([P, P, I64, I64, P, P, P, I64, ctypes.POINTER(I64), P], INT),
+            "dim3_plan_export": ([P, INT, P, I64, P], INT),
+            "dim3_plan_destroy": ([P], INT),
+            "dim3_join_project": ([P, P, P, I64, P, P, I64, P, P, I64, ctypes.POINTER(I64), P], INT),
+            "dim3_join_count": ([P, P, P, I64, P, P, I64, P, P, P, I64, ctypes.POINTER(I64), P], INT),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return _lib
+
+
+def launch_count() -> int:
+    """Kernels launched by libdim3.so in this process."""
+    n = ctypes.c_int64()
+    _check(load().dim3_launch_count(ctypes.byref(n)))
+    return n.value
+
+
+def _check(rc: int):
+    if rc != DIM3_OK:
+        raise Dim3Error(rc, load().dim3_last_error().decode(errors="replace"))
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None or t.numel() == 0 else ctypes.c_void_p(t.data_ptr())
+
+
+def _col(t: torch.Tensor, device: torch.device, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != torch.int32 or t.device != device or t.dim() != 1 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous 1-D int32 tensor on {device}")
+    return t
+
+
+def _stream(device, stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """A library context on one CUDA device (``dim3_ctx``)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        self.device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        _check(self._lib.dim3_ctx_create(ctypes.byref(h), device))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dim3_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def set_option(self, option: int, value: int):
+        _check(self._lib.dim3_ctx_set_option(self._h, option, int(value)))
+
+    def timing(self, reset: bool = False) -> dict:
+        """{phase: (total_ms, intervals)} recorded while OPT_TIMING is on."""
+        out = {}
+        for name, ph in PHASES.items():
+            ms = ctypes.c_double()
+            n = ctypes.c_int64()
+            _check(self._lib.dim3_ctx_timing(self._h, ph, ctypes.byref(ms), ctypes.byref(n), 0))
+            out[name] = (ms.value, n.value)
+        if reset:
+            _check(self._lib.dim3_ctx_timing(self._h, 0, None, None, 1))
+        return out
+
+    # -------------------------------------------------------------- mapping
+    def map(self, vals: torch.Tensor, stream=None):
+        """Order-preserving ids of a column: (ids, dict)."""
+        vals = _col(vals, self.device, "vals")
+        n = vals.numel()
+        ids = torch.empty(n, dtype=torch.int32, device=self.device)
+        d = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        nd = ctypes.c_int64()
+        _check(self._lib.dim3_map(self._h, _ptr(vals), n, _ptr(ids), _ptr(d), ctypes.byref(nd),
+                                  _stream(self.device, stream)))
+        return ids, d[: nd.value]
+
+    # ------------------------------------------------------------ partition
+    def partition(self, r_key, r_val, s_key, s_val, theta_z: int = -1, stream=None) -> "Plan":
+        r_key, r_val = _col(r_key, self.device, "r_key"), _col(r_val, self.device, "r_val")
+        s_key, s_val = _col(s_key, self.device, "s_key"), _col(s_val, self.device, "s_val")
+        if r_key.numel() != r_val.numel() or s_key.numel() != s_val.numel():
+            raise ValueError("column lengths differ")
+        h = ctypes.c_void_p()
+        info = PlanInfo()
+        _check(self._lib.dim3_partition(self._h, _ptr(r_key), _ptr(r_val), r_key.numel(), _ptr(s_key), _ptr(s_val),
+                                        s_key.numel(), int(theta_z), ctypes.byref(h), ctypes.byref(info),
+                                        _stream(self.device, stream)))
+        return Plan(self, h, info, stream)
+
+    # -------------------------------------------------------- one-call path
+    def join_project(self, r_key, r_val, s_key, s_val, out_x=None, out_z=None, stream=None):
+        """Pi_{x,z}(R join_y S): (out_x, out_z) in canonical order. With
+        preallocated outputs the single C call ``dim3_join_project`` runs;
+        otherwise a plan sizes the result first."""
+        if out_x is not None:
+            return self._join_call(False, r_key, r_val, s_key, s_val, out_x, out_z, None, stream)
+        plan = self.partition(r_key, r_val, s_key, s_val, stream=stream)
+        try:
+            return plan.join_project(stream=stream)
+        finally:
+            plan.close()
+
+    def join_count(self, r_key, r_val, s_key, s_val, out_x=None, out_z=None, out_c=None, stream=None):
+        """Join-Aggregate COUNT: (out_x, out_z, out_cnt)."""
+        if out_x is not None:
+            return self._join_call(True, r_key, r_val, s_key, s_val, out_x, out_z, out_c, stream)
+        plan = self.partition(r_key, r_val, s_key, s_val, stream=stream)
+        try:
+            return plan.join_count(stream=stream)
+        finally:
+            plan.close()
+
+    def _join_call(self, counts, r_key, r_val, s_key, s_val, out_x, out_z, out_c, stream):
+        r_key, r_val = _col(r_key, self.device, "r_key"), _col(r_val, self.device, "r_val")
+        s_key, s_val = _col(s_key, self.device, "s_key"), _col(s_val, self.device, "s_val")
+        cap = min(out_x.numel(), out_z.numel(), out_c.numel() if counts else out_x.numel())
+        cnt = ctypes.c_int64()
+        st = _stream(self.device, stream)
+        if counts:
+            rc = self._lib.dim3_join_count(self._h, _ptr(r_key), _ptr(r_val), r_key.numel(), _ptr(s_key),
+                                           _ptr(s_val), s_key.numel(), _ptr(out_x), _ptr(out_z), _ptr(out_c), cap,
+                                           ctypes.byref(cnt), st)
+        else:
+            rc = self._lib.dim3_join_project(self._h, _ptr(r_key), _ptr(r_val), r_key.numel(), _ptr(s_key),
+                                             _ptr(s_val), s_key.numel(), _ptr(out_x), _ptr(out_z), cap,
+                                             ctypes.byref(cnt), st)
+        if rc == DIM3_ERR_CAPACITY:
+            raise Dim3Error(rc, f"capacity {cap} < result {cnt.value}")
+        _check(rc)
+        n = cnt.value
+        if counts:
+            return out_x[:n], out_z[:n], out_c[:n]
+        return out_x[:n], out_z[:n]
+
+
+class Plan:
+    """A partitioned input resident on the device (``dim3_plan``)."""
+
+    def __init__(self, ctx: Context, handle, info: PlanInfo, stream=None):
+        self.ctx = ctx
+        self._h = handle
+        self._info = info
+        self.stream = stream
+
+    @property
+    def info(self) -> dict:
+        return self._info.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.ctx._lib.dim3_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def export(self, name: str, stream=None) -> torch.Tensor:
+        which, dtype = TABLES[name]
+        i = self._info
+        n = {"dict_x": i.n_x, "dict_y": i.n_y, "dict_z": i.n_z, "r_rowptr": i.n_x + 1, "r_col": i.n_r_kept,
+             "m_z": i.n_z, "dense_z": i.n_z, "ss_rowptr": i.n_y + 1, "ss_col": i.n_s_sparse, "deg_s": i.n_y,
+             "outj_x": i.n_x}[name]
+        out = torch.empty(n, dtype=dtype, device=self.ctx.device)
+        _check(self.ctx._lib.dim3_plan_export(self._h, which, _ptr(out), out.numel() * out.element_size(),
+                                              _stream(self.ctx.device, stream or self.stream)))
+        return out
+
+    def row_counts(self, x_begin: int = 0, x_end: int | None = None, stream=None) -> torch.Tensor:
+        x_end = self._info.n_x if x_end is None else x_end
+        out = torch.empty(max(x_end - x_begin, 0), dtype=torch.int64, device=self.ctx.device)
+        _check(self.ctx._lib.dim3_plan_row_counts(self.ctx._h, self._h, x_begin, x_end, _ptr(out),
+                                                  _stream(self.ctx.device, stream or self.stream)))
+        return out
+
+    def _run(self, counts, x_begin, x_end, out_x, out_z, out_c, stream):
+        x_end = self._info.n_x if x_end is None else x_end
+        L = self.ctx._lib
+        st = _stream(self.ctx.device, stream or self.stream)
+        cnt = ctypes.c_int64()
+        if out_x is None:
+            # size query (capacity 0), then allocate and emit; the plan keeps
+            # the counting pass of this range, so it is not repeated
+            if counts:
+                rc = L.dim3_plan_join_count(self.ctx._h, self._h, x_begin, x_end, None, None, None, 0,
+                                            ctypes.byref(cnt), st)
+            else:
+                rc = L.dim3_plan_join_project(self.ctx._h, self._h, x_begin, x_end, None, None, 0,
+                                              ctypes.byref(cnt), st)
+            if rc not in (DIM3_OK, DIM3_ERR_CAPACITY):
+                _check(rc)
+            n = cnt.value
+            dev = self.ctx.device
+            out_x = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+            out_z = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+            out_c = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if counts else None
+        cap = min(out_x.numel(), out_z.numel(), out_c.numel() if counts else out_x.numel())
+        if counts:
+            rc = L.dim3_plan_join_count(self.ctx._h, self._h, x_begin, x_end, _ptr(out_x), _ptr(out_z), _ptr(out_c),
+                                        cap, ctypes.byref(cnt), st)
+        else:
+            rc = L.dim3_plan_join_project(self.ctx._h, self._h, x_begin, x_end, _ptr(out_x), _ptr(out_z), cap,
+                                          ctypes.byref(cnt), st)
+        _check(rc)
+        n = cnt.value
+        return (out_x[:n], out_z[:n], out_c[:n]) if counts else (out_x[:n], out_z[:n])
+
+    def join_project(self, x_begin: int = 0, x_end: int | None = None, out_x=None, out_z=None, stream=None):
+        return self._run(False, x_begin, x_end, out_x, out_z, None, stream)
+
+    def join_count(self, x_begin: int = 0, x_end: int | None = None, out_x=None, out_z=None, out_c=None,
+                   stream=None):
+        return self._run(True, x_begin, x_end, out_x, out_z, out_c, stream)
