@@ -37,6 +37,7 @@ constexpr uint32_t kStageBytes = kStageBytesA + kStageBytesB;
 constexpr uint32_t kTmemCols = kTcTileN;  // one FP32 column per output column
 constexpr uint32_t kTcSmem = kStages * kStageBytes + 1024 + 256;
 constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 
 // Instruction descriptor of tcgen05.mma.kind::f8f6f4: D = F32 (bits 4-5 = 1),
 // A = B = E4M3 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0),
@@ -69,10 +70,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on the phase with the given parity; false if it gave up.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on the phase with the given parity: gives up (returns false)
+// after kWaitNs nanoseconds of wall time or kWaitLimit polls, whichever first.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 

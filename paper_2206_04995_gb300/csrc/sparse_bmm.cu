@@ -293,14 +293,16 @@ static size_t bits_smem(int64_t tile_bits) { return (size_t)(kStage + 8) * 4 + (
 static size_t cnt_smem(int64_t tile_bits) { return (size_t)(kCntChunk + 8) * 8 + (size_t)tile_bits * 4; }
 
 static void setup_attrs(const Ctx& ctx) {
+    // the largest dynamic shared memory any launch of these kernels asks for
     static bool done[64] = {false};
     const int d = ctx.device & 63;
     if (done[d]) return;
-    const int lim = ctx.smem_optin;
-    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    const int bits_max = (int)bits_smem(kMaxTileWords * 32);
+    const int cnt_max = (int)cnt_smem(kMaxCntTile);
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
     done[d] = true;
 }
 

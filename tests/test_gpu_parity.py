@@ -21,7 +21,7 @@ def ctx():
     c.close()
 
 
-def fresh_ctx(**opts):
+def fresh_ctx(opts):
     c = dim3.Context(0)
     for k, v in opts.items():
         c.set_option(k, v)
@@ -117,7 +117,7 @@ def test_fig3_example(ctx):
     r_key, r_val = np.array([1, 3], np.int32), np.array([2, 2], np.int32)
     s_key, s_val = np.array([1, 3], np.int32), np.array([2, 2], np.int32)
     for theta in (0, 1 << 30):
-        c = fresh_ctx(**{dim3.OPT_THETA_Z: theta})
+        c = fresh_ctx({dim3.OPT_THETA_Z: theta})
         x, z, cnt = c.join_count(dev(r_key), dev(r_val), dev(s_key), dev(s_val))
         assert host(x).tolist() == [2] and host(z).tolist() == [2] and host(cnt).tolist() == [2]
         c.close()
@@ -167,7 +167,7 @@ def test_chung_lu_small(ctx):
 def test_dense_variants_and_threshold(variant, theta):
     """Section 2.3 and 2.6: the result does not depend on the dense/sparse
     threshold or on the bitmap-intersection method."""
-    c = fresh_ctx(**{dim3.OPT_THETA_Z: theta, dim3.OPT_DENSE_VARIANT: variant})
+    c = fresh_ctx({dim3.OPT_THETA_Z: theta, dim3.OPT_DENSE_VARIANT: variant})
     for seed in range(3):
         inst = gen.small_two_table(100 + seed, n_r=6000, n_s=5000, nx=700, ny=500, nz=600, zipf=1.0,
                                    dup_frac=0.05)
@@ -180,7 +180,7 @@ def test_dense_variants_and_threshold(variant, theta):
 @pytest.mark.parametrize("variant", [dim3.DENSE_TC, dim3.DENSE_POPC])
 def test_dense_multi_tile(variant):
     """DenseEC over several 128 x 256 tiles and many K blocks with ragged edges."""
-    c = fresh_ctx(**{dim3.OPT_THETA_Z: 0, dim3.OPT_DENSE_VARIANT: variant})
+    c = fresh_ctx({dim3.OPT_THETA_Z: 0, dim3.OPT_DENSE_VARIANT: variant})
     inst = gen.small_two_table(7, n_r=60_000, n_s=50_000, nx=1000, ny=700, nz=600, zipf=0.9)
     assert_project(c, inst)
     assert_count(c, inst)
@@ -189,7 +189,7 @@ def test_dense_multi_tile(variant):
 
 @pytest.mark.parametrize("row_min", [0, 1, 1 << 40])
 def test_bitmap_rows_invariance(row_min):
-    c = fresh_ctx(**{dim3.OPT_BITMAP_ROW_MIN: row_min})
+    c = fresh_ctx({dim3.OPT_BITMAP_ROW_MIN: row_min})
     inst = gen.config2_two_table(scale=0.01)
     assert_project(c, inst)
     c.close()
