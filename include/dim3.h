@@ -142,6 +142,25 @@ DIM3_API int dim3_map(dim3_ctx *ctx, const int32_t *d_vals, int64_t n, int32_t *
              int32_t *d_dict, int64_t *n_distinct, void *stream);
 
 /*
+ * dim3_map_noalloc -- dim3_map for callers that may not allocate device
+ * memory (a host engine that fixed its GPU memory budget at start-up and
+ * forbids later allocations, code living under another framework's allocator,
+ * or latency-critical code that must not enter the allocator). The paper has
+ * no counterpart: it is an interface variant, not a step of the method.
+ *   d_vals, d_ids, d_dict, n_distinct: as for dim3_map; n <= 65536.
+ * No context. Runs on the current device and stream. All scratch lives in one
+ * fixed 2,883,840-byte device array inside the library (held by every GPU
+ * that loads it until the process exits); nothing is allocated or freed.
+ * The first call on a device looks up that array's device address, so make it
+ * before any stream capture. Every call reuses the same array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. n > 65536 gives DIM3_ERR_OVERFLOW.
+ * Synchronises the stream.
+ */
+DIM3_API int dim3_map_noalloc(const int32_t *d_vals, int64_t n, int32_t *d_ids, int32_t *d_dict,
+                              int64_t *n_distinct, void *stream);
+
+/*
  * dim3_partition -- Algorithm 1 up to the compute steps: map y from S.y and
  * drop R tuples whose y is not in S.y (Section 2.2, Opt. 2); map x and z;
  * build R_CSR by x (Section 2.5); split S by z into S_sparse (CSR by y) and

@@ -189,6 +189,11 @@ int dim3_map(dim3_ctx* ctx, const int32_t* d_vals, int64_t n, int32_t* d_ids, in
     });
 }
 
+int dim3_map_noalloc(const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,
+                     void* stream) {
+    return guarded([&] { dimcube::map_noalloc(d_vals, n, d_ids, d_dict, n_distinct, as_stream(stream)); });
+}
+
 int dim3_ctx_timing(dim3_ctx* ctx, int phase, double* total_ms, int64_t* launches, int reset) {
     return guarded([&] {
         DIM3_REQUIRE(ctx, DIM3_ERR_ARG, "ctx is null");

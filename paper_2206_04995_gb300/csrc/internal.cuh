@@ -120,4 +120,8 @@ void dense_ec(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int 
 void dense_build_operands(const Ctx& ctx, Plan& p, const uint64_t* s_keys_u64, const uint32_t* s_keys_u32,
                           int64_t n_s, int bz, const int32_t* zd_index, cudaStream_t s);
 
+// Value mapping with all scratch in a fixed device array (noalloc.cu).
+void map_noalloc(const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,
+                 cudaStream_t s);
+
 }  // namespace dimcube
