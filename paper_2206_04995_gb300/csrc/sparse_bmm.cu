@@ -26,8 +26,8 @@
 
 namespace dimcube {
 
-constexpr int kStage = 8192;            // staged output values per chunk
-constexpr int kChunkWords = kThreads;   // bitmap words compacted per chunk
+constexpr int kWarps = kThreads / 32;
+constexpr int kWarpStage = 1040;        // staged output values per warp (1024 + alignment shift, 16-byte multiple)
 constexpr int64_t kMaxTileWords = 24 * 1024;   // 96 KiB bitmap tile = 786,432 z
 constexpr int kCntChunk = 4096;         // z per compaction chunk (count mode)
 constexpr int64_t kMaxCntTile = 16 * 1024;     // counters per tile (64 KiB)
@@ -89,11 +89,30 @@ __device__ __forceinline__ void flush_stage(int32_t* dst, const int32_t* stage, 
     }
 }
 
+// Warp-level version of flush_stage.
+__device__ __forceinline__ void flush_warp(int32_t* dst, const int32_t* st, int sh, int cnt, bool vec_ok) {
+    const int end = sh + cnt;
+    const int nv = (end + 3) >> 2;
+    const int lane = threadIdx.x & 31;
+    for (int v = lane; v < nv; v += 32) {
+        const int s = v << 2;
+        if (vec_ok && s >= sh && s + 4 <= end) {
+            *reinterpret_cast<int4*>(dst + s) = *reinterpret_cast<const int4*>(st + s);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int t = s + j;
+                if (t >= sh && t < end) dst[t] = st[t];
+            }
+        }
+    }
+}
+
 template <bool kEmit>
 __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
-    int32_t* stage = reinterpret_cast<int32_t*>(smem);  // kStage + 8
-    uint32_t* bm = smem + kStage + 8;                   // tile words
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);       // emit: kWarps x kWarpStage
+    uint32_t* bm = smem + (kEmit ? kWarps * kWarpStage : 0);  // tile words
     __shared__ int64_t s_scan[kThreads / 32 + 1];
     __shared__ int32_t s_list[kThreads];
     __shared__ int32_t s_wc[kThreads / 32 + 1];
@@ -181,24 +200,52 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
             for (int w = tid; w < tw; w += kThreads) c += __popc(bm[w]);
             total += block_sum<int64_t, kThreads>(c, s_scan);
         } else {
-            for (int cw = 0; cw < tw; cw += kChunkWords) {
-                const int w = cw + tid;
-                uint32_t word = w < tw ? bm[w] : 0u;
-                int64_t ctot;
-                const int64_t ex = block_exclusive_scan<int64_t, kThreads>(__popc(word), &ctot, s_scan);
-                const int sh = (int)(out_pos & 3);
-                int pos = sh + (int)ex;
-                const int32_t zb = (int32_t)zt0 + (w << 5);
-                while (word) {
-                    const int b = __ffs(word) - 1;
-                    word &= word - 1;
-                    stage[pos++] = a.dict_z[zb + b];
-                }
-                __syncthreads();
-                flush_stage(a.out_z + (out_pos - sh), stage, sh, (int)ctot, a.vec_ok);
-                out_pos += ctot;
-                __syncthreads();
+            // Each warp owns a run of 32-word groups (1024 z ids each). The
+            // warps' output offsets come from one popcount pass; after that
+            // every warp compacts and writes its run without block barriers.
+            const int groups = (tw + 31) >> 5;
+            const int gpw = (groups + kWarps - 1) / kWarps;
+            const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
+            int mine = 0;
+            for (int g = g0; g < g1; ++g) {
+                const int w = (g << 5) + lane;
+                mine += w < tw ? __popc(bm[w]) : 0;
             }
+            mine = warp_sum(mine);
+            if (lane == 0) s_wc[warp] = mine;
+            __syncthreads();
+            int64_t wpos = out_pos, tile_total = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                const int c = s_wc[w];
+                if (w < warp) wpos += c;
+                tile_total += c;
+            }
+            int32_t* st = stage + warp * kWarpStage;
+            const unsigned lt = lanemask_lt();
+            for (int g = g0; g < g1; ++g) {
+                const int w = (g << 5) + lane;
+                const uint32_t word = w < tw ? bm[w] : 0u;
+                const int c = __popc(word);
+                const int incl = warp_inclusive_scan(c);
+                const int total_g = __shfl_sync(kFull, incl, 31);
+                if (total_g == 0) continue;
+                const int excl = incl - c;
+                const int sh = (int)(wpos & 3);
+                // dictionary slice of this group: lane l reads entry 32 j + l
+                // while word j is broadcast, so every load is one 128-byte line
+                const int32_t* dz = a.dict_z + zt0 + ((int64_t)g << 10);
+#pragma unroll 4
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t wj = __shfl_sync(kFull, word, j);
+                    const int pj = __shfl_sync(kFull, excl, j);
+                    if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = __ldg(dz + (j << 5) + lane);
+                }
+                __syncwarp();
+                flush_warp(a.out_z + (wpos - sh), st, sh, total_g, a.vec_ok);
+                __syncwarp();
+                wpos += total_g;
+            }
+            out_pos += tile_total;
         }
         __syncthreads();
     }
@@ -289,7 +336,9 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
 }
 
 // ----------------------------------------------------------------- host side
-static size_t bits_smem(int64_t tile_bits) { return (size_t)(kStage + 8) * 4 + (size_t)(tile_bits / 32) * 4; }
+static size_t bits_smem(int64_t tile_bits, bool emit) {
+    return (emit ? (size_t)kWarps * kWarpStage * 4 : 0) + (size_t)(tile_bits / 32) * 4;
+}
 static size_t cnt_smem(int64_t tile_bits) { return (size_t)(kCntChunk + 8) * 8 + (size_t)tile_bits * 4; }
 
 static void setup_attrs(const Ctx& ctx) {
@@ -297,7 +346,7 @@ static void setup_attrs(const Ctx& ctx) {
     static bool done[64] = {false};
     const int d = ctx.device & 63;
     if (done[d]) return;
-    const int bits_max = (int)bits_smem(kMaxTileWords * 32);
+    const int bits_max = (int)bits_smem(kMaxTileWords * 32, true);
     const int cnt_max = (int)cnt_smem(kMaxCntTile);
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
@@ -339,7 +388,7 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
     const unsigned g = (unsigned)a.n_rows;
     PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
     if (kind == 0) {
-        const size_t sm = bits_smem(a.tile_bits);
+        const size_t sm = bits_smem(a.tile_bits, emit);
         if (emit) k_xrow_bits<true><<<g, kThreads, sm, s>>>(a);
         else k_xrow_bits<false><<<g, kThreads, sm, s>>>(a);
     } else {
