@@ -40,6 +40,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=WORKLOADS, default="two_table_1m_zipf1")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload proportionally (profiling captures only; bench lines use 1.0)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -47,14 +49,14 @@ def parse_args():
     return ap.parse_args()
 
 
-def make_workload(name: str, rank: int = 0):
+def make_workload(name: str, rank: int = 0, scale: float = 1.0):
     import gen
 
     if name == "two_table_1m_zipf1":
-        return gen.config2_two_table(seed=1 + 1000 * rank)
+        return gen.config2_two_table(seed=1 + 1000 * rank, scale=scale)
     if name == "self_20k":
         return gen.config1_self(seed=0 + 1000 * rank)
-    return gen.config3_chung_lu(seed=2 + 1000 * rank)
+    return gen.config3_chung_lu(seed=2 + 1000 * rank, scale=scale)
 
 
 def measured_peaks():
@@ -167,7 +169,7 @@ def cpu_baseline(inst, target_s: float, rng_seed: int = 5):
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
-    inst = make_workload(args.workload)
+    inst = make_workload(args.workload, 0, args.scale)
     import oracle
 
     oracle.build()
@@ -217,7 +219,7 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    inst = make_workload(args.workload, rank)
+    inst = make_workload(args.workload, rank, args.scale)
     dev = torch.device("cuda", local_rank)
     cols = [torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(dev)
             for a in (inst.r_key, inst.r_val, inst.s_key, inst.s_val)]

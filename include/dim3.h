@@ -90,7 +90,8 @@ typedef enum {
     DIM3_OPT_DENSE_VARIANT = 2, /* a dim3_dense_variant (default AUTO) */
     DIM3_OPT_BITMAP_ROW_MIN = 3,/* S_sparse rows with at least this many z are held as bitmaps; <0: |Z|/32 */
     DIM3_OPT_LIGHT_ROW_MAX = 4, /* x rows with at most this many join tuples dedup in shared memory by sort; <0: default */
-    DIM3_OPT_TIMING = 5         /* nonzero: record CUDA events around each phase (dim3_ctx_timing) */
+    DIM3_OPT_TIMING = 5,        /* nonzero: record CUDA events around each phase (dim3_ctx_timing) */
+    DIM3_OPT_EMIT_ROWS = 6      /* x rows per CTA in the emitting SparseBMM pass: 1, 2, 4; 0: automatic */
 } dim3_option;
 
 /* Phases timed under DIM3_OPT_TIMING. */

@@ -30,6 +30,7 @@ struct Options {
     int64_t dense_variant = DIM3_DENSE_AUTO;
     int64_t bitmap_row_min = -1;
     int64_t light_row_max = -1;
+    int64_t emit_rows = 0;  // x rows per CTA in the emitting pass (0: automatic)
 };
 
 struct Plan {

@@ -66,7 +66,7 @@ __device__ __forceinline__ void fill_range(int32_t* out, int64_t o0, int64_t o1,
     for (int64_t i = o0 + threadIdx.x; i < a; i += blockDim.x) out[i] = v;
     const int4 v4 = make_int4(v, v, v, v);
     for (int64_t i = a + 4 * (int64_t)threadIdx.x; i < b; i += 4 * (int64_t)blockDim.x)
-        *reinterpret_cast<int4*>(out + i) = v4;
+        __stcs(reinterpret_cast<int4*>(out + i), v4);  // streaming: the output is not re-read
     for (int64_t i = b + threadIdx.x; i < o1; i += blockDim.x) out[i] = v;
 }
 
@@ -97,12 +97,12 @@ __device__ __forceinline__ void flush_warp(int32_t* dst, const int32_t* st, int 
     for (int v = lane; v < nv; v += 32) {
         const int s = v << 2;
         if (vec_ok && s >= sh && s + 4 <= end) {
-            *reinterpret_cast<int4*>(dst + s) = *reinterpret_cast<const int4*>(st + s);
+            __stcs(reinterpret_cast<int4*>(dst + s), *reinterpret_cast<const int4*>(st + s));
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int t = s + j;
-                if (t >= sh && t < end) dst[t] = st[t];
+                if (t >= sh && t < end) __stcs(dst + t, st[t]);
             }
         }
     }
@@ -252,6 +252,203 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
     if (!kEmit && tid == 0) a.cnt[xr] = total;
 }
 
+// Emitting pass for G consecutive x rows per CTA. The rows' SPA bitmaps are
+// built together (their R_CSR rows are adjacent, so one flattened entry list
+// feeds the warps), and each 1024-entry slice of the z dictionary is loaded
+// once into registers (lane l holds entries 32 j + l) and used for all G rows,
+// which divides the dictionary's L2 traffic and the block barriers per row by G.
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);  // kWarps x kWarpStage
+    uint32_t* bm_all = smem + kWarps * kWarpStage;      // G bitmaps of tile_words words
+    __shared__ int32_t s_list[kThreads];
+    __shared__ int32_t s_lk[kThreads];
+    __shared__ int32_t s_wc[kWarps + 1];
+    __shared__ int32_t s_seg[G][kWarps];
+
+    const int64_t xr0 = (int64_t)blockIdx.x * G;
+    if (xr0 >= a.n_rows) return;
+    const int ng = (int)min64(G, a.n_rows - xr0);
+    const int64_t x0 = a.x_begin + xr0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = lanemask_lt();
+    const int64_t tile_words = a.tile_bits >> 5;
+    const bool tiled = a.tile_bits < a.n_z;
+    // R_CSR rows of the group are adjacent: [rb[0], rb[ng])
+    int64_t rb[G + 1];
+#pragma unroll
+    for (int k = 0; k <= G; ++k) rb[k] = a.r_rowptr[x0 + min(k, ng)];
+    int64_t out_pos[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        if (k < ng) {
+            out_pos[k] = a.off[xr0 + k];
+            fill_range(a.out_x, out_pos[k], a.off[xr0 + k + 1], a.dict_x[x0 + k], a.vec_ok);
+        }
+    }
+    auto row_of = [&](int64_t p) {
+        int k = 0;
+#pragma unroll
+        for (int q = 1; q < G; ++q) k += (q < ng && p >= rb[q]) ? 1 : 0;
+        return k;
+    };
+
+    for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += a.tile_bits) {
+        const int64_t zt1 = min64(zt0 + a.tile_bits, a.n_z);
+        const int tw = (int)((zt1 - zt0 + 31) >> 5);
+        for (int i = tid; i < ng * tile_words; i += kThreads) bm_all[i] = 0u;
+        __syncthreads();
+        // narrow S_sparse rows of all G rows: one warp per R entry
+        for (int64_t p = rb[0] + warp; p < rb[ng]; p += kWarps) {
+            const int32_t y = a.r_col[p];
+            if (a.bm_row_of_y[y] >= 0) continue;
+            uint32_t* bm = bm_all + row_of(p) * tile_words;
+            int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+            if (tiled) {
+                s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
+                s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
+            }
+            for (int64_t q = s0 + lane; q < s1; q += 32) {
+                const int32_t z = a.ss_col[q] - (int32_t)zt0;
+                atomicOr(&bm[z >> 5], 1u << (z & 31));
+            }
+        }
+        // wide S_sparse rows
+        for (int64_t base = rb[0]; base < rb[ng]; base += kThreads) {
+            const int64_t p = base + tid;
+            const int32_t b = p < rb[ng] ? a.bm_row_of_y[a.r_col[p]] : -1;
+            const unsigned bal = __ballot_sync(kFull, b >= 0);
+            if (lane == 0) s_wc[warp] = __popc(bal);
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int w = 0; w < kWarps; ++w) {
+                    const int c = s_wc[w];
+                    s_wc[w] = run;
+                    run += c;
+                }
+                s_wc[kWarps] = run;
+            }
+            __syncthreads();
+            if (b >= 0) {
+                const int slot = s_wc[warp] + __popc(bal & lt);
+                s_list[slot] = b;
+                s_lk[slot] = row_of(p);
+            }
+            __syncthreads();
+            const int nl = s_wc[kWarps];
+            if (nl > 0) {
+                const uint32_t* bits = a.ss_bits + (zt0 >> 5);
+                for (int w = tid; w < tw; w += kThreads) {
+                    uint32_t acc[G];
+#pragma unroll
+                    for (int k = 0; k < G; ++k) acc[k] = 0u;
+                    for (int i = 0; i < nl; ++i) {
+                        const uint32_t v = __ldg(bits + (int64_t)s_list[i] * a.zw + w);
+                        const int k = s_lk[i];
+#pragma unroll
+                        for (int q = 0; q < G; ++q) acc[q] |= (k == q) ? v : 0u;
+                    }
+#pragma unroll
+                    for (int k = 0; k < G; ++k)
+                        if (k < ng && acc[k]) bm_all[k * tile_words + w] |= acc[k];
+                }
+            }
+            __syncthreads();
+        }
+        if (a.n_zd > 0) {
+            for (int k = 0; k < ng; ++k) {
+                const uint32_t* drow = a.d_bits + (xr0 + k) * a.zdw;
+                uint32_t* bm = bm_all + k * tile_words;
+                for (int64_t w = tid; w < a.zdw; w += kThreads) {
+                    uint32_t word = drow[w];
+                    while (word) {
+                        const int b = __ffs(word) - 1;
+                        word &= word - 1;
+                        int32_t z = a.zd_list[w * 32 + b];
+                        if (z >= zt0 && z < zt1) {
+                            z -= (int32_t)zt0;
+                            atomicOr(&bm[z >> 5], 1u << (z & 31));
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // per-warp segment sizes of every row
+        const int groups = (tw + 31) >> 5;
+        const int gpw = (groups + kWarps - 1) / kWarps;
+        const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            int mine = 0;
+            if (k < ng) {
+                const uint32_t* bm = bm_all + k * tile_words;
+                for (int g = g0; g < g1; ++g) {
+                    const int w = (g << 5) + lane;
+                    mine += w < tw ? __popc(bm[w]) : 0;
+                }
+            }
+            mine = warp_sum(mine);
+            if (lane == 0) s_seg[k][warp] = mine;
+        }
+        __syncthreads();
+        int64_t wpos[G];
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            int64_t before = 0, all = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                const int c = s_seg[k][w];
+                if (w < warp) before += c;
+                all += c;
+            }
+            wpos[k] = (k < ng ? out_pos[k] : 0) + before;
+            if (k < ng) out_pos[k] += all;
+        }
+        int32_t* st = stage + warp * kWarpStage;
+        const int64_t zlim = a.n_z - zt0;
+        for (int g = g0; g < g1; ++g) {
+            const int w = (g << 5) + lane;
+            uint32_t word[G];
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                word[k] = (k < ng && w < tw) ? bm_all[k * tile_words + w] : 0u;
+                any |= word[k] != 0u;
+            }
+            if (!__any_sync(kFull, any)) continue;
+            int32_t dreg[32];
+            const int64_t gb = (int64_t)g << 10;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int64_t idx = gb + (j << 5) + lane;
+                dreg[j] = idx < zlim ? __ldg(a.dict_z + zt0 + idx) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const int c = __popc(word[k]);
+                const int incl = warp_inclusive_scan(c);
+                const int total_g = __shfl_sync(kFull, incl, 31);
+                if (total_g == 0) continue;
+                const int excl = incl - c;
+                const int sh = (int)(wpos[k] & 3);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t wj = __shfl_sync(kFull, word[k], j);
+                    const int pj = __shfl_sync(kFull, excl, j);
+                    if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = dreg[j];
+                }
+                __syncwarp();
+                flush_warp(a.out_z + (wpos[k] - sh), st, sh, total_g, a.vec_ok);
+                __syncwarp();
+                wpos[k] += total_g;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Join-Count: counters per z of a tile.
 template <bool kEmit>
 __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
@@ -381,6 +578,20 @@ static XRowArgs make_args(const Plan& p, int64_t x_begin, int64_t rows, int kind
     return a;
 }
 
+// x rows per CTA of the emitting pass: the option if set (1, 2 or 4), else 2
+// when the two bitmaps keep the CTA under 112 KiB of shared memory, else 1.
+// (Measured on the 1M x 1M Zipf workload: 1 row 8.8 ms, 2 rows 7.6 ms,
+// 4 rows 8.1 ms; four rows need 100 registers and fit only two CTAs per SM.)
+static int emit_rows_per_cta(const Ctx& ctx, int64_t tile_bits) {
+    const int64_t want = ctx.opt.emit_rows;
+    const int64_t stage = (int64_t)kWarps * kWarpStage * 4, bm = (tile_bits / 32) * 4;
+    const int64_t cap = (int64_t)ctx.smem_optin - 4096;
+    auto fits = [&](int64_t g, int64_t lim) { return stage + g * bm <= lim; };
+    if (want == 1 || want == 2 || want == 4) return fits(want, cap) ? (int)want : 1;
+    if (fits(2, 112 * 1024)) return 2;
+    return 1;
+}
+
 static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, cudaStream_t s) {
     if (a.n_rows <= 0 || a.n_z <= 0) return;
     setup_attrs(ctx);
@@ -389,8 +600,26 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
     PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
     if (kind == 0) {
         const size_t sm = bits_smem(a.tile_bits, emit);
-        if (emit) k_xrow_bits<true><<<g, kThreads, sm, s>>>(a);
-        else k_xrow_bits<false><<<g, kThreads, sm, s>>>(a);
+        const int grp = emit ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
+        if (emit && grp > 1) {
+            const size_t smg = (size_t)kWarps * kWarpStage * 4 + (size_t)grp * (size_t)(a.tile_bits / 32) * 4;
+            const unsigned gg = (unsigned)ceil_div(a.n_rows, grp);
+            static int cur2[64] = {0}, cur4[64] = {0};
+            int* cur = (grp == 2 ? cur2 : cur4) + (ctx.device & 63);
+            if ((int)smg > *cur) {
+                if (grp == 2)
+                    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_emit_g<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg));
+                else
+                    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_emit_g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg));
+                *cur = (int)smg;
+            }
+            if (grp == 2) k_xrow_emit_g<2><<<gg, kThreads, smg, s>>>(a);
+            else k_xrow_emit_g<4><<<gg, kThreads, smg, s>>>(a);
+        } else if (emit) {
+            k_xrow_bits<true><<<g, kThreads, sm, s>>>(a);
+        } else {
+            k_xrow_bits<false><<<g, kThreads, sm, s>>>(a);
+        }
     } else {
         const size_t sm = cnt_smem(a.tile_bits);
         if (emit) k_xrow_counts<true><<<g, kThreads, sm, s>>>(a);

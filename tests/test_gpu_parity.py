@@ -262,3 +262,14 @@ def test_sorted_distinct_on_device(ctx):
     inst = gen.config2_two_table(scale=0.05)
     x, z = ctx.join_project(*inst_dev(inst))
     check_sorted_distinct(x, z)
+
+
+@pytest.mark.parametrize("rows", [1, 2, 4])
+def test_emit_rows_per_cta(rows):
+    """The emitting pass gives the same pairs with 1, 2 or 4 x rows per CTA,
+    including an odd number of rows (ragged last group)."""
+    c = fresh_ctx({6: rows})
+    for inst in (gen.config2_two_table(scale=0.01), gen.small_two_table(3, n_r=3001, n_s=2999, nx=301, ny=97,
+                                                                          nz=203, zipf=1.1)):
+        assert_project(c, inst)
+    c.close()
