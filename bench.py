@@ -30,7 +30,9 @@ if ROOT not in sys.path:
 
 METRIC = "dedup (x,z) pairs/s on 1 GB300 vs plain path; served p50/p99 latency"
 UNIT = "pairs/s"
-WORKLOADS = ("two_table_1m_zipf1", "self_20k", "chung_lu_1m_4m")
+WORKLOADS = ("two_table_1m_zipf1", "self_20k", "chung_lu_1m_4m", "dense_16k")
+# fp8 (f8f6f4) dense tensor rate = 2 x bf16 (nominal 4.5 vs 2.25 PFLOP/s)
+FP8_PER_BF16 = 2.0
 
 
 def parse_args():
@@ -44,6 +46,8 @@ def parse_args():
                     help="shrink the workload proportionally (profiling captures only; bench lines use 1.0)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--theta-z", type=int, default=None, help="dense iff m_z >= theta (default: library's)")
+    ap.add_argument("--dense-variant", type=int, default=None, help="0 auto, 1 tensor core, 2 popc, 3 probe")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -56,17 +60,26 @@ def make_workload(name: str, rank: int = 0, scale: float = 1.0):
         return gen.config2_two_table(seed=1 + 1000 * rank, scale=scale)
     if name == "self_20k":
         return gen.config1_self(seed=0 + 1000 * rank)
+    if name == "dense_16k":
+        # DenseEC shape: |X| = |Y| = |Z| = 16384, 4M uniform tuples per table
+        # (density 1.5%); with theta_z = 0 every z is dense and the tensor-core
+        # product covers 2 * 16384^3 FLOP
+        n = max(64, int(16384 * scale))
+        return gen.two_table(np.random.default_rng(7 + 1000 * rank), 16 * n * n // 1024, 16 * n * n // 1024,
+                             n, n, n, 0.0, name=f"dense_{n}")
     return gen.config3_chung_lu(seed=2 + 1000 * rank, scale=scale)
 
 
 def measured_peaks():
+    """HBM GB/s, bf16 TFLOP/s burst and sustained, and where they came from."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return {"hbm": float(d["hbm_gbs"]), "bf16": float(d["bf16_tflops"]),
+                "bf16_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "source": "measured"}
     except Exception:  # noqa: BLE001
-        return 6800.0, "fallback"
+        return {"hbm": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
 
 
 class ClockSampler:
@@ -224,6 +237,13 @@ def main():
     cols = [torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(dev)
             for a in (inst.r_key, inst.r_val, inst.s_key, inst.s_val)]
     ctx = dim3.Context(local_rank)
+    dense_wl = args.workload.startswith("dense")
+    theta = args.theta_z if args.theta_z is not None else (0 if dense_wl else None)
+    variant = args.dense_variant if args.dense_variant is not None else (dim3.DENSE_TC if dense_wl else None)
+    if theta is not None:
+        ctx.set_option(dim3.OPT_THETA_Z, theta)
+    if variant is not None:
+        ctx.set_option(dim3.OPT_DENSE_VARIANT, variant)
 
     # size the output once (plan path), then time the one-call path
     plan = ctx.partition(*cols)
@@ -283,14 +303,30 @@ def main():
         busy_max, pairs_all = busy_s, float(total_pairs)
     value = pairs_all / busy_max
 
-    # roofline of the dominant kernel: SparseBMM + union + compaction (emitting pass)
-    hbm_peak, peak_src = measured_peaks()
-    emit_ms, emit_n = tm["sparse_emit"]
-    emit_s = emit_ms / 1e3 / max(emit_n, 1)
-    alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
-    achieved = alg_bytes / emit_s / 1e9
-    traffic, _ = traffic_for("k_xrow_bits_emit")
+    # roofline of the dominant kernel: SparseBMM + union + compaction (emitting
+    # pass, HBM-bound), or the tensor-core DenseEC product when every z is dense
+    peaks = measured_peaks()
     phases = {k: round(v[0] / max(v[1], 1), 4) for k, v in tm.items() if v[1]}
+    tc_ms, tc_n = tm["dense_tc"]
+    if tc_n and tc_ms > tm["sparse_emit"][0]:
+        tc_s = tc_ms / 1e3 / tc_n
+        flops = 2.0 * info["n_x"] * info["n_y_dense"] * info["n_z_dense"]
+        peak = peaks["bf16"] * FP8_PER_BF16
+        achieved = flops / tc_s / 1e12
+        roofline = {"bound": "tensor", "kernel": "k_dense_tc (tcgen05 kind::f8f6f4, 0/1 operands)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": f"{peaks['source']} bf16 burst x {FP8_PER_BF16} (fp8/bf16 nominal ratio)",
+                    "traffic": None, "alg_flops_per_launch": flops, "launch_ms": tc_s * 1e3}
+    else:
+        emit_ms, emit_n = tm["sparse_emit"]
+        emit_s = emit_ms / 1e3 / max(emit_n, 1)
+        alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
+        achieved = alg_bytes / emit_s / 1e9
+        traffic, _ = traffic_for("k_xrow_bits_emit")
+        roofline = {"bound": "hbm", "kernel": "k_xrow_emit_g / k_xrow_bits<emit> (SparseBMM+union+compaction)",
+                    "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s", "frac": achieved / peaks["hbm"],
+                    "peak_source": peaks["source"], "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                    "launch_ms": emit_s * 1e3}
 
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
@@ -311,10 +347,7 @@ def main():
                        "l2": "flushed between steps (256 MiB write outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "join_tuples_per_s": info["out_j"] * args.steps * (pairs_all / total_pairs) / busy_max},
-            "roofline": {"bound": "hbm", "kernel": "k_xrow_bits<emit> (SparseBMM+union+compaction)",
-                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "peak_source": peak_src, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
-                         "launch_ms": emit_s * 1e3},
+            "roofline": roofline,
             "phase_ms": phases,
             "wall_s": t_wall,
             "gpu_launches": launches,

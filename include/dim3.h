@@ -100,7 +100,8 @@ typedef enum {
     DIM3_PHASE_PARTITION = 1,    /* mapping + CSR + split of dim3_partition / dim3_join_* */
     DIM3_PHASE_DENSE_EC = 2,     /* DenseEC kernels */
     DIM3_PHASE_SPARSE_COUNT = 3, /* SparseBMM + union, counting pass */
-    DIM3_PHASE_SPARSE_EMIT = 4   /* SparseBMM + union + compaction, emitting pass */
+    DIM3_PHASE_SPARSE_EMIT = 4,  /* SparseBMM + union + compaction, emitting pass */
+    DIM3_PHASE_DENSE_TC = 5      /* the tcgen05 DenseEC kernel alone (inside DIM3_PHASE_DENSE_EC) */
 } dim3_phase;
 
 /* Library version as major*10000 + minor*100 + patch. */

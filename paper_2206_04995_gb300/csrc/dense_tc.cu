@@ -314,6 +314,7 @@ void tc_dense_product(const Ctx& ctx, const uint8_t* A, int64_t rows, int64_t ro
     DIM3_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     const dim3 grid((unsigned)(n_pad / kTcTileN), (unsigned)(rows_pad / kTcTileM));
     const int num_kb = (int)(k_pad / kTcBlockK);
+    PhaseScope phase(ctx.stats, PH_DENSE_TC, s);
     if (kind == 0)
         k_dense_tc<0><<<grid, kTcThreads, kTcSmem, s>>>(ma, mb, rows, n_zd, num_kb, d_bits, zdw, nullptr,
                                                          err.as<int>());

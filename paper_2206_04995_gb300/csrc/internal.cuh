@@ -71,7 +71,7 @@ struct Plan {
 
 // Per-phase CUDA-event timing (DIM3_OPT_TIMING). Events are recorded on the
 // launching stream around a phase and resolved when the caller asks.
-enum Phase { PH_MAP = 0, PH_PARTITION = 1, PH_DENSE = 2, PH_COUNT = 3, PH_EMIT = 4, PH_N = 5 };
+enum Phase { PH_MAP = 0, PH_PARTITION = 1, PH_DENSE = 2, PH_COUNT = 3, PH_EMIT = 4, PH_DENSE_TC = 5, PH_N = 6 };
 struct Stats {
     bool on = false;
     double ms[PH_N] = {};

@@ -26,7 +26,7 @@ DIM3_ERR_UNSUPPORTED = -7
 
 DENSE_AUTO, DENSE_TC, DENSE_POPC, DENSE_PROBE = 0, 1, 2, 3
 OPT_THETA_Z, OPT_DENSE_VARIANT, OPT_BITMAP_ROW_MIN, OPT_LIGHT_ROW_MAX, OPT_TIMING = 1, 2, 3, 4, 5
-PHASES = {"map": 0, "partition": 1, "dense_ec": 2, "sparse_count": 3, "sparse_emit": 4}
+PHASES = {"map": 0, "partition": 1, "dense_ec": 2, "sparse_count": 3, "sparse_emit": 4, "dense_tc": 5}
 
 TABLES = {
     "dict_x": (1, torch.int32), "dict_y": (2, torch.int32), "dict_z": (3, torch.int32),
