@@ -75,6 +75,14 @@ typedef struct {
     int32_t dense_variant;/* DenseEC variant that will run (dim3_dense_variant) */
 } dim3_plan_info;
 
+/* One instance of a batch: device columns as for dim3_join_project. */
+typedef struct {
+    const int32_t *r_key, *r_val; /* R(x, y): key = y, value = x */
+    int64_t nr;
+    const int32_t *s_key, *s_val; /* S(z, y): key = y, value = z */
+    int64_t ns;
+} dim3_instance;
+
 /* DenseEC bitmap-intersection variants (Algorithm 3; the choice is the role
  * of f3 in Section 2.6). All give identical results. */
 typedef enum {
@@ -211,6 +219,36 @@ DIM3_API int dim3_plan_join_project(dim3_ctx *ctx, dim3_plan *plan, int64_t x_be
 DIM3_API int dim3_plan_join_count(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
                          int32_t *d_out_x, int32_t *d_out_z, int32_t *d_out_cnt,
                          int64_t capacity, int64_t *count, void *stream);
+
+/*
+ * Batches of independent instances (Eq. 1 for each), run through one pass
+ * of the path: the columns are gathered with an instance tag, mapping ranks
+ * (instance, value) pairs, so each instance owns a contiguous block of ids and
+ * no join crosses instances; SparseBMM works in each x's own z window and
+ * DenseEC computes only the block diagonal. Not a paper operation as such:
+ * the data-parallel outer x loop of Section 6 (OpenMP) extended across
+ * instances.
+ *
+ * dim3_batch_partition -- as dim3_partition for n_inst instances (host array
+ *   of dim3_instance with device columns). The plan's x ids list instance 0's
+ *   x first, then instance 1's, ...; info holds the batch totals.
+ * dim3_plan_instance_ranges -- x_lo[t] .. x_lo[t+1] (host, n_inst + 1 entries)
+ *   is instance t's x-id range, for x-range calls on a batch plan.
+ * dim3_batch_join_project / dim3_batch_join_count -- the whole path for a
+ *   batch: pairs of instance 0 in canonical order, then instance 1's, ...;
+ *   inst_counts (host, n_inst entries, may be NULL) receives each instance's
+ *   number of pairs, count their sum. Capacity protocol as dim3_join_project.
+ * All synchronise the stream.
+ */
+DIM3_API int dim3_batch_partition(dim3_ctx *ctx, int n_inst, const dim3_instance *inst, int32_t theta_z,
+                                  dim3_plan **plan_out, dim3_plan_info *info, void *stream);
+DIM3_API int dim3_plan_instance_ranges(const dim3_plan *plan, int64_t *x_lo);
+DIM3_API int dim3_batch_join_project(dim3_ctx *ctx, int n_inst, const dim3_instance *inst, int32_t *d_out_x,
+                                     int32_t *d_out_z, int64_t capacity, int64_t *inst_counts, int64_t *count,
+                                     void *stream);
+DIM3_API int dim3_batch_join_count(dim3_ctx *ctx, int n_inst, const dim3_instance *inst, int32_t *d_out_x,
+                                   int32_t *d_out_z, int32_t *d_out_cnt, int64_t capacity, int64_t *inst_counts,
+                                   int64_t *count, void *stream);
 
 /* Tables a plan can export (dim3_plan_export), for inspection and tests. */
 typedef enum {

@@ -113,6 +113,19 @@ void check_table(const int32_t* k, const int32_t* v, int64_t n, const char* name
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+dimcube::PlanInput single_input(const int32_t* rk, const int32_t* rv, int64_t nr, const int32_t* sk, const int32_t* sv,
+                                int64_t ns) {
+    dimcube::PlanInput in;
+    in.r_key = rk;
+    in.r_val = rv;
+    in.nr = nr;
+    in.s_key = sk;
+    in.s_val = sv;
+    in.ns = ns;
+    in.n_inst = 1;
+    return in;
+}
+
 }  // namespace
 
 extern "C" {
@@ -233,8 +246,8 @@ int dim3_partition(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val
         check_table(d_s_key, d_s_val, ns, "S");
         DeviceGuard g(ctx->c.device);
         std::unique_ptr<dim3_plan> pl(new dim3_plan());
-        pl->p.reset(dimcube::build_plan(ctx->c, d_r_key, d_r_val, nr, d_s_key, d_s_val, ns, resolve_theta(ctx, theta_z),
-                                        as_stream(stream)));
+        pl->p.reset(dimcube::build_plan(ctx->c, single_input(d_r_key, d_r_val, nr, d_s_key, d_s_val, ns),
+                                        resolve_theta(ctx, theta_z), as_stream(stream)));
         if (info) *info = pl->p->info;
         *plan_out = pl.release();
     });
@@ -334,7 +347,8 @@ static int join_common(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r
         DeviceGuard g(ctx->c.device);
         cudaStream_t s = as_stream(stream);
         std::unique_ptr<dimcube::Plan> p(
-            dimcube::build_plan(ctx->c, d_r_key, d_r_val, nr, d_s_key, d_s_val, ns, resolve_theta(ctx, -1), s));
+            dimcube::build_plan(ctx->c, single_input(d_r_key, d_r_val, nr, d_s_key, d_s_val, ns),
+                                resolve_theta(ctx, -1), s));
         try {
             dimcube::plan_join(ctx->c, *p, 0, p->info.n_x, kind, d_out_x, d_out_z, d_out_cnt, capacity, count, s);
         } catch (...) {
@@ -345,6 +359,65 @@ static int join_common(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r
         p.reset();
         DIM3_CUDA(cudaStreamSynchronize(s));
     });
+}
+
+int dim3_batch_partition(dim3_ctx* ctx, int n_inst, const dim3_instance* inst, int32_t theta_z, dim3_plan** plan_out,
+                         dim3_plan_info* info, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && plan_out && inst && n_inst >= 1, DIM3_ERR_ARG, "null ctx, plan_out or instances");
+        *plan_out = nullptr;
+        DeviceGuard g(ctx->c.device);
+        std::unique_ptr<dim3_plan> pl(new dim3_plan());
+        pl->p.reset(dimcube::build_batch_plan(ctx->c, n_inst, inst, resolve_theta(ctx, theta_z), as_stream(stream)));
+        if (info) *info = pl->p->info;
+        *plan_out = pl.release();
+    });
+}
+
+int dim3_plan_instance_ranges(const dim3_plan* plan, int64_t* x_lo) {
+    return guarded([&] {
+        DIM3_REQUIRE(plan && x_lo, DIM3_ERR_ARG, "null plan or x_lo");
+        const auto& v = plan->p->h_inst_x_lo;
+        std::copy(v.begin(), v.end(), x_lo);
+    });
+}
+
+static int batch_common(dim3_ctx* ctx, int n_inst, const dim3_instance* inst, int32_t* d_out_x, int32_t* d_out_z,
+                        int32_t* d_out_cnt, int64_t capacity, int64_t* inst_counts, int64_t* count, void* stream,
+                        int kind) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && count && inst && n_inst >= 1, DIM3_ERR_ARG, "null ctx, count or instances");
+        DIM3_REQUIRE(capacity >= 0, DIM3_ERR_ARG, "negative capacity");
+        *count = 0;
+        DeviceGuard g(ctx->c.device);
+        cudaStream_t s = as_stream(stream);
+        std::unique_ptr<dimcube::Plan> p(dimcube::build_batch_plan(ctx->c, n_inst, inst, resolve_theta(ctx, -1), s));
+        try {
+            dimcube::plan_join(ctx->c, *p, 0, p->info.n_x, kind, d_out_x, d_out_z, d_out_cnt, capacity, count, s);
+            if (inst_counts) dimcube::batch_instance_counts(*p, inst_counts, s);
+        } catch (const dimcube::Error& e) {
+            if (e.status == DIM3_ERR_CAPACITY && inst_counts) dimcube::batch_instance_counts(*p, inst_counts, s);
+            p.reset();
+            cudaStreamSynchronize(s);
+            throw;
+        } catch (...) {
+            p.reset();
+            cudaStreamSynchronize(s);
+            throw;
+        }
+        p.reset();
+        DIM3_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int dim3_batch_join_project(dim3_ctx* ctx, int n_inst, const dim3_instance* inst, int32_t* d_out_x, int32_t* d_out_z,
+                            int64_t capacity, int64_t* inst_counts, int64_t* count, void* stream) {
+    return batch_common(ctx, n_inst, inst, d_out_x, d_out_z, nullptr, capacity, inst_counts, count, stream, 0);
+}
+
+int dim3_batch_join_count(dim3_ctx* ctx, int n_inst, const dim3_instance* inst, int32_t* d_out_x, int32_t* d_out_z,
+                          int32_t* d_out_cnt, int64_t capacity, int64_t* inst_counts, int64_t* count, void* stream) {
+    return batch_common(ctx, n_inst, inst, d_out_x, d_out_z, d_out_cnt, capacity, inst_counts, count, stream, 1);
 }
 
 int dim3_join_project(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val, int64_t nr, const int32_t* d_s_key,

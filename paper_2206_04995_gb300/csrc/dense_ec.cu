@@ -109,11 +109,13 @@ __global__ void k_a_tc(const int64_t* r_rowptr, const int32_t* r_col, const int3
 template <bool kCount>
 __global__ void __launch_bounds__(kThreads) k_dense_popc(const uint32_t* __restrict__ A, const uint32_t* __restrict__ B,
                                                          int64_t rows, int64_t n_zd, int64_t kw, uint32_t* D,
-                                                         int64_t zdw, int32_t* C) {
+                                                         int64_t zdw, int32_t* C, const int2* __restrict__ tiles) {
     __shared__ uint32_t As[64][33];
     __shared__ uint32_t Bs[32][65];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t row0 = (int64_t)blockIdx.y * 64, col0 = (int64_t)blockIdx.x * 64;
+    // batches compute only the tiles of the block diagonal (tile list)
+    const int64_t row0 = (int64_t)(tiles ? tiles[blockIdx.x].x : (int)blockIdx.y) * 64;
+    const int64_t col0 = (int64_t)(tiles ? tiles[blockIdx.x].y : (int)blockIdx.x) * 64;
     int acc[8][2];
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = 0;
@@ -168,12 +170,16 @@ __global__ void __launch_bounds__(kThreads) k_dense_popc(const uint32_t* __restr
 template <bool kCount>
 __global__ void __launch_bounds__(128) k_dense_probe(const int64_t* r_rowptr, const int32_t* r_col, const int32_t* kidx,
                                                      int64_t x_begin, int64_t rows, const uint32_t* __restrict__ sdt,
-                                                     int64_t zdw, int64_t n_zd, uint32_t* D, int32_t* C) {
+                                                     int64_t zdw, int64_t n_zd, uint32_t* D, int32_t* C,
+                                                     const int32_t* x_tag, const int64_t* zd_lo) {
     const int64_t xr = blockIdx.x;
     if (xr >= rows) return;
     const int64_t x = x_begin + xr;
     const int64_t q0 = r_rowptr[x], q1 = r_rowptr[x + 1];
-    for (int64_t w = threadIdx.x; w < zdw; w += blockDim.x) {
+    // words of the dense indices of x's instance (batches; all words otherwise)
+    const int tg = x_tag ? x_tag[x] : 0;
+    const int64_t w0 = x_tag ? (zd_lo[tg] >> 5) : 0, w1 = x_tag ? ((zd_lo[tg + 1] + 31) >> 5) : zdw;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
         if (!kCount) {
             uint32_t acc = 0u;
             for (int64_t q = q0; q < q1; ++q) {
@@ -201,23 +207,75 @@ __global__ void __launch_bounds__(128) k_dense_probe(const int64_t* r_rowptr, co
     }
 }
 
+// Tiles (row tile, column tile) of size tm x tn that meet the block of some
+// instance: its x rows within [x_begin, x_begin + rows) times its dense z.
+// Uploaded to `out`; returns their number.
+static int64_t upload_block_tiles(const Plan& p, int64_t x_begin, int64_t rows, int tm, int tn, DevBuf& out,
+                                  cudaStream_t s) {
+    std::vector<int64_t> keys;
+    for (int t = 0; t < p.n_inst; ++t) {
+        const int64_t r0 = std::max(p.h_inst_x_lo[t], x_begin) - x_begin;
+        const int64_t r1 = std::min(p.h_inst_x_lo[t + 1], x_begin + rows) - x_begin;
+        const int64_t c0 = p.h_inst_zd_lo[t], c1 = p.h_inst_zd_lo[t + 1];
+        if (r1 <= r0 || c1 <= c0) continue;
+        for (int64_t m = r0 / tm; m <= (r1 - 1) / tm; ++m)
+            for (int64_t n = c0 / tn; n <= (c1 - 1) / tn; ++n) keys.push_back((m << 32) | n);
+    }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    std::vector<int2> tiles(keys.size());
+    for (size_t i = 0; i < keys.size(); ++i) tiles[i] = make_int2((int)(keys[i] >> 32), (int)(keys[i] & 0xffffffff));
+    if (tiles.empty()) return 0;
+    out.alloc(tiles.size() * sizeof(int2), s);
+    DIM3_CUDA(cudaMemcpyAsync(out.p, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    DIM3_CUDA(cudaStreamSynchronize(s));  // the host vector goes out of scope
+    return (int64_t)tiles.size();
+}
+
 void dense_ec(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int kind, uint32_t* d_bits, int32_t* d_cnt,
               cudaStream_t s) {
     const int64_t n_zd = p.info.n_z_dense;
     if (rows <= 0 || n_zd <= 0) return;
     const int variant = p.info.dense_variant;
     PhaseScope phase(ctx.stats, PH_DENSE, s);
+    const bool batch = p.n_inst > 1;
+    if (batch) {
+        // only the block diagonal is computed: everything else is zero
+        if (kind == 0) DIM3_CUDA(cudaMemsetAsync(d_bits, 0, (size_t)(rows * p.zdw) * 4, s));
+        else DIM3_CUDA(cudaMemsetAsync(d_cnt, 0, (size_t)(rows * n_zd) * 4, s));
+    }
     if (variant == DIM3_DENSE_PROBE) {
         DIM3_REQUIRE(rows < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long");
+        const int32_t* xt = batch ? p.x_tag.as<int32_t>() : nullptr;
         if (kind == 0)
             k_dense_probe<false><<<(unsigned)rows, 128, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(),
                                                                p.kidx_of_y.as<int32_t>(), x_begin, rows,
-                                                               p.sdt_bits.as<uint32_t>(), p.zdw, n_zd, d_bits, nullptr);
+                                                               p.sdt_bits.as<uint32_t>(), p.zdw, n_zd, d_bits, nullptr,
+                                                               xt, p.inst_zd_lo.as<int64_t>());
         else
             k_dense_probe<true><<<(unsigned)rows, 128, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(),
                                                               p.kidx_of_y.as<int32_t>(), x_begin, rows,
-                                                              p.sdt_bits.as<uint32_t>(), p.zdw, n_zd, nullptr, d_cnt);
+                                                              p.sdt_bits.as<uint32_t>(), p.zdw, n_zd, nullptr, d_cnt,
+                                                              xt, p.inst_zd_lo.as<int64_t>());
         DIM3_LAUNCHED();
+    } else if (variant == DIM3_DENSE_POPC && batch) {
+        DevBuf a;
+        a.alloc((size_t)(rows * p.kw) * 4, s);
+        DIM3_CUDA(cudaMemsetAsync(a.p, 0, a.bytes, s));
+        k_a_bits<<<grid_for(rows), kThreads, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(),
+                                                      p.kidx_of_y.as<int32_t>(), x_begin, rows, a.as<uint32_t>(), p.kw);
+        DIM3_LAUNCHED();
+        DevBuf tl;
+        const int64_t nt = upload_block_tiles(p, x_begin, rows, 64, 64, tl, s);
+        if (nt > 0) {
+            if (kind == 0)
+                k_dense_popc<false><<<(unsigned)nt, kThreads, 0, s>>>(a.as<uint32_t>(), p.b_bits.as<uint32_t>(), rows,
+                                                                      n_zd, p.kw, d_bits, p.zdw, nullptr, tl.as<int2>());
+            else
+                k_dense_popc<true><<<(unsigned)nt, kThreads, 0, s>>>(a.as<uint32_t>(), p.b_bits.as<uint32_t>(), rows,
+                                                                     n_zd, p.kw, nullptr, p.zdw, d_cnt, tl.as<int2>());
+            DIM3_LAUNCHED();
+        }
     } else if (variant == DIM3_DENSE_POPC) {
         DevBuf a;
         a.alloc((size_t)(rows * p.kw) * 4, s);
@@ -230,10 +288,10 @@ void dense_ec(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int 
             DIM3_REQUIRE(ceil_div(rows, 64) < 65536, DIM3_ERR_OVERFLOW, "x range too long for one DenseEC launch");
             if (kind == 0)
                 k_dense_popc<false><<<g, kThreads, 0, s>>>(a.as<uint32_t>(), p.b_bits.as<uint32_t>(), rows, n_zd, p.kw,
-                                                           d_bits, p.zdw, nullptr);
+                                                           d_bits, p.zdw, nullptr, nullptr);
             else
                 k_dense_popc<true><<<g, kThreads, 0, s>>>(a.as<uint32_t>(), p.b_bits.as<uint32_t>(), rows, n_zd, p.kw,
-                                                          nullptr, p.zdw, d_cnt);
+                                                          nullptr, p.zdw, d_cnt, nullptr);
             DIM3_LAUNCHED();
         }
     } else {
@@ -244,8 +302,14 @@ void dense_ec(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int 
         k_a_tc<<<grid_for(rows), kThreads, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(),
                                                     p.kidx_of_y.as<int32_t>(), x_begin, rows, a.as<uint8_t>(), p.k_pad);
         DIM3_LAUNCHED();
+        DevBuf tl;
+        int64_t nt = 0;
+        if (batch) {
+            nt = upload_block_tiles(p, x_begin, rows, kTcTileM, kTcTileN, tl, s);
+            if (nt == 0) return;
+        }
         tc_dense_product(ctx, a.as<uint8_t>(), rows, rows_pad, p.b_tc.as<uint8_t>(), n_zd, p.n_zd_pad, p.k_pad, kind,
-                         d_bits, p.zdw, d_cnt, s);
+                         d_bits, p.zdw, d_cnt, batch ? tl.as<int2>() : nullptr, nt, s);
     }
 }
 

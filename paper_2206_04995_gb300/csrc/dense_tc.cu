@@ -154,7 +154,7 @@ template <int kKind>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_dense_tc(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b, int64_t rows,
                int64_t n_zd, int num_kb, uint32_t* __restrict__ d_bits, int64_t zdw, int32_t* __restrict__ d_cnt,
-               int* err) {
+               int* err, const int2* __restrict__ tiles) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = base;
@@ -166,8 +166,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m0 = (int64_t)blockIdx.y * kTcTileM;
-    const int64_t n0 = (int64_t)blockIdx.x * kTcTileN;
+    // batches compute only the tiles of the block-diagonal (tile list)
+    const int64_t m0 = (int64_t)(tiles ? tiles[blockIdx.x].x : (int)blockIdx.y) * kTcTileM;
+    const int64_t n0 = (int64_t)(tiles ? tiles[blockIdx.x].y : (int)blockIdx.x) * kTcTileN;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -296,8 +297,9 @@ bool tc_supported(const Ctx& ctx) { return ctx.cc_major == 10 && ctx.cc_minor ==
 
 void tc_dense_product(const Ctx& ctx, const uint8_t* A, int64_t rows, int64_t rows_pad, const uint8_t* B, int64_t n_zd,
                       int64_t n_pad, int64_t k_pad, int kind, uint32_t* d_bits, int64_t zdw, int32_t* d_cnt,
-                      cudaStream_t s) {
-    if (rows <= 0 || n_zd <= 0) return;
+                      const int2* tiles, int64_t n_tiles, cudaStream_t s) {
+    if (rows <= 0 || n_zd <= 0 || (tiles && n_tiles <= 0)) return;
+    DIM3_REQUIRE(!tiles || n_tiles < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "too many DenseEC tiles");
     DIM3_REQUIRE(tc_supported(ctx), DIM3_ERR_UNSUPPORTED, "tensor-core DenseEC needs an sm_103 device");
     DIM3_REQUIRE(k_pad > 0 && k_pad < kTcMaxK, DIM3_ERR_OVERFLOW, "DenseEC K exceeds the exact FP32 range");
     DIM3_REQUIRE(rows_pad / kTcTileM < 65536, DIM3_ERR_OVERFLOW, "x range too long for one DenseEC launch");
@@ -312,15 +314,15 @@ void tc_dense_product(const Ctx& ctx, const uint8_t* A, int64_t rows, int64_t ro
     DevBuf err;
     err.alloc(sizeof(int), s);
     DIM3_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    const dim3 grid((unsigned)(n_pad / kTcTileN), (unsigned)(rows_pad / kTcTileM));
+    const dim3 grid = tiles ? dim3((unsigned)n_tiles) : dim3((unsigned)(n_pad / kTcTileN), (unsigned)(rows_pad / kTcTileM));
     const int num_kb = (int)(k_pad / kTcBlockK);
     PhaseScope phase(ctx.stats, PH_DENSE_TC, s);
     if (kind == 0)
         k_dense_tc<0><<<grid, kTcThreads, kTcSmem, s>>>(ma, mb, rows, n_zd, num_kb, d_bits, zdw, nullptr,
-                                                         err.as<int>());
+                                                         err.as<int>(), tiles);
     else
         k_dense_tc<1><<<grid, kTcThreads, kTcSmem, s>>>(ma, mb, rows, n_zd, num_kb, nullptr, zdw, d_cnt,
-                                                         err.as<int>());
+                                                         err.as<int>(), tiles);
     DIM3_LAUNCHED();
     int h = 0;
     DIM3_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -18,8 +18,10 @@ bool tc_supported(const Ctx& ctx);
 
 // C = A * B^T over K (both K-major e4m3 0/1), A [rows_pad][k_pad], B [n_pad][k_pad].
 // kind 0: bits D[r][zdw] = (C > 0); kind 1: counts C[r][n_zd] (int32).
+// tiles (device, n_tiles entries of (row tile, column tile)) restricts the
+// product to those 128 x 256 tiles (batches: the block diagonal); null = all.
 void tc_dense_product(const Ctx& ctx, const uint8_t* A, int64_t rows, int64_t rows_pad, const uint8_t* B,
                       int64_t n_zd, int64_t n_pad, int64_t k_pad, int kind, uint32_t* d_bits, int64_t zdw,
-                      int32_t* d_cnt, cudaStream_t s);
+                      int32_t* d_cnt, const int2* tiles, int64_t n_tiles, cudaStream_t s);
 
 }  // namespace dimcube

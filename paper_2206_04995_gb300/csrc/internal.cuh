@@ -20,9 +20,23 @@ struct ValueMap {
 // ids_out [n]; dict_out [n] capacity, first n_distinct ascending.
 void build_value_map(const int32_t* vals, const int32_t* pred, int64_t n, ValueMap& vm,
                      int32_t* ids_out, int32_t* dict_out, cudaStream_t s);
-// ids_out[i] = id of vals[i] in vm, or -1 if absent.
-void probe_value_map(const ValueMap& vm, const int32_t* vals, int64_t n, int32_t* ids_out,
+// Batched form: row i belongs to instance tags[i] (0 <= tag < n_tags); ids
+// rank the (instance, value) pairs; dict_tag_out[id] = the id's instance.
+void build_value_map(const int32_t* vals, const int32_t* tags, int n_tags, const int32_t* pred, int64_t n,
+                     ValueMap& vm, int32_t* ids_out, int32_t* dict_out, int32_t* dict_tag_out, cudaStream_t s);
+// ids_out[i] = id of (tags[i], vals[i]) in vm (tags may be null), or -1 if absent.
+void probe_value_map(const ValueMap& vm, const int32_t* vals, const int32_t* tags, int64_t n, int32_t* ids_out,
                      cudaStream_t s);
+
+// Input of the plan builder: one instance (tags null, n_inst 1) or a batch of
+// n_inst instances concatenated, row i of R belonging to instance r_tag[i].
+struct PlanInput {
+    const int32_t *r_key = nullptr, *r_val = nullptr, *r_tag = nullptr;
+    int64_t nr = 0;
+    const int32_t *s_key = nullptr, *s_val = nullptr, *s_tag = nullptr;
+    int64_t ns = 0;
+    int n_inst = 1;
+};
 
 // -------------------------------------------------------------------- plan
 struct Options {
@@ -52,8 +66,16 @@ struct Plan {
     DevBuf ss_rowptr;   // int64 [n_y + 1]
     DevBuf ss_col;      // int32 [n_s_sparse], z ids ascending per row
     DevBuf bm_row_of_y; // int32 [n_y], bitmap row or -1
-    DevBuf ss_bits;     // uint32 [n_y_bitmap][zw]
-    int64_t zw = 0;     // words per z bitmap
+    DevBuf bm_off;      // int64 [n_y_bitmap + 1]: first word of each bitmap row in ss_bits
+    DevBuf ss_bits;     // uint32, bitmap row b covers the z window of its instance
+    int64_t zw = 0;     // words of the widest z window
+    // batches: per-instance ranges (n_inst + 1 entries) and the instance of each x
+    int n_inst = 1;
+    DevBuf x_tag;       // int32 [n_x] (batches only)
+    DevBuf inst_x_lo;   // int64 [n_inst + 1]: x ids of instance i are [lo[i], lo[i+1])
+    DevBuf inst_z_lo;   // int64 [n_inst + 1]: z ids
+    DevBuf inst_zd_lo;  // int64 [n_inst + 1]: dense z indices
+    std::vector<int64_t> h_inst_x_lo, h_inst_z_lo, h_inst_zd_lo;
     // S_dense
     DevBuf zd_list;     // int32 [n_zd]: dense index -> z id (ascending)
     DevBuf kidx_of_y;   // int32 [n_y]: y id -> K index or -1
@@ -102,9 +124,7 @@ struct Ctx {
     Options opt;
 };
 
-Plan* build_plan(const Ctx& ctx, const int32_t* r_key, const int32_t* r_val, int64_t nr,
-                 const int32_t* s_key, const int32_t* s_val, int64_t ns, int64_t theta_z,
-                 cudaStream_t s);
+Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStream_t s);
 
 // Output of a join over an x-id range: counts pass + scan + emit pass.
 // kind 0 = project, 1 = count. Returns the number of pairs; writes only when
@@ -120,6 +140,11 @@ void dense_ec(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int 
               int32_t* d_cnt, cudaStream_t s);
 void dense_build_operands(const Ctx& ctx, Plan& p, const uint64_t* s_keys_u64, const uint32_t* s_keys_u32,
                           int64_t n_s, int bz, const int32_t* zd_index, cudaStream_t s);
+
+// Batches (batch.cu): plan over n_inst instances; per-instance pair counts
+// after a join over all x of that plan.
+Plan* build_batch_plan(const Ctx& ctx, int n_inst, const dim3_instance* inst, int64_t theta_z, cudaStream_t s);
+void batch_instance_counts(const Plan& p, int64_t* host_counts, cudaStream_t s);
 
 // Value mapping with all scratch in a fixed device array (noalloc.cu).
 void map_noalloc(const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,

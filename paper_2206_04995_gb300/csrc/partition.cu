@@ -102,8 +102,47 @@ __global__ void k_compact(const K* in, int64_t n, const int32_t* flag, const int
     GRID_STRIDE(i, n) if (flag[i]) out[pos[i]] = in[i];
 }
 
-__global__ void k_wide_flags(const int64_t* rowptr, int64_t n_rows, int64_t min_len, int32_t* flag) {
-    GRID_STRIDE(r, n_rows) flag[r] = (rowptr[r + 1] - rowptr[r]) >= min_len ? 1 : 0;
+// word window of instance t: [floor32(z_lo[t]), z_lo[t + 1])
+__device__ __forceinline__ int64_t window_words(const int64_t* z_lo, int t) {
+    const int64_t lo = z_lo[t] & ~int64_t(31);
+    return (z_lo[t + 1] - lo + 31) >> 5;
+}
+
+// Wide S_sparse rows: flag and words of the bitmap of every wide row.
+__global__ void k_wide_rows(const int64_t* rowptr, int64_t n_rows, const int32_t* y_tag, const int64_t* z_lo,
+                            int64_t fixed_min, int64_t mult, int32_t* flag, int64_t* words) {
+    GRID_STRIDE(r, n_rows) {
+        const int t = y_tag ? y_tag[r] : 0;
+        const int64_t ww = window_words(z_lo, t);
+        const int64_t thr = fixed_min >= 0 ? fixed_min * mult : max64(ww, 8) * mult;
+        const bool wide = (rowptr[r + 1] - rowptr[r]) >= max64(thr, 1);
+        flag[r] = wide ? 1 : 0;
+        words[r] = wide ? ww : 0;
+    }
+}
+
+// bm_off[b] = first word of wide row b (b = position among the flagged rows)
+__global__ void k_row_offsets(const int32_t* flag, const int64_t* pos, const int64_t* wpos, int64_t n, int64_t* off) {
+    GRID_STRIDE(r, n + 1) {
+        if (r == n) off[pos[n]] = wpos[n];
+        else if (flag[r]) off[pos[r]] = wpos[r];
+    }
+}
+
+// per-instance id ranges of a tag array sorted ascending: lo[t] = first index with tag >= t
+__global__ void k_tag_ranges(const int32_t* tags, int64_t n, int n_inst, int64_t* lo) {
+    GRID_STRIDE(t, (int64_t)n_inst + 1) {
+        int64_t a = 0, b = n;
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if (tags[m] < t) a = m + 1; else b = m;
+        }
+        lo[t] = a;
+    }
+}
+
+__global__ void k_gather_tags(const int32_t* idx, int64_t n, const int32_t* tag_of, int32_t* out) {
+    GRID_STRIDE(i, n) out[i] = tag_of[idx[i]];
 }
 
 __global__ void k_index_from_flags(const int32_t* flag, const int64_t* pos, int64_t n, int32_t* idx) {
@@ -113,13 +152,15 @@ __global__ void k_index_from_flags(const int32_t* flag, const int64_t* pos, int6
 // bitmap rows of the wide S_sparse rows
 template <typename K>
 __global__ void k_fill_row_bits(const K* keys, int64_t n, int bz, K zmask, const int32_t* row_of_y,
-                                uint32_t* bits, int64_t zw) {
+                                const int64_t* bm_off, const int32_t* y_tag, const int64_t* z_lo, uint32_t* bits) {
     GRID_STRIDE(i, n) {
         const K k = keys[i];
-        const int32_t b = row_of_y[(int64_t)(k >> bz)];
+        const int64_t y = (int64_t)(k >> bz);
+        const int32_t b = row_of_y[y];
         if (b >= 0) {
-            const int64_t z = (int64_t)(k & zmask);
-            atomicOr(&bits[(int64_t)b * zw + (z >> 5)], 1u << (z & 31));
+            const int t = y_tag ? y_tag[y] : 0;
+            const int64_t z = (int64_t)(k & zmask) - (z_lo[t] & ~int64_t(31));
+            atomicOr(&bits[bm_off[b] + (z >> 5)], 1u << (z & 31));
         }
     }
 }
@@ -196,7 +237,8 @@ static void build_r_side(Plan& p, const int32_t* rx_id, const int32_t* ry_id, in
 // S side: everything that depends on the distinct S tuples sorted by (y, z).
 template <typename K>
 static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const int32_t* sz_id, int64_t ns,
-                         int by, int bz, int64_t theta, cudaStream_t s) {
+                         int by, int bz, int64_t theta, const int32_t* y_tag_dev, const int32_t* z_tag_dev,
+                         cudaStream_t s) {
     const int64_t n_y = p.info.n_y, n_z = p.info.n_z, n_x = p.info.n_x;
     const K zmask = (K)((K(1) << bz) - 1);
     SortedPairs<K> sp;
@@ -255,6 +297,27 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
         DIM3_LAUNCHED();
     }
     p.info.n_z_dense = n_zd;
+    // dense index range of every instance
+    p.inst_zd_lo.alloc((size_t)(p.n_inst + 1) * 8, s);
+    p.h_inst_zd_lo.assign(p.n_inst + 1, 0);
+    if (p.n_inst > 1 && n_zd > 0) {
+        DevBuf zd_tag;
+        zd_tag.alloc((size_t)n_zd * 4, s);
+        k_gather_tags<<<grid_for(n_zd), kThreads, 0, s>>>(p.zd_list.as<int32_t>(), n_zd, z_tag_dev,
+                                                           zd_tag.as<int32_t>());
+        DIM3_LAUNCHED();
+        k_tag_ranges<<<grid_for(p.n_inst + 1), kThreads, 0, s>>>(zd_tag.as<int32_t>(), n_zd, p.n_inst,
+                                                                  p.inst_zd_lo.as<int64_t>());
+        DIM3_LAUNCHED();
+        DIM3_CUDA(cudaMemcpyAsync(p.h_inst_zd_lo.data(), p.inst_zd_lo.p, (size_t)(p.n_inst + 1) * 8,
+                                  cudaMemcpyDeviceToHost, s));
+        DIM3_CUDA(cudaStreamSynchronize(s));
+    } else {
+        for (int t = 1; t <= p.n_inst; ++t) p.h_inst_zd_lo[t] = n_zd;
+        DIM3_CUDA(cudaMemcpyAsync(p.inst_zd_lo.p, p.h_inst_zd_lo.data(), (size_t)(p.n_inst + 1) * 8,
+                                  cudaMemcpyHostToDevice, s));
+        DIM3_CUDA(cudaStreamSynchronize(s));
+    }
 
     // S_sparse: the distinct tuples of sparse z, still sorted by (y, z)
     DevBuf sflag, spos, skeys;
@@ -283,37 +346,55 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
     }
     rowptr_sorted<K>(skeys.as<K>(), n_ss, bz, n_y, p.ss_rowptr.as<int64_t>(), s);
 
-    // wide S_sparse rows held as z-bitmaps (|Z|/32 words per row)
-    p.zw = ceil_div(std::max<int64_t>(n_z, 1), 32);
-    int64_t min_len = p.opt.bitmap_row_min >= 0 ? p.opt.bitmap_row_min : std::max<int64_t>(p.zw, 8);
+    // wide S_sparse rows held as z-bitmaps over the z window of their
+    // instance (all of Z for a single instance): a row is wide when it holds
+    // at least max(8, window words) z, times a factor that doubles until the
+    // bitmaps fit 4 GiB
+    const int32_t* y_tag = p.n_inst > 1 ? y_tag_dev : nullptr;
+    p.zw = 1;
+    for (int t = 0; t < p.n_inst; ++t) {
+        const int64_t lo = p.h_inst_z_lo[t] & ~int64_t(31);
+        p.zw = std::max<int64_t>(p.zw, ceil_div(p.h_inst_z_lo[t + 1] - lo, 32));
+    }
     p.bm_row_of_y.alloc((size_t)std::max<int64_t>(n_y, 1) * 4, s);
-    int64_t n_bm = 0;
+    int64_t n_bm = 0, n_words = 0;
     if (n_y > 0) {
-        DevBuf yflag, ypos;
+        DevBuf yflag, ypos, words, wpos;
         yflag.alloc((size_t)n_y * 4, s);
         ypos.alloc((size_t)(n_y + 1) * 8, s);
-        // bound the bitmap memory: raise the threshold until the rows fit 4 GiB
+        words.alloc((size_t)n_y * 8, s);
+        wpos.alloc((size_t)(n_y + 1) * 8, s);
         const int64_t budget_words = (int64_t(4) << 30) / 4;
-        for (;;) {
-            k_wide_flags<<<grid_for(n_y), kThreads, 0, s>>>(p.ss_rowptr.as<int64_t>(), n_y, std::max<int64_t>(min_len, 1),
-                                                             yflag.as<int32_t>());
+        for (int64_t mult = 1;; mult *= 2) {
+            k_wide_rows<<<grid_for(n_y), kThreads, 0, s>>>(p.ss_rowptr.as<int64_t>(), n_y, y_tag,
+                                                            p.inst_z_lo.as<int64_t>(), p.opt.bitmap_row_min, mult,
+                                                            yflag.as<int32_t>(), words.as<int64_t>());
             DIM3_LAUNCHED();
-            exclusive_scan_i32_to_i64(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y, s);
-            n_bm = read_i64(ypos.as<int64_t>() + n_y, s);
-            if (n_bm * p.zw <= budget_words) break;
-            min_len = std::max<int64_t>(min_len * 2, 1);
+            exclusive_scan_i64(words.as<int64_t>(), wpos.as<int64_t>(), n_y, s);
+            n_words = read_i64(wpos.as<int64_t>() + n_y, s);
+            if (n_words <= budget_words) break;
         }
+        exclusive_scan_i32_to_i64(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y, s);
+        n_bm = read_i64(ypos.as<int64_t>() + n_y, s);
         k_index_from_flags<<<grid_for(n_y), kThreads, 0, s>>>(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y,
                                                                p.bm_row_of_y.as<int32_t>());
         DIM3_LAUNCHED();
+        p.bm_off.alloc((size_t)(n_bm + 1) * 8, s);
+        k_row_offsets<<<grid_for(n_y + 1), kThreads, 0, s>>>(yflag.as<int32_t>(), ypos.as<int64_t>(),
+                                                              wpos.as<int64_t>(), n_y, p.bm_off.as<int64_t>());
+        DIM3_LAUNCHED();
+    } else {
+        p.bm_off.alloc(8, s);
+        DIM3_CUDA(cudaMemsetAsync(p.bm_off.p, 0, 8, s));
     }
     p.info.n_y_bitmap = n_bm;
-    p.ss_bits.alloc((size_t)std::max<int64_t>(n_bm * p.zw, 1) * 4, s);
+    p.ss_bits.alloc((size_t)std::max<int64_t>(n_words, 1) * 4, s);
     if (n_bm > 0) {
-        DIM3_CUDA(cudaMemsetAsync(p.ss_bits.p, 0, (size_t)(n_bm * p.zw) * 4, s));
+        DIM3_CUDA(cudaMemsetAsync(p.ss_bits.p, 0, (size_t)n_words * 4, s));
         k_fill_row_bits<K><<<grid_for(n_ss), kThreads, 0, s>>>(skeys.as<K>(), n_ss, bz, zmask,
-                                                                p.bm_row_of_y.as<int32_t>(), p.ss_bits.as<uint32_t>(),
-                                                                p.zw);
+                                                                p.bm_row_of_y.as<int32_t>(), p.bm_off.as<int64_t>(),
+                                                                y_tag, p.inst_z_lo.as<int64_t>(),
+                                                                p.ss_bits.as<uint32_t>());
         DIM3_LAUNCHED();
     }
 
@@ -340,50 +421,82 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
     }
 }
 
-Plan* build_plan(const Ctx& ctx, const int32_t* r_key, const int32_t* r_val, int64_t nr, const int32_t* s_key,
-                 const int32_t* s_val, int64_t ns, int64_t theta_z, cudaStream_t s) {
+// lo[t] for t = 0..n_inst: first id whose instance is >= t (ids are ordered
+// by instance); a single instance gets {0, n}.
+static void instance_ranges(const int32_t* tag_dev, int64_t n, int n_inst, DevBuf& lo_dev, std::vector<int64_t>& lo,
+                            cudaStream_t s) {
+    lo_dev.alloc((size_t)(n_inst + 1) * 8, s);
+    lo.assign(n_inst + 1, 0);
+    if (n_inst > 1 && n > 0) {
+        k_tag_ranges<<<grid_for(n_inst + 1), kThreads, 0, s>>>(tag_dev, n, n_inst, lo_dev.as<int64_t>());
+        DIM3_LAUNCHED();
+        DIM3_CUDA(cudaMemcpyAsync(lo.data(), lo_dev.p, (size_t)(n_inst + 1) * 8, cudaMemcpyDeviceToHost, s));
+        DIM3_CUDA(cudaStreamSynchronize(s));
+    } else {
+        for (int t = 1; t <= n_inst; ++t) lo[t] = n;
+        DIM3_CUDA(cudaMemcpyAsync(lo_dev.p, lo.data(), (size_t)(n_inst + 1) * 8, cudaMemcpyHostToDevice, s));
+        DIM3_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStream_t s) {
     PhaseScope phase(ctx.stats, PH_PARTITION, s);
     std::unique_ptr<Plan> p(new Plan());
+    const int64_t nr = in.nr, ns = in.ns;
+    const bool batch = in.n_inst > 1;
     p->stream = s;
     p->device = ctx.device;
     p->opt = ctx.opt;
+    p->n_inst = std::max(in.n_inst, 1);
     p->info.n_r = nr;
     p->info.n_s = ns;
 
-    DevBuf sy_id, sz_id, ry_id, rx_id;
+    DevBuf sy_id, sz_id, ry_id, rx_id, y_tag, z_tag;
     sy_id.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
     sz_id.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
     ry_id.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
     rx_id.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+    if (batch) {
+        y_tag.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+        z_tag.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+        p->x_tag.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+    }
     {
         // y from S.y; R tuples whose y is absent from S.y get id -1 (dropped)
         ValueMap ymap;
         p->dict_y.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-        build_value_map(s_key, nullptr, ns, ymap, sy_id.as<int32_t>(), p->dict_y.as<int32_t>(), s);
+        build_value_map(in.s_key, in.s_tag, p->n_inst, nullptr, ns, ymap, sy_id.as<int32_t>(),
+                        p->dict_y.as<int32_t>(), y_tag.as<int32_t>(), s);
         p->info.n_y = ymap.n_distinct;
-        probe_value_map(ymap, r_key, nr, ry_id.as<int32_t>(), s);
+        probe_value_map(ymap, in.r_key, in.r_tag, nr, ry_id.as<int32_t>(), s);
     }
     {
         ValueMap xmap;
         p->dict_x.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
-        build_value_map(r_val, ry_id.as<int32_t>(), nr, xmap, rx_id.as<int32_t>(), p->dict_x.as<int32_t>(), s);
+        build_value_map(in.r_val, in.r_tag, p->n_inst, ry_id.as<int32_t>(), nr, xmap, rx_id.as<int32_t>(),
+                        p->dict_x.as<int32_t>(), p->x_tag.as<int32_t>(), s);
         p->info.n_x = xmap.n_distinct;
     }
     {
         ValueMap zmap;
         p->dict_z.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-        build_value_map(s_val, nullptr, ns, zmap, sz_id.as<int32_t>(), p->dict_z.as<int32_t>(), s);
+        build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(),
+                        p->dict_z.as<int32_t>(), z_tag.as<int32_t>(), s);
         p->info.n_z = zmap.n_distinct;
     }
+    instance_ranges(p->x_tag.as<int32_t>(), p->info.n_x, p->n_inst, p->inst_x_lo, p->h_inst_x_lo, s);
+    instance_ranges(z_tag.as<int32_t>(), p->info.n_z, p->n_inst, p->inst_z_lo, p->h_inst_z_lo, s);
     const int bx = bits_for(p->info.n_x), by = bits_for(p->info.n_y), bz = bits_for(p->info.n_z);
     if (bx + by <= 32)
         build_r_side<uint32_t>(*p, rx_id.as<int32_t>(), ry_id.as<int32_t>(), nr, bx, by, s);
     else
         build_r_side<uint64_t>(*p, rx_id.as<int32_t>(), ry_id.as<int32_t>(), nr, bx, by, s);
     if (by + bz <= 32)
-        build_s_side<uint32_t>(ctx, *p, sy_id.as<int32_t>(), sz_id.as<int32_t>(), ns, by, bz, theta_z, s);
+        build_s_side<uint32_t>(ctx, *p, sy_id.as<int32_t>(), sz_id.as<int32_t>(), ns, by, bz, theta_z,
+                               y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
     else
-        build_s_side<uint64_t>(ctx, *p, sy_id.as<int32_t>(), sz_id.as<int32_t>(), ns, by, bz, theta_z, s);
+        build_s_side<uint64_t>(ctx, *p, sy_id.as<int32_t>(), sz_id.as<int32_t>(), ns, by, bz, theta_z,
+                               y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
     DIM3_CUDA(cudaStreamSynchronize(s));
     return p.release();
 }

@@ -40,7 +40,11 @@ struct XRowArgs {
     const int64_t* ss_rowptr;
     const int32_t* ss_col;
     const int32_t* bm_row_of_y;
+    const int64_t* bm_off;   // first word of each wide row's bitmap
     const uint32_t* ss_bits;
+    const int32_t* x_tag;    // instance of each x (batches) or null
+    const int64_t* z_lo;     // [n_inst + 1] z id range of each instance
+    const int64_t* zd_lo;    // [n_inst + 1] dense index range of each instance
     const uint32_t* d_bits;  // [n_rows][zdw] or null
     const int32_t* d_cnt;    // [n_rows][n_zd] or null
     int64_t zdw, n_zd;
@@ -122,15 +126,19 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
     const int64_t x = a.x_begin + xr;
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool tiled = a.tile_bits < a.n_z;
+    // z window of x's instance (all of Z for a single instance), from a
+    // 32-aligned start so that bitmap words line up with the wide rows' words
+    const int tg = a.x_tag ? a.x_tag[x] : 0;
+    const int64_t zb = a.z_lo[tg] & ~int64_t(31), ze = a.z_lo[tg + 1];
+    const bool tiled = a.tile_bits < ze - zb;
     int64_t total = 0;
     int64_t out_pos = 0;
     if (kEmit) {
         out_pos = a.off[xr];
         fill_range(a.out_x, out_pos, a.off[xr + 1], a.dict_x[x], a.vec_ok);
     }
-    for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += a.tile_bits) {
-        const int64_t zt1 = min64(zt0 + a.tile_bits, a.n_z);
+    for (int64_t zt0 = zb; zt0 < ze; zt0 += a.tile_bits) {
+        const int64_t zt1 = min64(zt0 + a.tile_bits, ze);
         const int tw = (int)((zt1 - zt0 + 31) >> 5);
         for (int w = tid; w < tw; w += kThreads) bm[w] = 0u;
         __syncthreads();
@@ -169,19 +177,20 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
             __syncthreads();
             const int nl = s_wc[kThreads / 32];
             if (nl > 0) {
-                const uint32_t* bits = a.ss_bits + (zt0 >> 5);
+                const uint32_t* bits = a.ss_bits + ((zt0 - zb) >> 5);
                 for (int w = tid; w < tw; w += kThreads) {
                     uint32_t acc = 0u;
-                    for (int i = 0; i < nl; ++i) acc |= __ldg(bits + (int64_t)s_list[i] * a.zw + w);
+                    for (int i = 0; i < nl; ++i) acc |= __ldg(bits + a.bm_off[s_list[i]] + w);
                     if (acc) bm[w] |= acc;
                 }
             }
             __syncthreads();
         }
-        // DenseEC result of this x (disjoint from the sparse z set)
+        // DenseEC result of this x (disjoint from the sparse z set), over the
+        // dense indices of x's instance
         if (a.n_zd > 0) {
             const uint32_t* drow = a.d_bits + xr * a.zdw;
-            for (int64_t w = tid; w < a.zdw; w += kThreads) {
+            for (int64_t w = (a.zd_lo[tg] >> 5) + tid; w < ((a.zd_lo[tg + 1] + 31) >> 5); w += kThreads) {
                 uint32_t word = drow[w];
                 while (word) {
                     const int b = __ffs(word) - 1;
@@ -345,7 +354,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
 #pragma unroll
                     for (int k = 0; k < G; ++k) acc[k] = 0u;
                     for (int i = 0; i < nl; ++i) {
-                        const uint32_t v = __ldg(bits + (int64_t)s_list[i] * a.zw + w);
+                        const uint32_t v = __ldg(bits + a.bm_off[s_list[i]] + w);
                         const int k = s_lk[i];
 #pragma unroll
                         for (int q = 0; q < G; ++q) acc[q] |= (k == q) ? v : 0u;
@@ -463,15 +472,17 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
     const int64_t x = a.x_begin + xr;
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool tiled = a.tile_bits < a.n_z;
+    const int tg = a.x_tag ? a.x_tag[x] : 0;
+    const int64_t zb = a.z_lo[tg], ze = a.z_lo[tg + 1];  // z window of x's instance
+    const bool tiled = a.tile_bits < ze - zb;
     int64_t total = 0;
     int64_t out_pos = 0;
     if (kEmit) {
         out_pos = a.off[xr];
         fill_range(a.out_x, out_pos, a.off[xr + 1], a.dict_x[x], a.vec_ok);
     }
-    for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += a.tile_bits) {
-        const int64_t zt1 = min64(zt0 + a.tile_bits, a.n_z);
+    for (int64_t zt0 = zb; zt0 < ze; zt0 += a.tile_bits) {
+        const int64_t zt1 = min64(zt0 + a.tile_bits, ze);
         const int tn = (int)(zt1 - zt0);
         for (int i = tid; i < tn; i += kThreads) ctr[i] = 0u;
         __syncthreads();
@@ -486,7 +497,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
         }
         if (a.n_zd > 0) {
             const int32_t* crow = a.d_cnt + xr * a.n_zd;
-            for (int64_t d = tid; d < a.n_zd; d += kThreads) {
+            for (int64_t d = a.zd_lo[tg] + tid; d < a.zd_lo[tg + 1]; d += kThreads) {
                 const int32_t c = crow[d];
                 const int32_t z = a.zd_list[d];
                 if (c > 0 && z >= zt0 && z < zt1) atomicAdd(&ctr[z - (int32_t)zt0], (uint32_t)c);
@@ -562,14 +573,18 @@ static XRowArgs make_args(const Plan& p, int64_t x_begin, int64_t rows, int kind
         const int64_t tw = std::min<int64_t>(p.zw, kMaxTileWords);
         a.tile_bits = tw * 32;
     } else {
-        a.tile_bits = std::min<int64_t>(std::max<int64_t>(p.info.n_z, 1), kMaxCntTile);
+        a.tile_bits = std::min<int64_t>(std::max<int64_t>(p.zw * 32, 1), kMaxCntTile);
     }
     a.r_rowptr = p.r_rowptr.as<int64_t>();
     a.r_col = p.r_col.as<int32_t>();
     a.ss_rowptr = p.ss_rowptr.as<int64_t>();
     a.ss_col = p.ss_col.as<int32_t>();
     a.bm_row_of_y = p.bm_row_of_y.as<int32_t>();
+    a.bm_off = p.bm_off.as<int64_t>();
     a.ss_bits = p.ss_bits.as<uint32_t>();
+    a.x_tag = p.n_inst > 1 ? p.x_tag.as<int32_t>() : nullptr;
+    a.z_lo = p.inst_z_lo.as<int64_t>();
+    a.zd_lo = p.inst_zd_lo.as<int64_t>();
     a.zdw = p.zdw;
     a.n_zd = p.info.n_z_dense;
     a.zd_list = p.zd_list.as<int32_t>();
@@ -600,7 +615,8 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
     PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
     if (kind == 0) {
         const size_t sm = bits_smem(a.tile_bits, emit);
-        const int grp = emit ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
+        // several rows per CTA share one z window, so batches use one row per CTA
+        const int grp = (emit && a.x_tag == nullptr) ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
         if (emit && grp > 1) {
             const size_t smg = (size_t)kWarps * kWarpStage * 4 + (size_t)grp * (size_t)(a.tile_bits / 32) * 4;
             const unsigned gg = (unsigned)ceil_div(a.n_rows, grp);

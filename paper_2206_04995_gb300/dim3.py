@@ -51,6 +51,12 @@ class PlanInfo(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class Instance(ctypes.Structure):
+    """dim3_instance: one instance of a batch (device column pointers)."""
+    _fields_ = [("r_key", ctypes.c_void_p), ("r_val", ctypes.c_void_p), ("nr", ctypes.c_int64),
+                ("s_key", ctypes.c_void_p), ("s_val", ctypes.c_void_p), ("ns", ctypes.c_int64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -94,6 +100,10 @@ def load(build_if_missing: bool = True):
             "dim3_plan_destroy": ([P], INT),
             "dim3_join_project": ([P, P, P, I64, P, P, I64, P, P, I64, ctypes.POINTER(I64), P], INT),
             "dim3_join_count": ([P, P, P, I64, P, P, I64, P, P, P, I64, ctypes.POINTER(I64), P], INT),
+            "dim3_batch_partition": ([P, INT, P, I32, ctypes.POINTER(P), ctypes.POINTER(PlanInfo), P], INT),
+            "dim3_plan_instance_ranges": ([P, P], INT),
+            "dim3_batch_join_project": ([P, INT, P, P, P, I64, P, ctypes.POINTER(I64), P], INT),
+            "dim3_batch_join_count": ([P, INT, P, P, P, P, I64, P, ctypes.POINTER(I64), P], INT),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -216,6 +226,67 @@ class Context:
         finally:
             plan.close()
 
+    # -------------------------------------------------------------- batches
+    def _instances(self, instances):
+        arr = (Instance * len(instances))()
+        for i, (rk, rv, sk, sv) in enumerate(instances):
+            rk, rv = _col(rk, self.device, "r_key"), _col(rv, self.device, "r_val")
+            sk, sv = _col(sk, self.device, "s_key"), _col(sv, self.device, "s_val")
+            if rk.numel() != rv.numel() or sk.numel() != sv.numel():
+                raise ValueError(f"instance {i}: column lengths differ")
+            arr[i] = Instance(rk.data_ptr() if rk.numel() else None, rv.data_ptr() if rv.numel() else None,
+                              rk.numel(), sk.data_ptr() if sk.numel() else None,
+                              sv.data_ptr() if sv.numel() else None, sk.numel())
+        return arr
+
+    def batch_partition(self, instances, theta_z: int = -1, stream=None) -> "Plan":
+        """A plan over a batch of (r_key, r_val, s_key, s_val) instances."""
+        arr = self._instances(instances)
+        h = ctypes.c_void_p()
+        info = PlanInfo()
+        _check(self._lib.dim3_batch_partition(self._h, len(instances), arr, int(theta_z), ctypes.byref(h),
+                                              ctypes.byref(info), _stream(self.device, stream)))
+        return Plan(self, h, info, stream, n_inst=len(instances))
+
+    def batch_join_project(self, instances, out_x=None, out_z=None, stream=None):
+        """Eq. 1 for every instance of a batch in one pass: (out_x, out_z,
+        per-instance pair counts); instance t's pairs follow instance t-1's."""
+        return self._batch(False, instances, out_x, out_z, None, stream)
+
+    def batch_join_count(self, instances, out_x=None, out_z=None, out_c=None, stream=None):
+        return self._batch(True, instances, out_x, out_z, out_c, stream)
+
+    def _batch(self, counts, instances, out_x, out_z, out_c, stream):
+        if out_x is None:
+            plan = self.batch_partition(instances, stream=stream)
+            try:
+                res = plan.join_count(stream=stream) if counts else plan.join_project(stream=stream)
+                rc = plan.row_counts(stream=stream)
+                lo = plan.instance_ranges()
+                cs = torch.cumsum(torch.cat([torch.zeros(1, dtype=torch.int64, device=rc.device), rc]), 0)
+                at = cs[torch.tensor(lo, device=rc.device)]
+                per = (at[1:] - at[:-1]).tolist()
+                return (*res, per)
+            finally:
+                plan.close()
+        arr = self._instances(instances)
+        cap = min(out_x.numel(), out_z.numel(), out_c.numel() if counts else out_x.numel())
+        per = (ctypes.c_int64 * len(instances))()
+        cnt = ctypes.c_int64()
+        st = _stream(self.device, stream)
+        if counts:
+            rc = self._lib.dim3_batch_join_count(self._h, len(instances), arr, _ptr(out_x), _ptr(out_z), _ptr(out_c),
+                                                 cap, per, ctypes.byref(cnt), st)
+        else:
+            rc = self._lib.dim3_batch_join_project(self._h, len(instances), arr, _ptr(out_x), _ptr(out_z), cap, per,
+                                                   ctypes.byref(cnt), st)
+        if rc == DIM3_ERR_CAPACITY:
+            raise Dim3Error(rc, f"capacity {cap} < result {cnt.value}")
+        _check(rc)
+        n = cnt.value
+        res = (out_x[:n], out_z[:n], out_c[:n]) if counts else (out_x[:n], out_z[:n])
+        return (*res, list(per))
+
     def _join_call(self, counts, r_key, r_val, s_key, s_val, out_x, out_z, out_c, stream):
         r_key, r_val = _col(r_key, self.device, "r_key"), _col(r_val, self.device, "r_val")
         s_key, s_val = _col(s_key, self.device, "s_key"), _col(s_val, self.device, "s_val")
@@ -242,11 +313,18 @@ class Context:
 class Plan:
     """A partitioned input resident on the device (``dim3_plan``)."""
 
-    def __init__(self, ctx: Context, handle, info: PlanInfo, stream=None):
+    def __init__(self, ctx: Context, handle, info: PlanInfo, stream=None, n_inst: int = 1):
         self.ctx = ctx
         self._h = handle
         self._info = info
         self.stream = stream
+        self.n_inst = n_inst
+
+    def instance_ranges(self) -> list:
+        """x-id range [lo[t], lo[t+1]) of every instance of a batch plan."""
+        lo = (ctypes.c_int64 * (self.n_inst + 1))()
+        _check(self.ctx._lib.dim3_plan_instance_ranges(self._h, lo))
+        return list(lo)
 
     @property
     def info(self) -> dict:
