@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 
 METRIC = "dedup (x,z) pairs/s on 1 GB300 vs plain path; served p50/p99 latency"
 UNIT = "pairs/s"
-WORKLOADS = ("two_table_1m_zipf1", "self_20k", "chung_lu_1m_4m", "dense_16k")
+WORKLOADS = ("two_table_1m_zipf1", "self_20k", "chung_lu_1m_4m", "dense_16k", "batch256")
 # fp8 (f8f6f4) dense tensor rate = 2 x bf16 (nominal 4.5 vs 2.25 PFLOP/s)
 FP8_PER_BF16 = 2.0
 
@@ -220,6 +220,9 @@ def main():
         run_reference(args, rank, world)
         return
     assert args.warmup >= 3 or os.environ.get("DIM3_BENCH_ALLOW_SHORT"), "at least 3 warm-up steps"
+    if args.workload == "batch256":
+        run_batch(args, rank, world, local_rank)
+        return
 
     import torch
 
@@ -358,6 +361,136 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    ctx.close()
+
+
+def run_batch(args, rank, world, local_rank):
+    """256 independent two-table instances (log-uniform sizes): one step is
+    ONE dim3_batch_join_project call over all of them; the same instances run
+    one call each (the plain path) beside it for the ratio."""
+    import torch
+
+    import gen
+    import paper_2206_04995_gb300 as dim3
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    insts = gen.config4_batch(seed=3 + 1000 * rank)
+    cols = [[torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(dev)
+             for a in (i.r_key, i.r_val, i.s_key, i.s_val)] for i in insts]
+    ctx = dim3.Context(local_rank)
+    plan = ctx.batch_partition(cols)
+    info = plan.info
+    out_p = int(plan.row_counts().sum().item())
+    plan.close()
+    out_x = torch.empty(out_p, dtype=torch.int32, device=dev)
+    out_z = torch.empty(out_p, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def batched():
+        x, _, _ = ctx.batch_join_project(cols, out_x=out_x, out_z=out_z)
+        return x.numel()
+
+    # the plain path: one dim3_join_project per instance into the same buffers
+    sizes = []
+    for c in cols:
+        p = ctx.partition(*c)
+        sizes.append(int(p.row_counts().sum().item()))
+        p.close()
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+
+    def plain():
+        n = 0
+        for t, c in enumerate(cols):
+            x, _ = ctx.join_project(*c, out_x=out_x[offs[t]:offs[t + 1]], out_z=out_z[offs[t]:offs[t + 1]])
+            n += x.numel()
+        return n
+
+    def timed(fn, steps):
+        ms = []
+        for k in range(steps):
+            flush.fill_(k)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            assert fn() == out_p
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    for _ in range(args.warmup):
+        batched()
+        plain()
+    torch.cuda.synchronize()
+    plain_ms = timed(plain, max(1, min(args.steps, 3)))
+    ctx.set_option(dim3.OPT_TIMING, 1)
+    ctx.timing(reset=True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = dim3.launch_count()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    batch_ms = timed(batched, args.steps)
+    t_wall = time.perf_counter() - t_wall
+    launches = dim3.launch_count() - l0
+    clocks = sampler.stop()
+    tm = ctx.timing()
+    ctx.set_option(dim3.OPT_TIMING, 0)
+    busy = sum(batch_ms) / 1e3
+    value = out_p * args.steps / busy
+    plain_value = out_p * len(plain_ms) / (sum(plain_ms) / 1e3)
+    peaks = measured_peaks()
+    emit_ms, emit_n = tm["sparse_emit"]
+    emit_s = emit_ms / 1e3 / max(emit_n, 1)
+    alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
+    achieved = alg_bytes / emit_s / 1e9
+    e2e = None
+    if not args.no_e2e:
+        h_in = [[c.cpu().pin_memory() for c in cc] for cc in cols]
+        h_x = torch.empty(out_p, dtype=torch.int32, pin_memory=True)
+        h_z = torch.empty(out_p, dtype=torch.int32, pin_memory=True)
+
+        def e2e_step():
+            for d, h in zip(cols, h_in):
+                for dd, hh in zip(d, h):
+                    dd.copy_(hh, non_blocking=True)
+            x, z, _ = ctx.batch_join_project(cols, out_x=out_x, out_z=out_z)
+            h_x.copy_(x, non_blocking=True)
+            h_z.copy_(z, non_blocking=True)
+            return x.numel()
+
+        e2e_ms = timed(e2e_step, max(1, min(args.steps, args.e2e_steps)))
+        e2e = {"value": out_p * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": sum(i.nr + i.ns for i in insts) * 8, "d2h_bytes_per_step": 8 * out_p,
+               "host_memory": "pinned", "ms_per_step": sum(e2e_ms) / len(e2e_ms)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        small = sorted(insts, key=lambda i: i.nr)[:: max(1, len(insts) // 16)][:16]
+        import oracle
+
+        oracle.build()
+        t0 = time.perf_counter()
+        n = sum(oracle.join_project(i.r_key, i.r_val, i.s_key, i.s_val)[0].size for i in small)
+        dt = time.perf_counter() - t0
+        cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(small)} of the 256 instances (every 16th by size), whole; {n} pairs in {dt:.2f} s"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(batch_ms) / len(batch_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "batch256", "n_inst": len(insts), "tuples": int(sum(i.nr + i.ns for i in insts)),
+                       "out_p": out_p, "out_j": info["out_j"], "plain_pairs_per_s": plain_value,
+                       "plain_ms_per_step": sum(plain_ms) / len(plain_ms), "batched_over_plain": value / plain_value,
+                       "l2": "flushed between steps (256 MiB write outside the step events)"},
+            "roofline": {"bound": "hbm", "kernel": "k_xrow_bits<emit> over all instances", "achieved": achieved,
+                         "peak": peaks["hbm"], "unit": "GB/s", "frac": achieved / peaks["hbm"],
+                         "peak_source": peaks["source"], "traffic": None, "alg_bytes_per_launch": alg_bytes,
+                         "launch_ms": emit_s * 1e3},
+            "phase_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in tm.items() if v[1]},
+            "wall_s": t_wall, "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }), flush=True)
     ctx.close()
 
 
