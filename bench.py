@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--theta-z", type=int, default=None, help="dense iff m_z >= theta (default: library's)")
     ap.add_argument("--dense-variant", type=int, default=None, help="0 auto, 1 tensor core, 2 popc, 3 probe")
+    ap.add_argument("--opt", action="append", default=[],
+                    help="library option KEY=VALUE (dim3_option number), e.g. 6=1 for one x row per emitting CTA")
     ap.add_argument("--serve-queries", type=int, default=200)
     ap.add_argument("--serve-max-tuples", type=int, default=200_000)
     ap.add_argument("--no-e2e", action="store_true")
@@ -159,6 +161,20 @@ def traffic_for(kernel: str):
         return None, None
 
 
+def reduce_over_ranks(dist, busy_s: float, pairs: int, device):
+    """Whole-job numbers of N replicas: the slowest rank's busy time (max) and
+    the pairs all ranks produced (sum). dist is torch.distributed or None."""
+    if dist is None:
+        return busy_s, float(pairs)
+    import torch
+
+    t = torch.tensor([busy_s, float(pairs)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(t[1])
+
+
 def cpu_baseline(inst, target_s: float, rng_seed: int = 5):
     """The oracle as it stands, single-threaded, on the rows of a random x
     sample sized to take about target_s seconds."""
@@ -252,6 +268,9 @@ def main():
         ctx.set_option(dim3.OPT_THETA_Z, theta)
     if variant is not None:
         ctx.set_option(dim3.OPT_DENSE_VARIANT, variant)
+    for kv in args.opt:
+        k, v = kv.split("=")
+        ctx.set_option(int(k), int(v))
 
     # size the output once (plan path), then time the one-call path
     plan = ctx.partition(*cols)
@@ -301,14 +320,7 @@ def main():
     busy_s = sum(step_ms) / 1e3
 
     total_pairs = out_p * args.steps
-    if dist:
-        t = torch.tensor([busy_s, float(total_pairs)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        busy_max, pairs_all = float(mx[0]), float(t[1])
-    else:
-        busy_max, pairs_all = busy_s, float(total_pairs)
+    busy_max, pairs_all = reduce_over_ranks(dist, busy_s, total_pairs, dev)
     value = pairs_all / busy_max
 
     # roofline of the dominant kernel: SparseBMM + union + compaction (emitting

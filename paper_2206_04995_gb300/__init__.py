@@ -14,6 +14,7 @@ from .dim3 import (  # noqa: F401
     DENSE_TC,
     OPT_BITMAP_ROW_MIN,
     OPT_DENSE_VARIANT,
+    OPT_EMIT_ROWS,
     OPT_LIGHT_ROW_MAX,
     OPT_THETA_Z,
     OPT_TIMING,

@@ -72,6 +72,10 @@ struct Plan {
     // batches: per-instance ranges (n_inst + 1 entries) and the instance of each x
     int n_inst = 1;
     DevBuf x_tag;       // int32 [n_x] (batches only)
+    DevBuf y_tag;       // int32 [n_y] (batches only)
+    // z-tiled SparseBMM: start of every tile in each S_sparse row, per pass kind
+    DevBuf tile_ptr[2];
+    int64_t tile_ptr_bits[2] = {0, 0}, tile_cols[2] = {0, 0};
     DevBuf inst_x_lo;   // int64 [n_inst + 1]: x ids of instance i are [lo[i], lo[i+1])
     DevBuf inst_z_lo;   // int64 [n_inst + 1]: z ids
     DevBuf inst_zd_lo;  // int64 [n_inst + 1]: dense z indices

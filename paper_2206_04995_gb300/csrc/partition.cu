@@ -497,6 +497,7 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
     else
         build_s_side<uint64_t>(ctx, *p, sy_id.as<int32_t>(), sz_id.as<int32_t>(), ns, by, bz, theta_z,
                                y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
+    if (batch) p->y_tag = std::move(y_tag);
     DIM3_CUDA(cudaStreamSynchronize(s));
     return p.release();
 }

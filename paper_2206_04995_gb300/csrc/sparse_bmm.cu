@@ -28,7 +28,7 @@ namespace dimcube {
 
 constexpr int kWarps = kThreads / 32;
 constexpr int kWarpStage = 1040;        // staged output values per warp (1024 + alignment shift, 16-byte multiple)
-constexpr int64_t kMaxTileWords = 24 * 1024;   // 96 KiB bitmap tile = 786,432 z
+constexpr int64_t kMaxTileWords = 16 * 1024;   // 64 KiB bitmap tile = 524,288 z (two emitting CTAs per SM)
 constexpr int kCntChunk = 4096;         // z per compaction chunk (count mode)
 constexpr int64_t kMaxCntTile = 16 * 1024;     // counters per tile (64 KiB)
 
@@ -45,6 +45,8 @@ struct XRowArgs {
     const int32_t* x_tag;    // instance of each x (batches) or null
     const int64_t* z_lo;     // [n_inst + 1] z id range of each instance
     const int64_t* zd_lo;    // [n_inst + 1] dense index range of each instance
+    const int64_t* tile_ptr; // tiled: [n_y][tile_cols] start of every z tile in each S_sparse row
+    int64_t tile_cols;
     const uint32_t* d_bits;  // [n_rows][zdw] or null
     const int32_t* d_cnt;    // [n_rows][n_zd] or null
     int64_t zdw, n_zd;
@@ -112,6 +114,102 @@ __device__ __forceinline__ void flush_warp(int32_t* dst, const int32_t* st, int 
     }
 }
 
+// Write the z values of the set bits of one 32-word group (1024 z ids, lane j
+// holding word j, excl = set bits in words < j) to st[sh + ...] in z order.
+// Dense groups: lane l reads dictionary entry 32 j + l while word j is
+// broadcast, so every load is one 128-byte line; only nonzero words are
+// visited. Sparse groups: every lane writes its own word's few bits.
+__device__ __forceinline__ void compact_group(int32_t* st, int sh, uint32_t word, int excl, int total_g,
+                                              const int32_t* dz, int lane, unsigned lt) {
+    constexpr int kSparseGroup = 64;
+    if (total_g <= kSparseGroup) {
+        int pos = sh + excl;
+        uint32_t wv = word;
+        while (wv) {
+            const int b = __ffs(wv) - 1;
+            wv &= wv - 1;
+            st[pos++] = __ldg(dz + (lane << 5) + b);
+        }
+        return;
+    }
+    unsigned m = __ballot_sync(kFull, word != 0u);
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t wj = __shfl_sync(kFull, word, j);
+        const int pj = __shfl_sync(kFull, excl, j);
+        if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = __ldg(dz + (j << 5) + lane);
+    }
+}
+
+// Zero bm[0, n) with 16-byte stores (bm is 16-byte aligned).
+__device__ __forceinline__ void clear_words(uint32_t* bm, int n) {
+    const int n4 = n >> 2;
+    uint4* b4 = reinterpret_cast<uint4*>(bm);
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) b4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = (n4 << 2) + threadIdx.x; i < n; i += blockDim.x) bm[i] = 0u;
+}
+
+// This thread's share of the set bits of bm[0, n), read 16 bytes at a time.
+__device__ __forceinline__ int64_t popc_words(const uint32_t* bm, int n) {
+    const int n4 = n >> 2;
+    const uint4* b4 = reinterpret_cast<const uint4*>(bm);
+    int64_t c = 0;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        const uint4 v = b4[i];
+        c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    }
+    for (int i = (n4 << 2) + threadIdx.x; i < n; i += blockDim.x) c += __popc(bm[i]);
+    return c;
+}
+
+// Stage the z ids of the set bits of one 32-word group (lane j holds word j,
+// excl = set bits in words < j) at dst[0 ..] in id order.
+__device__ __forceinline__ void stage_group_ids(int32_t* dst, uint32_t word, int excl, int32_t zbase, int lane,
+                                                unsigned lt, int total_g) {
+    if (total_g <= 64) {
+        int pos = excl;
+        uint32_t wv = word;
+        while (wv) {
+            const int b = __ffs(wv) - 1;
+            wv &= wv - 1;
+            dst[pos++] = zbase + (lane << 5) + b;
+        }
+        return;
+    }
+    unsigned m = __ballot_sync(kFull, word != 0u);
+    while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1;
+        const uint32_t wj = __shfl_sync(kFull, word, j);
+        const int pj = __shfl_sync(kFull, excl, j);
+        if ((wj >> lane) & 1u) dst[pj + __popc(wj & lt)] = zbase + (j << 5) + lane;
+    }
+}
+
+// flush_warp for a stage of z ids: dst[t] = dict_z[st[t]] for t in [sh, sh + cnt).
+__device__ __forceinline__ void flush_warp_ids(int32_t* dst, const int32_t* st, int sh, int cnt,
+                                               const int32_t* __restrict__ dict_z, bool vec_ok) {
+    const int end = sh + cnt;
+    const int nv = (end + 3) >> 2;
+    const int lane = threadIdx.x & 31;
+    for (int v = lane; v < nv; v += 32) {
+        const int s = v << 2;
+        if (vec_ok && s >= sh && s + 4 <= end) {
+            const int4 id = *reinterpret_cast<const int4*>(st + s);
+            const int4 val = make_int4(__ldg(dict_z + id.x), __ldg(dict_z + id.y), __ldg(dict_z + id.z),
+                                       __ldg(dict_z + id.w));
+            __stcs(reinterpret_cast<int4*>(dst + s), val);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int t = s + j;
+                if (t >= sh && t < end) __stcs(dst + t, __ldg(dict_z + st[t]));
+            }
+        }
+    }
+}
+
 template <bool kEmit>
 __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -140,7 +238,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
     for (int64_t zt0 = zb; zt0 < ze; zt0 += a.tile_bits) {
         const int64_t zt1 = min64(zt0 + a.tile_bits, ze);
         const int tw = (int)((zt1 - zt0 + 31) >> 5);
-        for (int w = tid; w < tw; w += kThreads) bm[w] = 0u;
+        clear_words(bm, tw);
         __syncthreads();
         // narrow S_sparse rows: one warp per y of R[x]
         for (int64_t p = r0 + warp; p < r1; p += kThreads / 32) {
@@ -148,8 +246,9 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
             if (a.bm_row_of_y[y] >= 0) continue;
             int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
             if (tiled) {
-                s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
-                s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
+                const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + (zt0 - zb) / a.tile_bits;
+                s0 = tp[0];
+                s1 = tp[1];
             }
             for (int64_t q = s0 + lane; q < s1; q += 32) {
                 const int32_t z = a.ss_col[q] - (int32_t)zt0;
@@ -206,14 +305,14 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
         __syncthreads();
         if (!kEmit) {
             int64_t c = 0;
-            for (int w = tid; w < tw; w += kThreads) c += __popc(bm[w]);
+            c = popc_words(bm, tw);
             total += block_sum<int64_t, kThreads>(c, s_scan);
         } else {
             // Each warp owns a run of 32-word groups (1024 z ids each). The
             // warps' output offsets come from one popcount pass; after that
             // every warp compacts and writes its run without block barriers.
             const int groups = (tw + 31) >> 5;
-            const int gpw = (groups + kWarps - 1) / kWarps;
+            const int gpw = (((groups + kWarps - 1) / kWarps) + 3) & ~3;  // whole 4-group chunks per warp
             const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
             int mine = 0;
             for (int g = g0; g < g1; ++g) {
@@ -229,31 +328,74 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
                 if (w < warp) wpos += c;
                 tile_total += c;
             }
+            // Set bits are staged as z ids, group after group, and turned
+            // into z values only when the stage is flushed: a sparse row
+            // then costs one round of independent dictionary gathers per
+            // ~1000 pairs instead of one dependent round per group.
             int32_t* st = stage + warp * kWarpStage;
             const unsigned lt = lanemask_lt();
-            for (int g = g0; g < g1; ++g) {
-                const int w = (g << 5) + lane;
-                const uint32_t word = w < tw ? bm[w] : 0u;
-                const int c = __popc(word);
-                const int incl = warp_inclusive_scan(c);
-                const int total_g = __shfl_sync(kFull, incl, 31);
-                if (total_g == 0) continue;
-                const int excl = incl - c;
-                const int sh = (int)(wpos & 3);
-                // dictionary slice of this group: lane l reads entry 32 j + l
-                // while word j is broadcast, so every load is one 128-byte line
-                const int32_t* dz = a.dict_z + zt0 + ((int64_t)g << 10);
-#pragma unroll 4
-                for (int j = 0; j < 32; ++j) {
-                    const uint32_t wj = __shfl_sync(kFull, word, j);
-                    const int pj = __shfl_sync(kFull, excl, j);
-                    if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = __ldg(dz + (j << 5) + lane);
+            int sh = (int)(wpos & 3), sc = 0;  // stage holds pairs [wpos, wpos + sc) at st[sh ..]
+            // Chunks of 4 groups (128 words, 4096 z): lane l first reads words
+            // 4l .. 4l+3; a sparse chunk is extracted lane by lane in one step,
+            // a dense one group by group with the transposed dictionary reads.
+            for (int gc = g0; gc < g1; gc += 4) {
+                const int wl = (gc << 5) + (lane << 2);
+                const int wlim = min(tw, g1 << 5);
+                uint32_t wv[4];
+                int c4 = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    wv[k] = wl + k < wlim ? bm[wl + k] : 0u;
+                    c4 += __popc(wv[k]);
                 }
-                __syncwarp();
-                flush_warp(a.out_z + (wpos - sh), st, sh, total_g, a.vec_ok);
-                __syncwarp();
-                wpos += total_g;
+                const int incl4 = warp_inclusive_scan(c4);
+                const int total_c = __shfl_sync(kFull, incl4, 31);
+                if (total_c == 0) continue;
+                if (total_c <= 512) {
+                    if (sh + sc + total_c > kWarpStage) {
+                        __syncwarp();
+                        flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
+                        __syncwarp();
+                        wpos += sc;
+                        sh = (int)(wpos & 3);
+                        sc = 0;
+                    }
+                    int pos = sh + sc + incl4 - c4;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        uint32_t v = wv[k];
+                        while (v) {
+                            const int b = __ffs(v) - 1;
+                            v &= v - 1;
+                            st[pos++] = (int32_t)(zt0 + ((int64_t)(wl + k) << 5) + b);
+                        }
+                    }
+                    sc += total_c;
+                    continue;
+                }
+                for (int g = gc; g < min(gc + 4, g1); ++g) {
+                    const int w = (g << 5) + lane;
+                    const uint32_t word = w < tw ? bm[w] : 0u;
+                    const int c = __popc(word);
+                    const int incl = warp_inclusive_scan(c);
+                    const int total_g = __shfl_sync(kFull, incl, 31);
+                    if (total_g == 0) continue;
+                    if (sh + sc + total_g > kWarpStage) {
+                        __syncwarp();
+                        flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
+                        __syncwarp();
+                        wpos += sc;
+                        sh = (int)(wpos & 3);
+                        sc = 0;
+                    }
+                    stage_group_ids(st + sh + sc, word, incl - c, (int32_t)(zt0 + ((int64_t)g << 10)), lane, lt,
+                                    total_g);
+                    sc += total_g;
+                }
             }
+            __syncwarp();
+            if (sc) flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
+            __syncwarp();
             out_pos += tile_total;
         }
         __syncthreads();
@@ -306,7 +448,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
     for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += a.tile_bits) {
         const int64_t zt1 = min64(zt0 + a.tile_bits, a.n_z);
         const int tw = (int)((zt1 - zt0 + 31) >> 5);
-        for (int i = tid; i < ng * tile_words; i += kThreads) bm_all[i] = 0u;
+        clear_words(bm_all, (int)(ng * tile_words));
         __syncthreads();
         // narrow S_sparse rows of all G rows: one warp per R entry
         for (int64_t p = rb[0] + warp; p < rb[ng]; p += kWarps) {
@@ -428,12 +570,9 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
             }
             if (!__any_sync(kFull, any)) continue;
             int32_t dreg[32];
+            bool loaded = false;  // warp-uniform
             const int64_t gb = (int64_t)g << 10;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int64_t idx = gb + (j << 5) + lane;
-                dreg[j] = idx < zlim ? __ldg(a.dict_z + zt0 + idx) : 0;
-            }
+            const int32_t* dz = a.dict_z + zt0 + gb;
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 const int c = __popc(word[k]);
@@ -442,11 +581,30 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
                 if (total_g == 0) continue;
                 const int excl = incl - c;
                 const int sh = (int)(wpos[k] & 3);
+                if (total_g <= 64) {
+                    // few bits: each lane writes its own word's bits
+                    int pos = sh + excl;
+                    uint32_t wv = word[k];
+                    while (wv) {
+                        const int b = __ffs(wv) - 1;
+                        wv &= wv - 1;
+                        st[pos++] = __ldg(dz + (lane << 5) + b);
+                    }
+                } else {
+                    if (!loaded) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const uint32_t wj = __shfl_sync(kFull, word[k], j);
-                    const int pj = __shfl_sync(kFull, excl, j);
-                    if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = dreg[j];
+                        for (int j = 0; j < 32; ++j) {
+                            const int64_t idx = gb + (j << 5) + lane;
+                            dreg[j] = idx < zlim ? __ldg(a.dict_z + zt0 + idx) : 0;
+                        }
+                        loaded = true;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const uint32_t wj = __shfl_sync(kFull, word[k], j);
+                        const int pj = __shfl_sync(kFull, excl, j);
+                        if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = dreg[j];
+                    }
                 }
                 __syncwarp();
                 flush_warp(a.out_z + (wpos[k] - sh), st, sh, total_g, a.vec_ok);
@@ -473,7 +631,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tg = a.x_tag ? a.x_tag[x] : 0;
-    const int64_t zb = a.z_lo[tg], ze = a.z_lo[tg + 1];  // z window of x's instance
+    const int64_t zb = a.z_lo[tg] & ~int64_t(31), ze = a.z_lo[tg + 1];  // z window of x's instance
     const bool tiled = a.tile_bits < ze - zb;
     int64_t total = 0;
     int64_t out_pos = 0;
@@ -490,8 +648,9 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
             const int32_t y = a.r_col[p];
             int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
             if (tiled) {
-                s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
-                s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
+                const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + (zt0 - zb) / a.tile_bits;
+                s0 = tp[0];
+                s1 = tp[1];
             }
             for (int64_t q = s0 + lane; q < s1; q += 32) atomicAdd(&ctr[a.ss_col[q] - (int32_t)zt0], 1u);
         }
@@ -563,6 +722,40 @@ static void setup_attrs(const Ctx& ctx) {
     done[d] = true;
 }
 
+// tile_ptr[y * cols + t] = first entry of S_sparse row y with z >= start of
+// tile t of y's instance window (t = 0 .. cols - 1)
+__global__ void k_tile_ptr(const int64_t* rowptr, const int32_t* col, int64_t n_y, const int32_t* y_tag,
+                           const int64_t* z_lo, int64_t tile_bits, int64_t cols, int64_t* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_y * cols;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t y = i / cols, t = i % cols;
+        const int tg = y_tag ? y_tag[y] : 0;
+        const int64_t v = min64((z_lo[tg] & ~int64_t(31)) + t * tile_bits, (int64_t)INT32_MAX);
+        out[i] = lower_bound_dev<int32_t>(col, rowptr[y], rowptr[y + 1], (int32_t)v);
+    }
+}
+
+// Build (once per pass kind and tile size) the per-row tile starts of a z-tiled plan.
+static void ensure_tile_ptr(Plan& p, int kind, int64_t tile_bits, cudaStream_t s) {
+    if (p.tile_ptr_bits[kind] == tile_bits) return;
+    int64_t n_tiles = 1;
+    for (int t = 0; t < p.n_inst; ++t) {
+        const int64_t w = p.h_inst_z_lo[t + 1] - (p.h_inst_z_lo[t] & ~int64_t(31));
+        n_tiles = std::max<int64_t>(n_tiles, ceil_div(std::max<int64_t>(w, 1), tile_bits));
+    }
+    const int64_t cols = n_tiles + 1, n_y = p.info.n_y;
+    p.tile_ptr[kind].alloc((size_t)std::max<int64_t>(n_y * cols, 1) * 8, s);
+    if (n_y > 0) {
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_y * cols, kThreads), 152 * 16));
+        k_tile_ptr<<<g, kThreads, 0, s>>>(p.ss_rowptr.as<int64_t>(), p.ss_col.as<int32_t>(), n_y,
+                                          p.n_inst > 1 ? p.y_tag.as<int32_t>() : nullptr, p.inst_z_lo.as<int64_t>(),
+                                          tile_bits, cols, p.tile_ptr[kind].as<int64_t>());
+        DIM3_LAUNCHED();
+    }
+    p.tile_ptr_bits[kind] = tile_bits;
+    p.tile_cols[kind] = cols;
+}
+
 static XRowArgs make_args(const Plan& p, int64_t x_begin, int64_t rows, int kind) {
     XRowArgs a{};
     a.x_begin = x_begin;
@@ -605,6 +798,17 @@ static int emit_rows_per_cta(const Ctx& ctx, int64_t tile_bits) {
     if (want == 1 || want == 2 || want == 4) return fits(want, cap) ? (int)want : 1;
     if (fits(2, 112 * 1024)) return 2;
     return 1;
+}
+
+// make_args plus, for z-tiled plans, the per-row tile starts.
+static XRowArgs prep_args(Plan& p, int64_t x_begin, int64_t rows, int kind, cudaStream_t s) {
+    XRowArgs a = make_args(p, x_begin, rows, kind);
+    if (p.zw * 32 > a.tile_bits) {
+        ensure_tile_ptr(p, kind, a.tile_bits, s);
+        a.tile_ptr = p.tile_ptr[kind].as<int64_t>();
+        a.tile_cols = p.tile_cols[kind];
+    }
+    return a;
 }
 
 static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, cudaStream_t s) {
@@ -669,7 +873,7 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
         if (p.info.n_z <= 0 || p.info.n_r_kept == 0) {
             DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
         } else {
-            XRowArgs a = make_args(p, x_begin, rows, kind);
+            XRowArgs a = prep_args(p, x_begin, rows, kind, s);
             a.d_bits = p.cache_dbits.as<uint32_t>();
             a.d_cnt = p.cache_dcnt.as<int32_t>();
             a.cnt = cnt.as<int64_t>();
@@ -714,7 +918,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
                                                              " < result size " + std::to_string(total));
     if (total > 0) {
         DIM3_REQUIRE(out_x && out_z && (kind == 0 || out_cnt), DIM3_ERR_ARG, "null output buffer");
-        XRowArgs a = make_args(p, x_begin, rows, kind);
+        XRowArgs a = prep_args(p, x_begin, rows, kind, s);
         a.d_bits = p.cache_dbits.as<uint32_t>();
         a.d_cnt = p.cache_dcnt.as<int32_t>();
         a.off = p.cache_off.as<int64_t>();

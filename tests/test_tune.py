@@ -1,0 +1,50 @@
+"""Autotuner: candidate generation and cost bounds on the CPU; on the GPU,
+the chosen configuration gives the oracle's result and is cached."""
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from paper_2206_04995_gb300 import tune
+
+
+def test_theta_candidates_are_degree_quantiles():
+    m_z = np.array([1] * 900 + [5] * 90 + [50] * 9 + [500])
+    c = tune.theta_candidates(m_z)
+    assert c[0] == tune.INF
+    assert 500 in c and 50 in c and 5 in c and 1 in c
+    assert c == sorted(c, reverse=True)
+    assert tune.theta_candidates(np.zeros(0, np.int64)) == [tune.INF]
+
+
+def test_dense_estimate_bounds():
+    m_z = np.array([10, 20, 30])
+    n_zd, flops, b = tune.dense_estimate(m_z, 20, n_x=100, n_y=1000)
+    assert n_zd == 2 and flops == 2.0 * 100 * 50 * 2
+    n_zd, flops, b = tune.dense_estimate(m_z, 1, n_x=100, n_y=40)
+    assert n_zd == 3 and flops == 2.0 * 100 * 40 * 3  # K bounded by |Y|
+    assert tune.dense_estimate(m_z, tune.INF, 100, 40)[0] == 0
+
+
+@pytest.mark.gpu
+def test_tuner_decision_is_exact_and_cached(tmp_path):
+    import torch
+
+    import paper_2206_04995_gb300 as dim3
+    from tests.gpu_util import host, inst_dev
+
+    path = str(tmp_path / "tune.json")
+    for inst in (gen.small_two_table(4, n_r=60_000, n_s=60_000, nx=600, ny=300, nz=500, zipf=0.7),
+                 gen.config2_two_table(scale=0.02)):
+        ctx = dim3.Context(0)
+        cols = inst_dev(inst)
+        d = tune.tune(ctx, cols, cache_path=path)
+        assert not d["cached"] and d["trials"]
+        x, z = ctx.join_project(*cols)
+        ox, oz, _ = oracle.join_project(inst.r_key, inst.r_val, inst.s_key, inst.s_val)
+        assert np.array_equal(host(x), ox) and np.array_equal(host(z), oz)
+        again = tune.tune(dim3.Context(0), cols, cache_path=path)
+        assert again["cached"] and again["theta"] == d["theta"] and again["variant"] == d["variant"]
+        ctx.close()
+        torch.cuda.synchronize()
