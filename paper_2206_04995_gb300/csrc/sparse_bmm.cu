@@ -28,7 +28,8 @@ namespace dimcube {
 
 constexpr int kWarps = kThreads / 32;
 constexpr int kWarpStage = 1040;        // staged output values per warp (1024 + alignment shift, 16-byte multiple)
-constexpr int64_t kMaxTileWords = 16 * 1024;   // 64 KiB bitmap tile = 524,288 z (two emitting CTAs per SM)
+constexpr int kWarpStageIds = 528;      // staged z ids per warp in the one-row kernel (512 + shift)
+constexpr int64_t kMaxTileWords = 12 * 1024;   // 48 KiB bitmap tile = 393,216 z (three emitting CTAs per SM)
 constexpr int kCntChunk = 4096;         // z per compaction chunk (count mode)
 constexpr int64_t kMaxCntTile = 16 * 1024;     // counters per tile (64 KiB)
 
@@ -213,8 +214,8 @@ __device__ __forceinline__ void flush_warp_ids(int32_t* dst, const int32_t* st, 
 template <bool kEmit>
 __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
-    int32_t* stage = reinterpret_cast<int32_t*>(smem);       // emit: kWarps x kWarpStage
-    uint32_t* bm = smem + (kEmit ? kWarps * kWarpStage : 0);  // tile words
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);          // emit: kWarps x kWarpStageIds
+    uint32_t* bm = smem + (kEmit ? kWarps * kWarpStageIds : 0);  // tile words
     __shared__ int64_t s_scan[kThreads / 32 + 1];
     __shared__ int32_t s_list[kThreads];
     __shared__ int32_t s_wc[kThreads / 32 + 1];
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
             // into z values only when the stage is flushed: a sparse row
             // then costs one round of independent dictionary gathers per
             // ~1000 pairs instead of one dependent round per group.
-            int32_t* st = stage + warp * kWarpStage;
+            int32_t* st = stage + warp * kWarpStageIds;
             const unsigned lt = lanemask_lt();
             int sh = (int)(wpos & 3), sc = 0;  // stage holds pairs [wpos, wpos + sc) at st[sh ..]
             // Chunks of 4 groups (128 words, 4096 z): lane l first reads words
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
                 const int total_c = __shfl_sync(kFull, incl4, 31);
                 if (total_c == 0) continue;
                 if (total_c <= 512) {
-                    if (sh + sc + total_c > kWarpStage) {
+                    if (sh + sc + total_c > kWarpStageIds) {
                         __syncwarp();
                         flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
                         __syncwarp();
@@ -373,14 +374,18 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
                     sc += total_c;
                     continue;
                 }
-                for (int g = gc; g < min(gc + 4, g1); ++g) {
+                // dense chunk: half-groups (16 words, at most 512 set bits) so
+                // that one always fits the stage after a flush
+                for (int h = gc * 2; h < min(gc + 4, g1) * 2; ++h) {
+                    const int g = h >> 1;
                     const int w = (g << 5) + lane;
-                    const uint32_t word = w < tw ? bm[w] : 0u;
+                    const bool mine_half = (lane >> 4) == (h & 1);
+                    const uint32_t word = (mine_half && w < tw) ? bm[w] : 0u;
                     const int c = __popc(word);
                     const int incl = warp_inclusive_scan(c);
                     const int total_g = __shfl_sync(kFull, incl, 31);
                     if (total_g == 0) continue;
-                    if (sh + sc + total_g > kWarpStage) {
+                    if (sh + sc + total_g > kWarpStageIds) {
                         __syncwarp();
                         flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
                         __syncwarp();
@@ -704,7 +709,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
 
 // ----------------------------------------------------------------- host side
 static size_t bits_smem(int64_t tile_bits, bool emit) {
-    return (emit ? (size_t)kWarps * kWarpStage * 4 : 0) + (size_t)(tile_bits / 32) * 4;
+    return (emit ? (size_t)kWarps * kWarpStageIds * 4 : 0) + (size_t)(tile_bits / 32) * 4;
 }
 static size_t cnt_smem(int64_t tile_bits) { return (size_t)(kCntChunk + 8) * 8 + (size_t)tile_bits * 4; }
 
