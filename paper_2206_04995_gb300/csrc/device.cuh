@@ -80,6 +80,33 @@ __device__ __forceinline__ T block_sum(T v, T* s_warp) {
     return r;
 }
 
+// Block-aggregated append: every thread with `want` gets a distinct slot in
+// [base, base + block total) of a global counter, with ONE atomicAdd per block
+// (instead of one per warp). Call from all threads of the block; s_cnt is
+// shared scratch of NT/32 + 2 entries.
+template <int NT>
+__device__ __forceinline__ unsigned long long block_append(bool want, unsigned long long* counter,
+                                                           unsigned long long* s_cnt) {
+    constexpr int NW = NT / 32;
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    const unsigned b = __ballot_sync(kFull, want);
+    if (lane == 0) s_cnt[w] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int i = 0; i < NW; ++i) {
+            const unsigned long long c = s_cnt[i];
+            s_cnt[i] = run;
+            run += c;
+        }
+        s_cnt[NW] = run ? atomicAdd(counter, run) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long pos = s_cnt[NW] + s_cnt[w] + __popc(b & lanemask_lt());
+    __syncthreads();
+    return pos;
+}
+
 // 32-bit finaliser of MurmurHash3 (Appleby): spreads keys over table slots.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;

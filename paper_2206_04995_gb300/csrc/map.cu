@@ -65,19 +65,15 @@ __global__ void k_hash_insert(const int32_t* __restrict__ vals, const int32_t* _
 template <typename K>
 __global__ void k_hash_collect(const unsigned long long* table, int64_t cap, K* okeys, uint32_t* oslots,
                                unsigned long long* counter) {
+    __shared__ unsigned long long s_cnt[kThreads / 32 + 2];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t iters = (cap + stride - 1) / stride;
-    const unsigned lane = lane_id();
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t s = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
         const unsigned long long t = s < cap ? table[s] : 0ull;
         const bool occ = t != 0ull;
-        const unsigned b = __ballot_sync(kFull, occ);
-        unsigned long long base = 0;
-        if (lane == 0 && b) base = atomicAdd(counter, (unsigned long long)__popc(b));
-        base = __shfl_sync(kFull, base, 0);
+        const unsigned long long pos = block_append<kThreads>(occ, counter, s_cnt);
         if (occ) {
-            const unsigned long long pos = base + __popc(b & lanemask_lt());
             const uint64_t tag = (t >> 32) & 0x7fffffffull;
             okeys[pos] = (K)((tag << 32) | (uint64_t)(((uint32_t)t) ^ 0x80000000u));
             oslots[pos] = (uint32_t)s;

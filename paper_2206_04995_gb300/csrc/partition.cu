@@ -29,9 +29,9 @@ static unsigned grid_for(int64_t n) {
 template <typename K>
 __global__ void k_pack_pairs(const int32_t* a, const int32_t* b, int64_t n, int shift, K* keys,
                              unsigned long long* counter) {
+    __shared__ unsigned long long s_cnt[kThreads / 32 + 2];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t iters = (n + stride - 1) / stride;
-    const unsigned lane = lane_id();
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
         int32_t av = -1, bv = -1;
@@ -40,11 +40,8 @@ __global__ void k_pack_pairs(const int32_t* a, const int32_t* b, int64_t n, int 
             bv = b[i];
         }
         const bool ok = av >= 0 && bv >= 0;
-        const unsigned bal = __ballot_sync(kFull, ok);
-        unsigned long long base = 0;
-        if (lane == 0 && bal) base = atomicAdd(counter, (unsigned long long)__popc(bal));
-        base = __shfl_sync(kFull, base, 0);
-        if (ok) keys[base + __popc(bal & lanemask_lt())] = ((K)(uint32_t)av << shift) | (K)(uint32_t)bv;
+        const unsigned long long pos = block_append<kThreads>(ok, counter, s_cnt);
+        if (ok) keys[pos] = ((K)(uint32_t)av << shift) | (K)(uint32_t)bv;
     }
 }
 
@@ -63,12 +60,16 @@ __global__ void k_row_len(const int64_t* rowptr, int64_t n_rows, int32_t* len) {
 }
 
 // join tuples per x: sum of deg_S(y) over y in R[x]
+// one warp per x (rows are power-law in graphs: a thread per row stalls on hubs)
 __global__ void k_outj_x(const int64_t* r_rowptr, const int32_t* r_col, int64_t n_x, const int32_t* deg_s,
                          int64_t* outj_x) {
-    GRID_STRIDE(x, n_x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; x < n_x; x += warps) {
         int64_t acc = 0;
-        for (int64_t p = r_rowptr[x]; p < r_rowptr[x + 1]; ++p) acc += deg_s[r_col[p]];
-        outj_x[x] = acc;
+        for (int64_t p = r_rowptr[x] + lane; p < r_rowptr[x + 1]; p += 32) acc += deg_s[r_col[p]];
+        acc = warp_sum(acc);
+        if (lane == 0) outj_x[x] = acc;
     }
 }
 
@@ -265,7 +266,7 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
     // join tuples per x and |OUT_J|
     p.outj_x.alloc((size_t)std::max<int64_t>(n_x, 1) * 8, s);
     if (n_x > 0) {
-        k_outj_x<<<grid_for(n_x), kThreads, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(), n_x,
+        k_outj_x<<<grid_for(n_x * 32), kThreads, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(), n_x,
                                                      p.deg_s.as<int32_t>(), p.outj_x.as<int64_t>());
         DIM3_LAUNCHED();
         DevBuf sc;
