@@ -396,6 +396,9 @@ def run_batch(args, rank, world, local_rank):
     cols = [[torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(dev)
              for a in (i.r_key, i.r_val, i.s_key, i.s_val)] for i in insts]
     ctx = dim3.Context(local_rank)
+    for kv in args.opt:
+        k, v = kv.split("=")
+        ctx.set_option(int(k), int(v))
     plan = ctx.batch_partition(cols)
     info = plan.info
     out_p = int(plan.row_counts().sum().item())

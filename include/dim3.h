@@ -99,7 +99,11 @@ typedef enum {
     DIM3_OPT_BITMAP_ROW_MIN = 3,/* S_sparse rows with at least this many z are held as bitmaps; <0: |Z|/32 */
     DIM3_OPT_LIGHT_ROW_MAX = 4, /* x rows with at most this many join tuples dedup in shared memory by sort; <0: default */
     DIM3_OPT_TIMING = 5,        /* nonzero: record CUDA events around each phase (dim3_ctx_timing) */
-    DIM3_OPT_EMIT_ROWS = 6      /* x rows per CTA in the emitting SparseBMM pass: 1, 2, 4; 0: automatic */
+    DIM3_OPT_EMIT_ROWS = 6,     /* x rows per CTA in the emitting SparseBMM pass: 1, 2, 4; 0: automatic */
+    DIM3_OPT_TWO_PASS = 7,      /* nonzero: always count before emitting (no single-pass look-back) */
+    DIM3_OPT_ID_CHUNK_MAX = 8   /* emitting pass: a 4096-z chunk of one x row holding at most this many
+                                   pairs is written through staged z ids, a denser one group by group;
+                                   0: always group by group; <0: default (512); at most 1024 */
 } dim3_option;
 
 /* Phases timed under DIM3_OPT_TIMING. */
@@ -204,7 +208,11 @@ DIM3_API int dim3_plan_row_counts(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begi
  *                     canonical order (x ids are rank-ordered, so ranges
  *                     concatenate into the full canonical result).
  *   count             host, out: pairs of the range; always set.
- * If capacity < count nothing is written and DIM3_ERR_CAPACITY is returned.
+ * If capacity < count, DIM3_ERR_CAPACITY is returned and the contents of the
+ * output buffers are unspecified (a single-pass emission may have written a
+ * prefix). capacity = 0 (or null buffers) only sizes the range: it runs a
+ * counting pass that the plan keeps, so the next call for the same range
+ * emits without counting again.
  * x_begin = 0, x_end = n_x covers everything. Synchronises the stream.
  */
 DIM3_API int dim3_plan_join_project(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
@@ -276,7 +284,7 @@ DIM3_API int dim3_plan_destroy(dim3_plan *plan);
  * SparseBMM + DenseEC, union, compaction.
  *   d_out_x, d_out_z [capacity] int32 device, out.
  *   count            host, out: |OUT_P|; always set, also on DIM3_ERR_CAPACITY
- *                    (then nothing is written).
+ *                    (then the buffers' contents are unspecified).
  * Synchronises the stream.
  */
 DIM3_API int dim3_join_project(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,

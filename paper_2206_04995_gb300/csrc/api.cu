@@ -179,6 +179,11 @@ int dim3_ctx_set_option(dim3_ctx* ctx, int option, int64_t value) {
             case DIM3_OPT_BITMAP_ROW_MIN: ctx->c.opt.bitmap_row_min = value; break;
             case DIM3_OPT_LIGHT_ROW_MAX: ctx->c.opt.light_row_max = value; break;
             case DIM3_OPT_TIMING: ctx->stats.on = value != 0; break;
+            case DIM3_OPT_TWO_PASS: ctx->c.opt.two_pass = value; break;
+            case DIM3_OPT_ID_CHUNK_MAX:
+                DIM3_REQUIRE(value <= 1024, DIM3_ERR_ARG, "id chunk maximum above 1024");
+                ctx->c.opt.id_chunk_max = value;
+                break;
             case DIM3_OPT_EMIT_ROWS:
                 DIM3_REQUIRE(value == 0 || value == 1 || value == 2 || value == 4, DIM3_ERR_ARG,
                              "emit rows per CTA must be 0 (auto), 1, 2 or 4");

@@ -70,12 +70,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Bounded wait on the phase with the given parity: gives up (returns false)
 // after kWaitNs nanoseconds of wall time or kWaitLimit polls, whichever first.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {

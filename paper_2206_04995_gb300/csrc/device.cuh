@@ -107,6 +107,61 @@ __device__ __forceinline__ unsigned long long block_append(bool want, unsigned l
     return pos;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Decoupled look-back (single-pass prefix sum across CTAs). status[b] holds a
+// flag in its top two bits (0 none yet, 1 aggregate of block b, 2 inclusive
+// prefix up to b) and the value in the rest. Blocks take logical numbers in
+// dispatch order (a ticket), so a block only waits on blocks that are already
+// running. Called by one whole warp; returns the exclusive prefix of block b
+// (the same in every lane), or -1 if a predecessor did not publish within
+// wait_ns (then *err is set and a placeholder is published so that the blocks
+// after this one do not wait either).
+constexpr unsigned long long kLbAgg = 1ull << 62, kLbInc = 2ull << 62, kLbVal = (1ull << 62) - 1;
+
+__device__ __forceinline__ int64_t lookback_prefix(unsigned long long* status, int64_t b, int64_t aggregate, int* err,
+                                                   uint64_t wait_ns) {
+    const int lane = lane_id();
+    if (b == 0) {
+        if (lane == 0) atomicExch(&status[0], kLbInc | (unsigned long long)aggregate);
+        return 0;
+    }
+    if (lane == 0) atomicExch(&status[b], kLbAgg | (unsigned long long)aggregate);
+    int64_t prefix = 0, j = b - 1;
+    const uint64_t t0 = global_ns();
+    uint32_t polls = 0;
+    while (true) {
+        const int64_t idx = j - lane;
+        const unsigned long long v = idx >= 0 ? ld_relaxed_u64(&status[idx]) : kLbInc;
+        if (!__all_sync(kFull, (v >> 62) != 0ull)) {
+            const bool late = ((++polls & 63u) == 0u) && (global_ns() - t0 > wait_ns);
+            if (__any_sync(kFull, late)) {
+                if (lane == 0) atomicExch(err, 1);
+                prefix = -1;
+                break;
+            }
+            continue;
+        }
+        const unsigned inc = __ballot_sync(kFull, (v >> 62) == 2ull);
+        const int stop = inc ? __ffs(inc) - 1 : 31;
+        prefix += warp_sum(lane <= stop ? (int64_t)(v & kLbVal) : (int64_t)0);
+        if (inc) break;
+        j -= 32;
+    }
+    if (lane == 0) atomicExch(&status[b], kLbInc | (unsigned long long)((prefix < 0 ? 0 : prefix) + aggregate));
+    return prefix;
+}
+
 // 32-bit finaliser of MurmurHash3 (Appleby): spreads keys over table slots.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;

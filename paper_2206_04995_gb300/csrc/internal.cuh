@@ -45,6 +45,8 @@ struct Options {
     int64_t bitmap_row_min = -1;
     int64_t light_row_max = -1;
     int64_t emit_rows = 0;  // x rows per CTA in the emitting pass (0: automatic)
+    int64_t two_pass = 0;   // nonzero: always a counting pass before the emitting pass
+    int64_t id_chunk_max = -1;  // pairs per 4096-z chunk written through staged ids (<0: 512)
 };
 
 struct Plan {

@@ -32,6 +32,7 @@ constexpr int kWarpStageIds = 528;      // staged z ids per warp in the one-row 
 constexpr int64_t kMaxTileWords = 12 * 1024;   // 48 KiB bitmap tile = 393,216 z (three emitting CTAs per SM)
 constexpr int kCntChunk = 4096;         // z per compaction chunk (count mode)
 constexpr int64_t kMaxCntTile = 16 * 1024;     // counters per tile (64 KiB)
+constexpr uint64_t kLookbackWaitNs = 2000000000ull;  // single pass: give up on a predecessor after 2 s
 
 struct XRowArgs {
     int64_t x_begin, n_rows;
@@ -55,6 +56,17 @@ struct XRowArgs {
     const int32_t* dict_x;
     const int32_t* dict_z;
     int64_t* cnt;            // counting pass out
+    // single pass (no counting pass): look-back status per logical block,
+    // ticket counter, error flag and the output capacity
+    unsigned long long* lb_status;
+    unsigned long long* lb_ticket;
+    int* lb_err;
+    int64_t capacity;
+    // one-row emitting kernel: staged entries per warp, kWarpStageIds (sparse
+    // output, more CTAs per SM) or kWarpStage (dense output, whole groups)
+    int stage_ints;
+    int id_max;  // a 4096-z chunk with at most this many pairs goes through staged ids
+    int flat_max;  // x rows (groups) with at most this many R entries take the one-phase build
     const int64_t* off;      // emitting pass: [n_rows + 1]
     int32_t* out_x;
     int32_t* out_z;
@@ -134,6 +146,15 @@ __device__ __forceinline__ void compact_group(int32_t* st, int sh, uint32_t word
         return;
     }
     unsigned m = __ballot_sync(kFull, word != 0u);
+    if (__popc(m) >= 24) {  // nearly every word set: a fixed, unrolled sweep
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t wj = __shfl_sync(kFull, word, j);
+            const int pj = __shfl_sync(kFull, excl, j);
+            if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = __ldg(dz + (j << 5) + lane);
+        }
+        return;
+    }
     while (m) {
         const int j = __ffs(m) - 1;
         m &= m - 1;
@@ -164,30 +185,6 @@ __device__ __forceinline__ int64_t popc_words(const uint32_t* bm, int n) {
     return c;
 }
 
-// Stage the z ids of the set bits of one 32-word group (lane j holds word j,
-// excl = set bits in words < j) at dst[0 ..] in id order.
-__device__ __forceinline__ void stage_group_ids(int32_t* dst, uint32_t word, int excl, int32_t zbase, int lane,
-                                                unsigned lt, int total_g) {
-    if (total_g <= 64) {
-        int pos = excl;
-        uint32_t wv = word;
-        while (wv) {
-            const int b = __ffs(wv) - 1;
-            wv &= wv - 1;
-            dst[pos++] = zbase + (lane << 5) + b;
-        }
-        return;
-    }
-    unsigned m = __ballot_sync(kFull, word != 0u);
-    while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1;
-        const uint32_t wj = __shfl_sync(kFull, word, j);
-        const int pj = __shfl_sync(kFull, excl, j);
-        if ((wj >> lane) & 1u) dst[pj + __popc(wj & lt)] = zbase + (j << 5) + lane;
-    }
-}
-
 // flush_warp for a stage of z ids: dst[t] = dict_z[st[t]] for t in [sh, sh + cnt).
 __device__ __forceinline__ void flush_warp_ids(int32_t* dst, const int32_t* st, int sh, int cnt,
                                                const int32_t* __restrict__ dict_z, bool vec_ok) {
@@ -211,16 +208,30 @@ __device__ __forceinline__ void flush_warp_ids(int32_t* dst, const int32_t* st, 
     }
 }
 
+// Register caps: 32 for the counting instance (eight CTAs per SM), 64 for the
+// emitting one (four, no spills); both are latency-bound. Measured on the
+// 256-instance batch: the emitting instance at 64 registers 18.4 ms, at 48
+// (spilling) 19.3 ms.
 template <bool kEmit>
-__global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
+__global__ void __launch_bounds__(kThreads, kEmit ? 4 : 8) k_xrow_bits(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
-    int32_t* stage = reinterpret_cast<int32_t*>(smem);          // emit: kWarps x kWarpStageIds
-    uint32_t* bm = smem + (kEmit ? kWarps * kWarpStageIds : 0);  // tile words
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);           // emit: kWarps x a.stage_ints
+    uint32_t* bm = smem + (kEmit ? kWarps * a.stage_ints : 0);  // tile words
     __shared__ int64_t s_scan[kThreads / 32 + 1];
     __shared__ int32_t s_list[kThreads];
+    __shared__ int32_t s_ny[kThreads];
+    __shared__ int64_t s_woff[kThreads];
     __shared__ int32_t s_wc[kThreads / 32 + 1];
+    __shared__ int32_t s_cw[kWarps], s_cn[kWarps];
+    __shared__ int64_t s_blk, s_prefix;
 
-    const int64_t xr = blockIdx.x;
+    // single pass (emitting kernel, one z tile): row number from a ticket
+    int64_t xr = blockIdx.x;
+    if (kEmit && a.lb_status) {
+        if (threadIdx.x == 0) s_blk = (int64_t)atomicAdd(a.lb_ticket, 1ull);
+        __syncthreads();
+        xr = s_blk;
+    }
     if (xr >= a.n_rows) return;
     const int64_t x = a.x_begin + xr;
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
@@ -232,59 +243,117 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
     const bool tiled = a.tile_bits < ze - zb;
     int64_t total = 0;
     int64_t out_pos = 0;
-    if (kEmit) {
+    bool write = true;
+    if (kEmit && !a.lb_status) {
         out_pos = a.off[xr];
         fill_range(a.out_x, out_pos, a.off[xr + 1], a.dict_x[x], a.vec_ok);
+    }
+    // At most kThreads R entries: sorted once into per-warp lists of narrow
+    // rows (y) and wide rows (bitmap), then each tile is built in one
+    // barrier-free phase (warps walk narrow rows while every thread ORs the
+    // wide rows into its words, both with shared atomics).
+    const bool flat = r1 - r0 <= a.flat_max;  // block-uniform
+    if (flat) {
+        const int64_t p = r0 + tid;
+        int32_t y = -1, b = -1;
+        if (p < r1) {
+            y = a.r_col[p];
+            b = a.bm_row_of_y[y];
+        }
+        const bool isw = b >= 0, isn = p < r1 && b < 0;
+        const unsigned bw = __ballot_sync(kFull, isw), bn = __ballot_sync(kFull, isn);
+        if (isw) s_woff[(warp << 5) + __popc(bw & lanemask_lt())] = a.bm_off[b];
+        if (isn) s_ny[(warp << 5) + __popc(bn & lanemask_lt())] = y;
+        if (lane == 0) {
+            s_cw[warp] = __popc(bw);
+            s_cn[warp] = __popc(bn);
+        }
     }
     for (int64_t zt0 = zb; zt0 < ze; zt0 += a.tile_bits) {
         const int64_t zt1 = min64(zt0 + a.tile_bits, ze);
         const int tw = (int)((zt1 - zt0 + 31) >> 5);
         clear_words(bm, tw);
         __syncthreads();
-        // narrow S_sparse rows: one warp per y of R[x]
-        for (int64_t p = r0 + warp; p < r1; p += kThreads / 32) {
-            const int32_t y = a.r_col[p];
-            if (a.bm_row_of_y[y] >= 0) continue;
-            int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
-            if (tiled) {
-                const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + (zt0 - zb) / a.tile_bits;
-                s0 = tp[0];
-                s1 = tp[1];
+        if (flat) {
+            int n_nar = 0;
+            unsigned wmask = 0u;  // warps whose list holds wide rows
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                n_nar += s_cn[w];
+                wmask |= s_cw[w] > 0 ? 1u << w : 0u;
             }
-            for (int64_t q = s0 + lane; q < s1; q += 32) {
-                const int32_t z = a.ss_col[q] - (int32_t)zt0;
-                atomicOr(&bm[z >> 5], 1u << (z & 31));
-            }
-        }
-        // wide S_sparse rows: gather up to kThreads bitmap rows, OR them word-wise
-        for (int64_t base = r0; base < r1; base += kThreads) {
-            const int64_t p = base + tid;
-            const int32_t b = p < r1 ? a.bm_row_of_y[a.r_col[p]] : -1;
-            const unsigned bal = __ballot_sync(kFull, b >= 0);
-            if (lane == 0) s_wc[warp] = __popc(bal);
-            __syncthreads();
-            if (tid == 0) {
-                int run = 0;
-                for (int w = 0; w < kThreads / 32; ++w) {
-                    const int c = s_wc[w];
-                    s_wc[w] = run;
-                    run += c;
+            for (int e = warp; e < n_nar; e += kWarps) {
+                int sg = 0, base = 0;
+                while (e - base >= s_cn[sg]) base += s_cn[sg++];
+                const int32_t y = s_ny[(sg << 5) + (e - base)];
+                int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+                if (tiled) {
+                    const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + (zt0 - zb) / a.tile_bits;
+                    s0 = tp[0];
+                    s1 = tp[1];
                 }
-                s_wc[kThreads / 32] = run;
+                for (int64_t q = s0 + lane; q < s1; q += 32) {
+                    const int32_t z = a.ss_col[q] - (int32_t)zt0;
+                    atomicOr(&bm[z >> 5], 1u << (z & 31));
+                }
             }
-            __syncthreads();
-            if (b >= 0) s_list[s_wc[warp] + __popc(bal & lanemask_lt())] = b;
-            __syncthreads();
-            const int nl = s_wc[kThreads / 32];
-            if (nl > 0) {
+            if (wmask) {
                 const uint32_t* bits = a.ss_bits + ((zt0 - zb) >> 5);
                 for (int w = tid; w < tw; w += kThreads) {
                     uint32_t acc = 0u;
-                    for (int i = 0; i < nl; ++i) acc |= __ldg(bits + a.bm_off[s_list[i]] + w);
-                    if (acc) bm[w] |= acc;
+                    for (unsigned m = wmask; m; m &= m - 1) {
+                        const int sg = __ffs(m) - 1, c = s_cw[sg];
+                        for (int i = sg << 5; i < (sg << 5) + c; ++i) acc |= __ldg(bits + s_woff[i] + w);
+                    }
+                    if (acc) atomicOr(&bm[w], acc);
                 }
             }
-            __syncthreads();
+        } else {
+            // narrow S_sparse rows: one warp per y of R[x]
+            for (int64_t p = r0 + warp; p < r1; p += kThreads / 32) {
+                const int32_t y = a.r_col[p];
+                if (a.bm_row_of_y[y] >= 0) continue;
+                int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+                if (tiled) {
+                    const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + (zt0 - zb) / a.tile_bits;
+                    s0 = tp[0];
+                    s1 = tp[1];
+                }
+                for (int64_t q = s0 + lane; q < s1; q += 32) {
+                    const int32_t z = a.ss_col[q] - (int32_t)zt0;
+                    atomicOr(&bm[z >> 5], 1u << (z & 31));
+                }
+            }
+            // wide S_sparse rows: gather up to kThreads bitmap rows, OR them word-wise
+            for (int64_t base = r0; base < r1; base += kThreads) {
+                const int64_t p = base + tid;
+                const int32_t b = p < r1 ? a.bm_row_of_y[a.r_col[p]] : -1;
+                const unsigned bal = __ballot_sync(kFull, b >= 0);
+                if (lane == 0) s_wc[warp] = __popc(bal);
+                __syncthreads();
+                if (tid == 0) {
+                    int run = 0;
+                    for (int w = 0; w < kThreads / 32; ++w) {
+                        const int c = s_wc[w];
+                        s_wc[w] = run;
+                        run += c;
+                    }
+                    s_wc[kThreads / 32] = run;
+                }
+                __syncthreads();
+                if (b >= 0) s_list[s_wc[warp] + __popc(bal & lanemask_lt())] = b;
+                __syncthreads();
+                const int nl = s_wc[kThreads / 32];
+                if (nl > 0) {
+                    const uint32_t* bits = a.ss_bits + ((zt0 - zb) >> 5);
+                    for (int w = tid; w < tw; w += kThreads) {
+                        uint32_t acc = 0u;
+                        for (int i = 0; i < nl; ++i) acc |= __ldg(bits + a.bm_off[s_list[i]] + w);
+                        if (acc) bm[w] |= acc;
+                    }
+                }
+                __syncthreads();
+            }
         }
         // DenseEC result of this x (disjoint from the sparse z set), over the
         // dense indices of x's instance
@@ -313,7 +382,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
             // warps' output offsets come from one popcount pass; after that
             // every warp compacts and writes its run without block barriers.
             const int groups = (tw + 31) >> 5;
-            const int gpw = (((groups + kWarps - 1) / kWarps) + 3) & ~3;  // whole 4-group chunks per warp
+            const int gpw = (groups + kWarps - 1) / kWarps;  // chunk reads below are masked at g1
             const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
             int mine = 0;
             for (int g = g0; g < g1; ++g) {
@@ -323,6 +392,19 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
             mine = warp_sum(mine);
             if (lane == 0) s_wc[warp] = mine;
             __syncthreads();
+            if (a.lb_status) {
+                int64_t agg = 0;
+                for (int w = 0; w < kWarps; ++w) agg += s_wc[w];
+                if (warp == 0) {
+                    const int64_t pre = lookback_prefix(a.lb_status, xr, agg, a.lb_err, kLookbackWaitNs);
+                    if (lane == 0) s_prefix = pre;
+                }
+                __syncthreads();
+                const int64_t pre = s_prefix;
+                write = pre >= 0 && pre + agg <= a.capacity;
+                out_pos = pre;
+                if (write) fill_range(a.out_x, pre, pre + agg, a.dict_x[x], a.vec_ok);
+            }
             int64_t wpos = out_pos, tile_total = 0;
             for (int w = 0; w < kWarps; ++w) {
                 const int c = s_wc[w];
@@ -333,13 +415,30 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
             // into z values only when the stage is flushed: a sparse row
             // then costs one round of independent dictionary gathers per
             // ~1000 pairs instead of one dependent round per group.
-            int32_t* st = stage + warp * kWarpStageIds;
+            int32_t* st = stage + warp * a.stage_ints;
             const unsigned lt = lanemask_lt();
             int sh = (int)(wpos & 3), sc = 0;  // stage holds pairs [wpos, wpos + sc) at st[sh ..]
             // Chunks of 4 groups (128 words, 4096 z): lane l first reads words
             // 4l .. 4l+3; a sparse chunk is extracted lane by lane in one step,
             // a dense one group by group with the transposed dictionary reads.
-            for (int gc = g0; gc < g1; gc += 4) {
+            // A dense run (an eighth of its bits set or more, large stage):
+            // every group straight through compact_group, no chunk scan.
+            const bool dense_run = a.stage_ints >= kWarpStage && (int64_t)mine * 8 >= (int64_t)(g1 - g0) * 1024;
+            for (int g = g0; write && dense_run && g < g1; ++g) {
+                const int w = (g << 5) + lane;
+                const uint32_t word = w < tw ? bm[w] : 0u;
+                const int c = __popc(word);
+                const int incl = warp_inclusive_scan(c);
+                const int total_g = __shfl_sync(kFull, incl, 31);
+                if (total_g == 0) continue;
+                sh = (int)(wpos & 3);
+                compact_group(st, sh, word, incl - c, total_g, a.dict_z + zt0 + ((int64_t)g << 10), lane, lt);
+                __syncwarp();
+                flush_warp(a.out_z + (wpos - sh), st, sh, total_g, a.vec_ok);
+                __syncwarp();
+                wpos += total_g;
+            }
+            for (int gc = g0; write && !dense_run && gc < g1; gc += 4) {
                 const int wl = (gc << 5) + (lane << 2);
                 const int wlim = min(tw, g1 << 5);
                 uint32_t wv[4];
@@ -352,8 +451,8 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
                 const int incl4 = warp_inclusive_scan(c4);
                 const int total_c = __shfl_sync(kFull, incl4, 31);
                 if (total_c == 0) continue;
-                if (total_c <= 512) {
-                    if (sh + sc + total_c > kWarpStageIds) {
+                if (total_c <= a.id_max) {
+                    if (sh + sc + total_c > a.stage_ints) {
                         __syncwarp();
                         flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
                         __syncwarp();
@@ -374,32 +473,37 @@ __global__ void __launch_bounds__(kThreads) k_xrow_bits(const XRowArgs a) {
                     sc += total_c;
                     continue;
                 }
-                // dense chunk: half-groups (16 words, at most 512 set bits) so
-                // that one always fits the stage after a flush
-                for (int h = gc * 2; h < min(gc + 4, g1) * 2; ++h) {
-                    const int g = h >> 1;
+                // dense chunk: write z values directly (coalesced dictionary
+                // reads, lane l reading entry 32 j + l), one half-group (16
+                // words, at most 512 pairs) per flush; pending ids go first
+                if (sc) {
+                    __syncwarp();
+                    flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
+                    __syncwarp();
+                    wpos += sc;
+                    sc = 0;
+                }
+                const int per = a.stage_ints >= kWarpStage ? 1 : 2;  // whole groups fit a large stage
+                for (int h = gc * per; h < min(gc + 4, g1) * per; ++h) {
+                    const int g = h / per;
                     const int w = (g << 5) + lane;
-                    const bool mine_half = (lane >> 4) == (h & 1);
+                    const bool mine_half = per == 1 || (lane >> 4) == (h & 1);
                     const uint32_t word = (mine_half && w < tw) ? bm[w] : 0u;
                     const int c = __popc(word);
                     const int incl = warp_inclusive_scan(c);
                     const int total_g = __shfl_sync(kFull, incl, 31);
                     if (total_g == 0) continue;
-                    if (sh + sc + total_g > kWarpStageIds) {
-                        __syncwarp();
-                        flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
-                        __syncwarp();
-                        wpos += sc;
-                        sh = (int)(wpos & 3);
-                        sc = 0;
-                    }
-                    stage_group_ids(st + sh + sc, word, incl - c, (int32_t)(zt0 + ((int64_t)g << 10)), lane, lt,
-                                    total_g);
-                    sc += total_g;
+                    sh = (int)(wpos & 3);
+                    compact_group(st, sh, word, incl - c, total_g, a.dict_z + zt0 + ((int64_t)g << 10), lane, lt);
+                    __syncwarp();
+                    flush_warp(a.out_z + (wpos - sh), st, sh, total_g, a.vec_ok);
+                    __syncwarp();
+                    wpos += total_g;
                 }
+                sh = (int)(wpos & 3);
             }
             __syncwarp();
-            if (sc) flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
+            if (write && sc) flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
             __syncwarp();
             out_pos += tile_total;
         }
@@ -420,10 +524,22 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
     uint32_t* bm_all = smem + kWarps * kWarpStage;      // G bitmaps of tile_words words
     __shared__ int32_t s_list[kThreads];
     __shared__ int32_t s_lk[kThreads];
+    __shared__ int32_t s_ny[kThreads];
+    __shared__ int32_t s_nk[kThreads];
+    __shared__ int64_t s_woff[kThreads];
     __shared__ int32_t s_wc[kWarps + 1];
+    __shared__ int32_t s_cw[kWarps], s_cn[kWarps];
     __shared__ int32_t s_seg[G][kWarps];
+    __shared__ int64_t s_blk, s_prefix;
 
-    const int64_t xr0 = (int64_t)blockIdx.x * G;
+    // single pass: logical block number from a ticket (dispatch order)
+    int64_t blk = blockIdx.x;
+    if (a.lb_status) {
+        if (threadIdx.x == 0) s_blk = (int64_t)atomicAdd(a.lb_ticket, 1ull);
+        __syncthreads();
+        blk = s_blk;
+    }
+    const int64_t xr0 = blk * G;
     if (xr0 >= a.n_rows) return;
     const int ng = (int)min64(G, a.n_rows - xr0);
     const int64_t x0 = a.x_begin + xr0;
@@ -431,14 +547,18 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
     const unsigned lt = lanemask_lt();
     const int64_t tile_words = a.tile_bits >> 5;
     const bool tiled = a.tile_bits < a.n_z;
-    // R_CSR rows of the group are adjacent: [rb[0], rb[ng])
+    // R_CSR rows of the group are adjacent: [rb[0], r_end); rb is indexed
+    // only with unrolled constants so that it stays in registers
     int64_t rb[G + 1];
 #pragma unroll
     for (int k = 0; k <= G; ++k) rb[k] = a.r_rowptr[x0 + min(k, ng)];
+    const int64_t r_end = a.r_rowptr[x0 + ng];
     int64_t out_pos[G];
+    bool write = true;
 #pragma unroll
     for (int k = 0; k < G; ++k) {
-        if (k < ng) {
+        out_pos[k] = 0;
+        if (k < ng && !a.lb_status) {
             out_pos[k] = a.off[xr0 + k];
             fill_range(a.out_x, out_pos[k], a.off[xr0 + k + 1], a.dict_x[x0 + k], a.vec_ok);
         }
@@ -450,68 +570,147 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
         return k;
     };
 
+    // At most kThreads R entries (the usual case): one thread per entry sorts
+    // them once into per-warp lists of narrow rows (y, row) and wide rows
+    // (bitmap, row); each tile then builds its bitmaps in ONE barrier-free
+    // phase, warps walking narrow rows while every thread ORs wide rows into
+    // its words (both with shared atomics).
+    const int64_t n_ent = r_end - rb[0];
+    const bool flat = n_ent <= a.flat_max;  // block-uniform
+    if (flat) {
+        const int64_t p = rb[0] + tid;
+        int32_t y = -1, b = -1;
+        if (tid < n_ent) {
+            y = a.r_col[p];
+            b = a.bm_row_of_y[y];
+        }
+        const bool isw = b >= 0, isn = tid < n_ent && b < 0;
+        const unsigned bw = __ballot_sync(kFull, isw), bn = __ballot_sync(kFull, isn);
+        const int k = tid < n_ent ? row_of(p) : 0;
+        if (isw) {
+            const int slot = (warp << 5) + __popc(bw & lt);
+            s_woff[slot] = a.bm_off[b];
+            s_lk[slot] = k;
+        }
+        if (isn) {
+            const int slot = (warp << 5) + __popc(bn & lt);
+            s_ny[slot] = y;
+            s_nk[slot] = k;
+        }
+        if (lane == 0) {
+            s_cw[warp] = __popc(bw);
+            s_cn[warp] = __popc(bn);
+        }
+    }
+
     for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += a.tile_bits) {
         const int64_t zt1 = min64(zt0 + a.tile_bits, a.n_z);
         const int tw = (int)((zt1 - zt0 + 31) >> 5);
         clear_words(bm_all, (int)(ng * tile_words));
         __syncthreads();
-        // narrow S_sparse rows of all G rows: one warp per R entry
-        for (int64_t p = rb[0] + warp; p < rb[ng]; p += kWarps) {
-            const int32_t y = a.r_col[p];
-            if (a.bm_row_of_y[y] >= 0) continue;
-            uint32_t* bm = bm_all + row_of(p) * tile_words;
-            int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
-            if (tiled) {
-                s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
-                s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
+        if (flat) {
+            int n_nar = 0;
+            unsigned wmask = 0u;  // warps whose list holds wide rows
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                n_nar += s_cn[w];
+                wmask |= s_cw[w] > 0 ? 1u << w : 0u;
             }
-            for (int64_t q = s0 + lane; q < s1; q += 32) {
-                const int32_t z = a.ss_col[q] - (int32_t)zt0;
-                atomicOr(&bm[z >> 5], 1u << (z & 31));
-            }
-        }
-        // wide S_sparse rows
-        for (int64_t base = rb[0]; base < rb[ng]; base += kThreads) {
-            const int64_t p = base + tid;
-            const int32_t b = p < rb[ng] ? a.bm_row_of_y[a.r_col[p]] : -1;
-            const unsigned bal = __ballot_sync(kFull, b >= 0);
-            if (lane == 0) s_wc[warp] = __popc(bal);
-            __syncthreads();
-            if (tid == 0) {
-                int run = 0;
-                for (int w = 0; w < kWarps; ++w) {
-                    const int c = s_wc[w];
-                    s_wc[w] = run;
-                    run += c;
+            for (int e = warp; e < n_nar; e += kWarps) {
+                int sg = 0, base = 0;
+                while (e - base >= s_cn[sg]) base += s_cn[sg++];
+                const int slot = (sg << 5) + (e - base);
+                const int32_t y = s_ny[slot];
+                uint32_t* bm = bm_all + s_nk[slot] * tile_words;
+                int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+                if (tiled) {
+                    s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
+                    s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
                 }
-                s_wc[kWarps] = run;
+                for (int64_t q = s0 + lane; q < s1; q += 32) {
+                    const int32_t z = a.ss_col[q] - (int32_t)zt0;
+                    atomicOr(&bm[z >> 5], 1u << (z & 31));
+                }
             }
-            __syncthreads();
-            if (b >= 0) {
-                const int slot = s_wc[warp] + __popc(bal & lt);
-                s_list[slot] = b;
-                s_lk[slot] = row_of(p);
-            }
-            __syncthreads();
-            const int nl = s_wc[kWarps];
-            if (nl > 0) {
+            if (wmask) {
                 const uint32_t* bits = a.ss_bits + (zt0 >> 5);
                 for (int w = tid; w < tw; w += kThreads) {
                     uint32_t acc[G];
 #pragma unroll
                     for (int k = 0; k < G; ++k) acc[k] = 0u;
-                    for (int i = 0; i < nl; ++i) {
-                        const uint32_t v = __ldg(bits + a.bm_off[s_list[i]] + w);
-                        const int k = s_lk[i];
+                    for (unsigned m = wmask; m; m &= m - 1) {
+                        const int sg = __ffs(m) - 1, c = s_cw[sg];
+                        for (int i = sg << 5; i < (sg << 5) + c; ++i) {
+                            const uint32_t v = __ldg(bits + s_woff[i] + w);
+                            const int k = s_lk[i];
 #pragma unroll
-                        for (int q = 0; q < G; ++q) acc[q] |= (k == q) ? v : 0u;
+                            for (int q = 0; q < G; ++q) acc[q] |= (k == q) ? v : 0u;
+                        }
                     }
 #pragma unroll
                     for (int k = 0; k < G; ++k)
-                        if (k < ng && acc[k]) bm_all[k * tile_words + w] |= acc[k];
+                        if (k < ng && acc[k]) atomicOr(&bm_all[k * tile_words + w], acc[k]);
                 }
             }
-            __syncthreads();
+        } else {
+            // narrow S_sparse rows of all G rows: one warp per R entry
+            for (int64_t p = rb[0] + warp; p < r_end; p += kWarps) {
+                const int32_t y = a.r_col[p];
+                if (a.bm_row_of_y[y] >= 0) continue;
+                uint32_t* bm = bm_all + row_of(p) * tile_words;
+                int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+                if (tiled) {
+                    s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
+                    s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
+                }
+                for (int64_t q = s0 + lane; q < s1; q += 32) {
+                    const int32_t z = a.ss_col[q] - (int32_t)zt0;
+                    atomicOr(&bm[z >> 5], 1u << (z & 31));
+                }
+            }
+            // wide S_sparse rows
+            for (int64_t base = rb[0]; base < r_end; base += kThreads) {
+                const int64_t p = base + tid;
+                const int32_t b = p < r_end ? a.bm_row_of_y[a.r_col[p]] : -1;
+                const unsigned bal = __ballot_sync(kFull, b >= 0);
+                if (lane == 0) s_wc[warp] = __popc(bal);
+                __syncthreads();
+                if (tid == 0) {
+                    int run = 0;
+                    for (int w = 0; w < kWarps; ++w) {
+                        const int c = s_wc[w];
+                        s_wc[w] = run;
+                        run += c;
+                    }
+                    s_wc[kWarps] = run;
+                }
+                __syncthreads();
+                if (b >= 0) {
+                    const int slot = s_wc[warp] + __popc(bal & lt);
+                    s_list[slot] = b;
+                    s_lk[slot] = row_of(p);
+                }
+                __syncthreads();
+                const int nl = s_wc[kWarps];
+                if (nl > 0) {
+                    const uint32_t* bits = a.ss_bits + (zt0 >> 5);
+                    for (int w = tid; w < tw; w += kThreads) {
+                        uint32_t acc[G];
+#pragma unroll
+                        for (int k = 0; k < G; ++k) acc[k] = 0u;
+                        for (int i = 0; i < nl; ++i) {
+                            const uint32_t v = __ldg(bits + a.bm_off[s_list[i]] + w);
+                            const int k = s_lk[i];
+#pragma unroll
+                            for (int q = 0; q < G; ++q) acc[q] |= (k == q) ? v : 0u;
+                        }
+#pragma unroll
+                        for (int k = 0; k < G; ++k)
+                            if (k < ng && acc[k]) bm_all[k * tile_words + w] |= acc[k];
+                    }
+                }
+                __syncthreads();
+            }
         }
         if (a.n_zd > 0) {
             for (int k = 0; k < ng; ++k) {
@@ -550,6 +749,30 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
             if (lane == 0) s_seg[k][warp] = mine;
         }
         __syncthreads();
+        if (a.lb_status) {
+            // single pass (one z tile): this block's rows start after all
+            // earlier blocks' pairs
+            int64_t agg = 0;
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                for (int w = 0; w < kWarps; ++w) agg += k < ng ? s_seg[k][w] : 0;
+            if (warp == 0) {
+                const int64_t pre = lookback_prefix(a.lb_status, blk, agg, a.lb_err, kLookbackWaitNs);
+                if (lane == 0) s_prefix = pre;
+            }
+            __syncthreads();
+            const int64_t pre = s_prefix;
+            write = pre >= 0 && pre + agg <= a.capacity;
+            int64_t run = pre;
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                int64_t ck = 0;
+                for (int w = 0; w < kWarps; ++w) ck += k < ng ? s_seg[k][w] : 0;
+                out_pos[k] = run;
+                if (write && k < ng) fill_range(a.out_x, run, run + ck, a.dict_x[x0 + k], a.vec_ok);
+                run += ck;
+            }
+        }
         int64_t wpos[G];
 #pragma unroll
         for (int k = 0; k < G; ++k) {
@@ -564,7 +787,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
         }
         int32_t* st = stage + warp * kWarpStage;
         const int64_t zlim = a.n_z - zt0;
-        for (int g = g0; g < g1; ++g) {
+        for (int g = g0; write && g < g1; ++g) {
             const int w = (g << 5) + lane;
             uint32_t word[G];
             bool any = false;
@@ -708,8 +931,8 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
 }
 
 // ----------------------------------------------------------------- host side
-static size_t bits_smem(int64_t tile_bits, bool emit) {
-    return (emit ? (size_t)kWarps * kWarpStageIds * 4 : 0) + (size_t)(tile_bits / 32) * 4;
+static size_t bits_smem(int64_t tile_bits, bool emit, int stage_ints) {
+    return (emit ? (size_t)kWarps * stage_ints * 4 : 0) + (size_t)(tile_bits / 32) * 4;
 }
 static size_t cnt_smem(int64_t tile_bits) { return (size_t)(kCntChunk + 8) * 8 + (size_t)tile_bits * 4; }
 
@@ -718,7 +941,7 @@ static void setup_attrs(const Ctx& ctx) {
     static bool done[64] = {false};
     const int d = ctx.device & 63;
     if (done[d]) return;
-    const int bits_max = (int)bits_smem(kMaxTileWords * 32, true);
+    const int bits_max = (int)bits_smem(kMaxTileWords * 32, true, kWarpStage);
     const int cnt_max = (int)cnt_smem(kMaxCntTile);
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
@@ -788,6 +1011,9 @@ static XRowArgs make_args(const Plan& p, int64_t x_begin, int64_t rows, int kind
     a.zd_list = p.zd_list.as<int32_t>();
     a.dict_x = p.dict_x.as<int32_t>();
     a.dict_z = p.dict_z.as<int32_t>();
+    a.stage_ints = kWarpStageIds;
+    a.id_max = 512;
+    a.flat_max = kThreads;
     return a;
 }
 
@@ -803,6 +1029,32 @@ static int emit_rows_per_cta(const Ctx& ctx, int64_t tile_bits) {
     if (want == 1 || want == 2 || want == 4) return fits(want, cap) ? (int)want : 1;
     if (fits(2, 112 * 1024)) return 2;
     return 1;
+}
+
+// Staged entries per warp for the one-row emitting kernel: the large stage
+// (whole 1024-z groups per flush) when the range's output fills more than 2 %
+// of its rows' z-window bits, else the small one (more CTAs per SM). `pairs`
+// is the exact result size or an upper bound of it.
+static int stage_for(const Plan& p, int64_t x_begin, int64_t rows, int64_t pairs) {
+    double bits = 0.0;
+    if (p.n_inst > 1) {
+        const int64_t x_end = x_begin + rows;
+        for (int t = 0; t < p.n_inst; ++t) {
+            const int64_t lo = std::max(x_begin, p.h_inst_x_lo[t]), hi = std::min(x_end, p.h_inst_x_lo[t + 1]);
+            if (hi > lo) bits += (double)(hi - lo) * (double)(p.h_inst_z_lo[t + 1] - p.h_inst_z_lo[t]);
+        }
+    } else {
+        bits = (double)rows * (double)p.info.n_z;
+    }
+    return (double)pairs > 0.02 * bits ? kWarpStage : kWarpStageIds;
+}
+
+// Stage size and id-chunk threshold of an emitting launch; the threshold
+// leaves room for a chunk plus the 16-byte alignment shift in an empty stage.
+static void set_stage(const Ctx& ctx, const Plan& p, XRowArgs& a, int64_t pairs) {
+    a.stage_ints = stage_for(p, a.x_begin, a.n_rows, pairs);
+    const int64_t want = ctx.opt.id_chunk_max < 0 ? 512 : ctx.opt.id_chunk_max;
+    a.id_max = (int)std::min<int64_t>(want, a.stage_ints - 4);
 }
 
 // make_args plus, for z-tiled plans, the per-row tile starts.
@@ -823,7 +1075,7 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
     const unsigned g = (unsigned)a.n_rows;
     PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
     if (kind == 0) {
-        const size_t sm = bits_smem(a.tile_bits, emit);
+        const size_t sm = bits_smem(a.tile_bits, emit, a.stage_ints);
         // several rows per CTA share one z window, so batches use one row per CTA
         const int grp = (emit && a.x_tag == nullptr) ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
         if (emit && grp > 1) {
@@ -912,9 +1164,80 @@ void plan_row_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, in
     }
 }
 
+// off[0] = 0, off[i + 1] = inclusive prefix published by row i
+__global__ void k_status_to_offsets(const unsigned long long* status, int64_t rows, int64_t* off) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= rows; i += (int64_t)gridDim.x * blockDim.x)
+        off[i] = i == 0 ? 0 : (int64_t)(status[i - 1] & kLbVal);
+}
+
+// Join-Project of a range in ONE emitting pass (no counting pass): every CTA
+// counts its rows' pairs, finds its output offset by decoupled look-back over
+// the CTAs before it and writes at once. Used when each row's bitmap fits one
+// z tile and the caller gave output buffers.
+static int64_t plan_join_single_pass(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int32_t* out_x,
+                                     int32_t* out_z, int64_t capacity, int64_t* count, cudaStream_t s) {
+    const int64_t rows = x_end - x_begin;
+    DevBuf dbits;
+    if (p.info.n_z_dense > 0) {
+        dbits.alloc((size_t)(rows * p.zdw) * 4, s);
+        dense_ec(ctx, p, x_begin, rows, 0, dbits.as<uint32_t>(), nullptr, s);
+    }
+    XRowArgs a = prep_args(p, x_begin, rows, 0, s);
+    a.d_bits = dbits.as<uint32_t>();
+    a.out_x = out_x;
+    a.out_z = out_z;
+    a.vec_ok = ((reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z)) & 15u) == 0;
+    const int grp = a.x_tag == nullptr ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
+    const int64_t nb = ceil_div(rows, grp);
+    DevBuf status, ticket, err;
+    status.alloc((size_t)nb * 8, s);
+    ticket.alloc(8, s);
+    err.alloc(4, s);
+    DIM3_CUDA(cudaMemsetAsync(status.p, 0, (size_t)nb * 8, s));
+    DIM3_CUDA(cudaMemsetAsync(ticket.p, 0, 8, s));
+    DIM3_CUDA(cudaMemsetAsync(err.p, 0, 4, s));
+    a.lb_status = status.as<unsigned long long>();
+    a.lb_ticket = ticket.as<unsigned long long>();
+    a.lb_err = err.as<int>();
+    a.capacity = capacity;
+    set_stage(ctx, p, a, std::min<int64_t>(p.info.out_j, capacity));
+    launch_rows(ctx, a, 0, true, s);
+    unsigned long long last = 0;
+    int h_err = 0;
+    DIM3_CUDA(cudaMemcpyAsync(&last, status.as<unsigned long long>() + nb - 1, 8, cudaMemcpyDeviceToHost, s));
+    DIM3_CUDA(cudaMemcpyAsync(&h_err, err.p, 4, cudaMemcpyDeviceToHost, s));
+    DIM3_CUDA(cudaStreamSynchronize(s));
+    DIM3_REQUIRE(h_err == 0 && (last >> 62) == 2ull, DIM3_ERR_TIMEOUT,
+                 "single-pass compaction: a block's offset was not published in time");
+    const int64_t total = (int64_t)(last & kLbVal);
+    if (grp == 1) {
+        // one row per block: the inclusive prefixes are the row offsets; keep
+        // them (and the dense result) as the plan's counting-pass cache
+        p.cache_off.alloc((size_t)(rows + 1) * 8, s);
+        const unsigned g = (unsigned)std::min<int64_t>(ceil_div(rows + 1, kThreads), 4096);
+        k_status_to_offsets<<<g, kThreads, 0, s>>>(status.as<unsigned long long>(), rows, p.cache_off.as<int64_t>());
+        DIM3_LAUNCHED();
+        p.cache_dbits = std::move(dbits);
+        p.cache_dcnt.release();
+        p.cache_begin = x_begin;
+        p.cache_end = x_end;
+        p.cache_kind = 0;
+        DIM3_CUDA(cudaStreamSynchronize(s));
+    }
+    if (count) *count = total;
+    if (total > capacity)
+        throw Error(DIM3_ERR_CAPACITY,
+                    "output capacity " + std::to_string(capacity) + " < result size " + std::to_string(total));
+    return total;
+}
+
 int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int kind, int32_t* out_x, int32_t* out_z,
                   int32_t* out_cnt, int64_t capacity, int64_t* count, cudaStream_t s) {
     check_range(p, x_begin, x_end);
+    const bool cached = p.cache_begin == x_begin && p.cache_end == x_end && p.cache_kind == kind;
+    if (!cached && kind == 0 && capacity > 0 && out_x && out_z && x_end > x_begin && p.info.n_z > 0 &&
+        p.info.n_r_kept > 0 && p.zw <= kMaxTileWords && !ctx.opt.two_pass)
+        return plan_join_single_pass(ctx, p, x_begin, x_end, out_x, out_z, capacity, count, s);
     ensure_counts(ctx, p, x_begin, x_end, kind, s);
     const int64_t rows = x_end - x_begin;
     const int64_t total = read_i64(p.cache_off.as<int64_t>() + rows, s);
@@ -933,6 +1256,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
         const uintptr_t al = reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z) |
                              (kind ? reinterpret_cast<uintptr_t>(out_cnt) : 0);
         a.vec_ok = (al & 15u) == 0;
+        set_stage(ctx, p, a, total);
         launch_rows(ctx, a, kind, true, s);
     }
     DIM3_CUDA(cudaStreamSynchronize(s));

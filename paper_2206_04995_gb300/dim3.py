@@ -27,6 +27,8 @@ DIM3_ERR_UNSUPPORTED = -7
 DENSE_AUTO, DENSE_TC, DENSE_POPC, DENSE_PROBE = 0, 1, 2, 3
 OPT_THETA_Z, OPT_DENSE_VARIANT, OPT_BITMAP_ROW_MIN, OPT_LIGHT_ROW_MAX, OPT_TIMING = 1, 2, 3, 4, 5
 OPT_EMIT_ROWS = 6
+OPT_TWO_PASS = 7
+OPT_ID_CHUNK_MAX = 8
 PHASES = {"map": 0, "partition": 1, "dense_ec": 2, "sparse_count": 3, "sparse_emit": 4, "dense_tc": 5}
 
 TABLES = {
