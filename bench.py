@@ -142,14 +142,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current source of that kernel."""
+def traffic_for(workload: str):
+    """DRAM bytes per launch of the emitting kernel on `workload` from the
+    committed ncu summary (scaled to the full launch), if it was taken on the
+    current source of that kernel; else (None, entry or None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        e = d[kernel]
+        e = d[workload]
         import hashlib
 
         src = os.path.join(ROOT, "paper_2206_04995_gb300", "csrc", e["source"])
@@ -342,8 +343,9 @@ def main():
         emit_s = emit_ms / 1e3 / max(emit_n, 1)
         alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
         achieved = alg_bytes / emit_s / 1e9
-        traffic, _ = traffic_for("k_xrow_bits_emit")
-        roofline = {"bound": "hbm", "kernel": "k_xrow_emit_g / k_xrow_bits<emit> (SparseBMM+union+compaction)",
+        traffic, tinfo = traffic_for(args.workload)
+        kname = (tinfo or {}).get("kernel", "k_xrow_emit_g / k_xrow_bits<emit>")
+        roofline = {"bound": "hbm", "kernel": f"{kname} (SparseBMM+union+compaction)",
                     "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s", "frac": achieved / peaks["hbm"],
                     "peak_source": peaks["source"], "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
                     "launch_ms": emit_s * 1e3}
