@@ -9,6 +9,9 @@ shares no code with that path.
   classical solution (Section 1.1): hash join on y, hash-based duplicate
   elimination, sort (``oracle.c``).
 * ``rank_map`` -- the order-preserving value mapping (Section 2.2).
+* ``join_project_ids`` / ``join_count_ids`` / ``map_tuples`` -- Section 2.2's
+  skipped mapping (Optimization 1) and multi-attribute mapping
+  (``mapping.py``).
 * ``plan`` -- the mapping and partition quantities of Algorithm 1 (semi-join
   filtered y dictionary of Section 2.2 "Optimization 2", x/z dictionaries,
   degrees m_x and m_z, |OUT_J|, the dense z set of Section 2.3) written out
@@ -26,4 +29,5 @@ from .core import (  # noqa: F401
     lib_path,
     rank_map,
 )
+from .mapping import join_count_ids, join_project_ids, map_tuples  # noqa: F401
 from .plan import plan  # noqa: F401
