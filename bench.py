@@ -52,6 +52,8 @@ def parse_args():
                     help="library option KEY=VALUE (dim3_option number), e.g. 6=1 for one x row per emitting CTA")
     ap.add_argument("--serve-queries", type=int, default=200)
     ap.add_argument("--serve-max-tuples", type=int, default=200_000)
+    ap.add_argument("--premapped", action="store_true",
+                    help="columns given as ids (mapping skipped, dim3_partition_ids); ids made on the host before timing")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -72,6 +74,18 @@ def make_workload(name: str, rank: int = 0, scale: float = 1.0):
         return gen.two_table(np.random.default_rng(7 + 1000 * rank), 16 * n * n // 1024, 16 * n * n // 1024,
                              n, n, n, 0.0, name=f"dense_{n}")
     return gen.config3_chung_lu(seed=2 + 1000 * rank, scale=scale)
+
+
+def premap(inst):
+    """Rank ids of an instance's columns, as a database would hold them for
+    auto-increment or dictionary-encoded columns: y over S.y (R tuples whose y
+    is not in S.y get -1), x over R.x, z over S.z. Host numpy, outside any
+    timed region."""
+    yv, xv, zv = np.unique(inst.s_key), np.unique(inst.r_val), np.unique(inst.s_val)
+    r_y = np.searchsorted(yv, inst.r_key)
+    r_y = np.where((r_y < yv.size) & (yv[np.minimum(r_y, max(yv.size - 1, 0))] == inst.r_key), r_y, -1)
+    cols = (r_y, np.searchsorted(xv, inst.r_val), np.searchsorted(yv, inst.s_key), np.searchsorted(zv, inst.s_val))
+    return [np.ascontiguousarray(c, np.int32) for c in cols], (xv.size, yv.size, zv.size)
 
 
 def measured_peaks():
@@ -259,8 +273,11 @@ def main():
 
     inst = make_workload(args.workload, rank, args.scale)
     dev = torch.device("cuda", local_rank)
-    cols = [torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(dev)
-            for a in (inst.r_key, inst.r_val, inst.s_key, inst.s_val)]
+    host_cols = [inst.r_key, inst.r_val, inst.s_key, inst.s_val]
+    ranges = None
+    if args.premapped:
+        host_cols, ranges = premap(inst)
+    cols = [torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(dev) for a in host_cols]
     ctx = dim3.Context(local_rank)
     dense_wl = args.workload.startswith("dense")
     theta = args.theta_z if args.theta_z is not None else (0 if dense_wl else None)
@@ -273,8 +290,19 @@ def main():
         k, v = kv.split("=")
         ctx.set_option(int(k), int(v))
 
+    def join_call(c, ox, oz):
+        """The public path: one dim3_join_project, or, for pre-mapped ids,
+        dim3_partition_ids + dim3_plan_join_project + dim3_plan_destroy."""
+        if ranges is None:
+            return ctx.join_project(*c, out_x=ox, out_z=oz)
+        pl = ctx.partition_ids(*c, *ranges)
+        try:
+            return pl.join_project(out_x=ox, out_z=oz)
+        finally:
+            pl.close()
+
     # size the output once (plan path), then time the one-call path
-    plan = ctx.partition(*cols)
+    plan = ctx.partition_ids(*cols, *ranges) if ranges else ctx.partition(*cols)
     info = plan.info
     out_p = int(plan.row_counts().sum().item())
     plan.close()
@@ -283,7 +311,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > 129 MB L2
 
     def step():
-        x, _ = ctx.join_project(*cols, out_x=out_x, out_z=out_z)
+        x, _ = join_call(cols, out_x, out_z)
         return x.numel()
 
     for _ in range(args.warmup):
@@ -352,7 +380,7 @@ def main():
 
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
-        e2e = run_e2e(torch, ctx, inst, dev, out_p, args.e2e_steps)
+        e2e = run_e2e(torch, host_cols, join_call, dev, out_p, args.e2e_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -368,6 +396,8 @@ def main():
                        "out_p": out_p, "out_j": info["out_j"], "theta_z": info["theta_z"],
                        "l2": "flushed between steps (256 MiB write outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single",
+                       "mapping": ("skipped: pre-mapped id columns (dim3_partition_ids); output pairs are ids"
+                                   if ranges else "order-preserving hash + radix rank (dim3_join_project)"),
                        "join_tuples_per_s": info["out_j"] * args.steps * (pairs_all / total_pairs) / busy_max},
             "roofline": roofline,
             "phase_ms": phases,
@@ -578,19 +608,17 @@ def dataclasses_replace(q):
     return dataclasses.replace(q)
 
 
-def run_e2e(torch, ctx, inst, dev, out_p, steps):
+def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
     """Same metric through the public call with HOST buffers: pinned host
-    inputs copied in, dim3_join_project, both output columns copied out."""
+    inputs copied in, the join (``join_call``), both output columns copied out."""
     pin = True
     try:
-        h_in = [torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
-                for a in (inst.r_key, inst.r_val, inst.s_key, inst.s_val)]
+        h_in = [torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory() for a in host_cols]
         h_x = torch.empty(out_p, dtype=torch.int32, pin_memory=True)
         h_z = torch.empty(out_p, dtype=torch.int32, pin_memory=True)
     except Exception:  # noqa: BLE001
         pin = False
-        h_in = [torch.from_numpy(np.ascontiguousarray(a, np.int32)) for a in
-                (inst.r_key, inst.r_val, inst.s_key, inst.s_val)]
+        h_in = [torch.from_numpy(np.ascontiguousarray(a, np.int32)) for a in host_cols]
         h_x = torch.empty(out_p, dtype=torch.int32)
         h_z = torch.empty(out_p, dtype=torch.int32)
     d_in = [torch.empty_like(h, device=dev) for h in h_in]
@@ -602,7 +630,7 @@ def run_e2e(torch, ctx, inst, dev, out_p, steps):
     def one():
         for d, h in zip(d_in, h_in):
             d.copy_(h, non_blocking=pin)
-        x, z = ctx.join_project(*d_in, out_x=d_x, out_z=d_z)
+        x, z = join_call(d_in, d_x, d_z)
         h_x.copy_(x, non_blocking=pin)
         h_z.copy_(z, non_blocking=pin)
 

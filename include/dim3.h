@@ -189,6 +189,56 @@ DIM3_API int dim3_partition(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t
                    const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns,
                    int32_t theta_z, dim3_plan **plan_out, dim3_plan_info *info, void *stream);
 
+/*
+ * dim3_partition_ids -- dim3_partition for columns that already hold natural
+ * numbers, with the mapping step skipped (Section 2.2, Optimization 1: auto-
+ * increment keys, dictionary-encoded strings, or ids from dim3_map_tuples).
+ *   d_r_y, d_r_x [nr] int32 device: R's y and x ids; d_s_y, d_s_z [ns]: S's.
+ *   n_x, n_y, n_z: the id ranges; every id must be < its range.
+ * A negative id removes its tuple from the input (e.g. an R tuple whose y is
+ * missing from S's dictionary). Ids are used as they are: the plan's x and z
+ * dictionaries are the identity, so the emitted pairs are ids, in id order
+ * (canonical order), and the bitmaps span the declared ranges, however few
+ * ids occur. R tuples whose y no S tuple holds stay in R_CSR with an empty S
+ * row (the semi-join of Optimization 2 belongs to the caller's mapping).
+ * An id >= its range gives DIM3_ERR_ARG and no plan; ranges above 2^31 - 1
+ * too. Synchronises the stream.
+ */
+DIM3_API int dim3_partition_ids(dim3_ctx *ctx, const int32_t *d_r_y, const int32_t *d_r_x, int64_t nr,
+                                const int32_t *d_s_y, const int32_t *d_s_z, int64_t ns, int64_t n_x,
+                                int64_t n_y, int64_t n_z, int32_t theta_z, dim3_plan **plan_out,
+                                dim3_plan_info *info, void *stream);
+
+/*
+ * dim3_map_tuples -- mapping of several attributes together (Section 2.2,
+ * "Supporting Wider Range of Join-Project Operations"): Pi_{a,b,c,d,e}(R(a,b,
+ * c,d) join_{c,d} S(c,d,e,f)) runs as Pi_{x,z}(R(x,y) join_y S(z,y)) with
+ * x = (a,b), y = (c,d), z = (c,d,e). Rows of k int32 columns (1 <= k <= 8) are
+ * numbered by the rank of their tuple among the distinct tuples in
+ * lexicographic order (column 0 most significant).
+ *   d_cols        host array of k device pointers, each [n] int32.
+ *   unsigned_mask bit c set: column c compares as unsigned 32-bit, else as
+ *                 signed (an int64 key is (high word signed, low word unsigned)).
+ *   d_ids         [n] int32 device, out: the tuple rank of each row.
+ *   d_first       [n] int32 device, out: the first *n_distinct entries give,
+ *                 per id, the smallest row holding that tuple (gather the
+ *                 columns there to translate ids back, e.g. dim3_gather_i32).
+ *   n_distinct    host, out.
+ * Ids from one call over R's and S's join columns together share a numbering,
+ * ready for dim3_partition_ids. n < 2^31. Synchronises the stream.
+ */
+DIM3_API int dim3_map_tuples(dim3_ctx *ctx, const int32_t *const *d_cols, int k, uint32_t unsigned_mask,
+                             int64_t n, int32_t *d_ids, int32_t *d_first, int64_t *n_distinct, void *stream);
+
+/*
+ * dim3_gather_i32 -- d_dst[i] = d_src[d_idx[i]] for i < n (int32 device
+ * arrays; d_src has n_src entries). Translates ids back to attribute values
+ * through dim3_map_tuples' d_first. An index outside [0, n_src) gives
+ * DIM3_ERR_ARG, with d_dst[i] = -1 there. Synchronises the stream.
+ */
+DIM3_API int dim3_gather_i32(dim3_ctx *ctx, const int32_t *d_src, int64_t n_src, const int32_t *d_idx, int64_t n,
+                             int32_t *d_dst, void *stream);
+
 /* Copy of the plan's sizes. */
 DIM3_API int dim3_plan_get_info(const dim3_plan *plan, dim3_plan_info *info);
 

@@ -258,6 +258,62 @@ int dim3_partition(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val
     });
 }
 
+int dim3_partition_ids(dim3_ctx* ctx, const int32_t* d_r_y, const int32_t* d_r_x, int64_t nr, const int32_t* d_s_y,
+                       const int32_t* d_s_z, int64_t ns, int64_t n_x, int64_t n_y, int64_t n_z, int32_t theta_z,
+                       dim3_plan** plan_out, dim3_plan_info* info, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && plan_out, DIM3_ERR_ARG, "null ctx or plan_out");
+        *plan_out = nullptr;
+        check_table(d_r_y, d_r_x, nr, "R");
+        check_table(d_s_y, d_s_z, ns, "S");
+        DeviceGuard g(ctx->c.device);
+        dimcube::PlanInput in = single_input(d_r_y, d_r_x, nr, d_s_y, d_s_z, ns);
+        in.premapped = true;
+        in.n_x = n_x;
+        in.n_y = n_y;
+        in.n_z = n_z;
+        std::unique_ptr<dim3_plan> pl(new dim3_plan());
+        pl->p.reset(dimcube::build_plan(ctx->c, in, resolve_theta(ctx, theta_z), as_stream(stream)));
+        if (info) *info = pl->p->info;
+        *plan_out = pl.release();
+    });
+}
+
+int dim3_map_tuples(dim3_ctx* ctx, const int32_t* const* d_cols, int k, uint32_t unsigned_mask, int64_t n,
+                    int32_t* d_ids, int32_t* d_first, int64_t* n_distinct, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && n_distinct, DIM3_ERR_ARG, "null ctx or n_distinct");
+        DIM3_REQUIRE(k >= 1 && k <= dimcube::kMaxTupleCols, DIM3_ERR_ARG, "k must be 1..8");
+        DIM3_REQUIRE(n >= 0, DIM3_ERR_ARG, "negative row count");
+        DIM3_REQUIRE(n < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "more than 2^31 - 1 rows");
+        if (n > 0) {
+            DIM3_REQUIRE(d_cols && d_ids && d_first, DIM3_ERR_ARG, "null column or output pointer");
+            for (int c = 0; c < k; ++c) DIM3_REQUIRE(d_cols[c], DIM3_ERR_ARG, "null column pointer");
+        }
+        DeviceGuard g(ctx->c.device);
+        cudaStream_t s = as_stream(stream);
+        int64_t d = 0;
+        {
+            dimcube::PhaseScope ps(ctx->c.stats, dimcube::PH_MAP, s);
+            d = dimcube::map_tuples(d_cols, k, unsigned_mask, n, d_ids, d_first, s);
+        }
+        DIM3_CUDA(cudaStreamSynchronize(s));
+        *n_distinct = d;
+    });
+}
+
+int dim3_gather_i32(dim3_ctx* ctx, const int32_t* d_src, int64_t n_src, const int32_t* d_idx, int64_t n,
+                    int32_t* d_dst, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx, DIM3_ERR_ARG, "null ctx");
+        DIM3_REQUIRE(n >= 0 && n_src >= 0, DIM3_ERR_ARG, "negative length");
+        DIM3_REQUIRE(n == 0 || (d_idx && d_dst && (n_src == 0 || d_src)), DIM3_ERR_ARG, "null pointer");
+        DeviceGuard g(ctx->c.device);
+        const bool ok = dimcube::gather_i32(d_src, n_src, d_idx, n, d_dst, as_stream(stream));
+        DIM3_REQUIRE(ok, DIM3_ERR_ARG, "an index lies outside [0, n_src)");
+    });
+}
+
 int dim3_plan_get_info(const dim3_plan* plan, dim3_plan_info* info) {
     return guarded([&] {
         DIM3_REQUIRE(plan && info, DIM3_ERR_ARG, "null plan or info");

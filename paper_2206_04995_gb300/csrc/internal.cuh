@@ -36,6 +36,11 @@ struct PlanInput {
     const int32_t *s_key = nullptr, *s_val = nullptr, *s_tag = nullptr;
     int64_t ns = 0;
     int n_inst = 1;
+    // Section 2.2, Optimization 1: the columns already hold natural numbers
+    // (x ids < n_x, y ids < n_y, z ids < n_z; a negative id drops its tuple)
+    // and the mapping step is skipped
+    bool premapped = false;
+    int64_t n_x = 0, n_y = 0, n_z = 0;
 };
 
 // -------------------------------------------------------------------- plan
@@ -151,6 +156,15 @@ void dense_build_operands(const Ctx& ctx, Plan& p, const uint64_t* s_keys_u64, c
 // after a join over all x of that plan.
 Plan* build_batch_plan(const Ctx& ctx, int n_inst, const dim3_instance* inst, int64_t theta_z, cudaStream_t s);
 void batch_instance_counts(const Plan& p, int64_t* host_counts, cudaStream_t s);
+
+// Multi-attribute mapping (tuples.cu): ranks of k-column tuples in
+// lexicographic order (column c unsigned when bit c of unsigned_mask is set),
+// first row of every distinct tuple; returns the number of distinct tuples.
+constexpr int kMaxTupleCols = 8;
+int64_t map_tuples(const int32_t* const* cols, int k, uint32_t unsigned_mask, int64_t n, int32_t* ids, int32_t* first,
+                   cudaStream_t s);
+// dst[i] = src[idx[i]]; false (dst[i] = -1 there) when an index is outside [0, n_src).
+bool gather_i32(const int32_t* src, int64_t n_src, const int32_t* idx, int64_t n, int32_t* dst, cudaStream_t s);
 
 // Value mapping with all scratch in a fixed device array (noalloc.cu).
 void map_noalloc(const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,

@@ -440,6 +440,51 @@ static void instance_ranges(const int32_t* tag_dev, int64_t n, int n_inst, DevBu
     }
 }
 
+__global__ void k_ids_above(const int32_t* v, int64_t n, int64_t limit, int* flag) {
+    GRID_STRIDE(i, n) {
+        if ((int64_t)v[i] >= limit) *flag = 1;
+    }
+}
+
+__global__ void k_iota(int32_t* out, int64_t n) { GRID_STRIDE(i, n) out[i] = (int32_t)i; }
+
+// Skipped mapping (Section 2.2, Optimization 1): check every id column
+// against its range, and make the dictionaries the identity.
+static void premapped_ids(Plan& p, const PlanInput& in, cudaStream_t s) {
+    DIM3_REQUIRE(in.n_inst <= 1, DIM3_ERR_ARG, "pre-mapped ids take a single instance");
+    DIM3_REQUIRE(in.n_x >= 0 && in.n_y >= 0 && in.n_z >= 0 && in.n_x <= INT32_MAX && in.n_y <= INT32_MAX &&
+                     in.n_z <= INT32_MAX,
+                 DIM3_ERR_ARG, "id ranges must lie in [0, 2^31 - 1]");
+    DevBuf flag;
+    flag.alloc(4, s);
+    DIM3_CUDA(cudaMemsetAsync(flag.p, 0, 4, s));
+    const struct {
+        const int32_t* v;
+        int64_t n, lim;
+    } cols[4] = {{in.r_val, in.nr, in.n_x}, {in.r_key, in.nr, in.n_y}, {in.s_key, in.ns, in.n_y}, {in.s_val, in.ns, in.n_z}};
+    for (const auto& c : cols) {
+        if (c.n <= 0) continue;
+        k_ids_above<<<grid_for(c.n), kThreads, 0, s>>>(c.v, c.n, c.lim, flag.as<int>());
+        DIM3_LAUNCHED();
+    }
+    int h = 0;
+    DIM3_CUDA(cudaMemcpyAsync(&h, flag.p, 4, cudaMemcpyDeviceToHost, s));
+    DIM3_CUDA(cudaStreamSynchronize(s));
+    DIM3_REQUIRE(h == 0, DIM3_ERR_ARG, "an id is not below its declared range");
+    p.info.n_x = in.n_x;
+    p.info.n_y = in.n_y;
+    p.info.n_z = in.n_z;
+    DevBuf* dicts[3] = {&p.dict_x, &p.dict_y, &p.dict_z};
+    const int64_t lens[3] = {in.n_x, in.n_y, in.n_z};
+    for (int d = 0; d < 3; ++d) {
+        dicts[d]->alloc((size_t)std::max<int64_t>(lens[d], 1) * 4, s);
+        if (lens[d] > 0) {
+            k_iota<<<grid_for(lens[d]), kThreads, 0, s>>>(dicts[d]->as<int32_t>(), lens[d]);
+            DIM3_LAUNCHED();
+        }
+    }
+}
+
 Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStream_t s) {
     PhaseScope phase(ctx.stats, PH_PARTITION, s);
     std::unique_ptr<Plan> p(new Plan());
@@ -453,51 +498,62 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
     p->info.n_s = ns;
 
     DevBuf sy_id, sz_id, ry_id, rx_id, y_tag, z_tag;
-    sy_id.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-    sz_id.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-    ry_id.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
-    rx_id.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
-    if (batch) {
-        y_tag.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-        z_tag.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-        p->x_tag.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
-    }
-    {
-        // y from S.y; R tuples whose y is absent from S.y get id -1 (dropped)
-        ValueMap ymap;
-        p->dict_y.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-        build_value_map(in.s_key, in.s_tag, p->n_inst, nullptr, ns, ymap, sy_id.as<int32_t>(),
-                        p->dict_y.as<int32_t>(), y_tag.as<int32_t>(), s);
-        p->info.n_y = ymap.n_distinct;
-        probe_value_map(ymap, in.r_key, in.r_tag, nr, ry_id.as<int32_t>(), s);
-    }
-    {
-        ValueMap xmap;
-        p->dict_x.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
-        build_value_map(in.r_val, in.r_tag, p->n_inst, ry_id.as<int32_t>(), nr, xmap, rx_id.as<int32_t>(),
-                        p->dict_x.as<int32_t>(), p->x_tag.as<int32_t>(), s);
-        p->info.n_x = xmap.n_distinct;
-    }
-    {
-        ValueMap zmap;
-        p->dict_z.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-        build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(),
-                        p->dict_z.as<int32_t>(), z_tag.as<int32_t>(), s);
-        p->info.n_z = zmap.n_distinct;
+    const int32_t *rx = nullptr, *ry = nullptr, *sy = nullptr, *sz = nullptr;
+    if (in.premapped) {
+        premapped_ids(*p, in, s);
+        rx = in.r_val;
+        ry = in.r_key;
+        sy = in.s_key;
+        sz = in.s_val;
+    } else {
+        sy_id.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+        sz_id.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+        ry_id.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+        rx_id.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+        if (batch) {
+            y_tag.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+            z_tag.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+            p->x_tag.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+        }
+        {
+            // y from S.y; R tuples whose y is absent from S.y get id -1 (dropped)
+            ValueMap ymap;
+            p->dict_y.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+            build_value_map(in.s_key, in.s_tag, p->n_inst, nullptr, ns, ymap, sy_id.as<int32_t>(),
+                            p->dict_y.as<int32_t>(), y_tag.as<int32_t>(), s);
+            p->info.n_y = ymap.n_distinct;
+            probe_value_map(ymap, in.r_key, in.r_tag, nr, ry_id.as<int32_t>(), s);
+        }
+        {
+            ValueMap xmap;
+            p->dict_x.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+            build_value_map(in.r_val, in.r_tag, p->n_inst, ry_id.as<int32_t>(), nr, xmap, rx_id.as<int32_t>(),
+                            p->dict_x.as<int32_t>(), p->x_tag.as<int32_t>(), s);
+            p->info.n_x = xmap.n_distinct;
+        }
+        {
+            ValueMap zmap;
+            p->dict_z.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+            build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(),
+                            p->dict_z.as<int32_t>(), z_tag.as<int32_t>(), s);
+            p->info.n_z = zmap.n_distinct;
+        }
+        rx = rx_id.as<int32_t>();
+        ry = ry_id.as<int32_t>();
+        sy = sy_id.as<int32_t>();
+        sz = sz_id.as<int32_t>();
     }
     instance_ranges(p->x_tag.as<int32_t>(), p->info.n_x, p->n_inst, p->inst_x_lo, p->h_inst_x_lo, s);
     instance_ranges(z_tag.as<int32_t>(), p->info.n_z, p->n_inst, p->inst_z_lo, p->h_inst_z_lo, s);
     const int bx = bits_for(p->info.n_x), by = bits_for(p->info.n_y), bz = bits_for(p->info.n_z);
     if (bx + by <= 32)
-        build_r_side<uint32_t>(*p, rx_id.as<int32_t>(), ry_id.as<int32_t>(), nr, bx, by, s);
+        build_r_side<uint32_t>(*p, rx, ry, nr, bx, by, s);
     else
-        build_r_side<uint64_t>(*p, rx_id.as<int32_t>(), ry_id.as<int32_t>(), nr, bx, by, s);
+        build_r_side<uint64_t>(*p, rx, ry, nr, bx, by, s);
     if (by + bz <= 32)
-        build_s_side<uint32_t>(ctx, *p, sy_id.as<int32_t>(), sz_id.as<int32_t>(), ns, by, bz, theta_z,
-                               y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
+        build_s_side<uint32_t>(ctx, *p, sy, sz, ns, by, bz, theta_z, y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
     else
-        build_s_side<uint64_t>(ctx, *p, sy_id.as<int32_t>(), sz_id.as<int32_t>(), ns, by, bz, theta_z,
-                               y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
+        build_s_side<uint64_t>(ctx, *p, sy, sz, ns, by, bz, theta_z, y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
     if (batch) p->y_tag = std::move(y_tag);
     DIM3_CUDA(cudaStreamSynchronize(s));
     return p.release();

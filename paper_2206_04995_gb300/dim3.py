@@ -95,6 +95,10 @@ def load(build_if_missing: bool = True):
             "dim3_launch_count": ([ctypes.POINTER(I64)], INT),
             "dim3_map": ([P, P, I64, P, P, ctypes.POINTER(I64), P], INT),
             "dim3_partition": ([P, P, P, I64, P, P, I64, I32, ctypes.POINTER(P), ctypes.POINTER(PlanInfo), P], INT),
+            "dim3_partition_ids": ([P, P, P, I64, P, P, I64, I64, I64, I64, I32, ctypes.POINTER(P),
+                                    ctypes.POINTER(PlanInfo), P], INT),
+            "dim3_map_tuples": ([P, P, ctypes.c_int, ctypes.c_uint32, I64, P, P, ctypes.POINTER(I64), P], INT),
+            "dim3_gather_i32": ([P, P, I64, P, I64, P, P], INT),
             "dim3_plan_get_info": ([P, ctypes.POINTER(PlanInfo)], INT),
             "dim3_plan_row_counts": ([P, P, I64, I64, P, P], INT),
             "dim3_plan_join_project": ([P, P, I64, I64, P, P, I64, ctypes.POINTER(I64), P], INT),
@@ -193,7 +197,44 @@ class Context:
                                   _stream(self.device, stream)))
         return ids, d[: nd.value]
 
+    def map_tuples(self, cols, unsigned_mask: int = 0, stream=None):
+        """Ranks of k-column tuples in lexicographic order: (ids, first), first[id]
+        = smallest row with that tuple (``dim3_map_tuples``)."""
+        cols = [_col(c, self.device, f"col{i}") for i, c in enumerate(cols)]
+        n = cols[0].numel() if cols else 0
+        if any(c.numel() != n for c in cols):
+            raise ValueError("column lengths differ")
+        ptrs = (ctypes.c_void_p * max(len(cols), 1))(*[_ptr(c) for c in cols])
+        ids = torch.empty(n, dtype=torch.int32, device=self.device)
+        first = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        nd = ctypes.c_int64()
+        _check(self._lib.dim3_map_tuples(self._h, ptrs, len(cols), int(unsigned_mask) & 0xFFFFFFFF, n, _ptr(ids),
+                                         _ptr(first), ctypes.byref(nd), _stream(self.device, stream)))
+        return ids, first[: nd.value]
+
+    def gather(self, src, idx, stream=None):
+        """src[idx] through ``dim3_gather_i32`` (int32)."""
+        src, idx = _col(src, self.device, "src"), _col(idx, self.device, "idx")
+        out = torch.empty(idx.numel(), dtype=torch.int32, device=self.device)
+        _check(self._lib.dim3_gather_i32(self._h, _ptr(src), src.numel(), _ptr(idx), idx.numel(), _ptr(out),
+                                         _stream(self.device, stream)))
+        return out
+
     # ------------------------------------------------------------ partition
+    def partition_ids(self, r_y, r_x, s_y, s_z, n_x: int, n_y: int, n_z: int, theta_z: int = -1,
+                      stream=None) -> "Plan":
+        """Plan over pre-mapped ids (mapping skipped, ``dim3_partition_ids``)."""
+        r_y, r_x = _col(r_y, self.device, "r_y"), _col(r_x, self.device, "r_x")
+        s_y, s_z = _col(s_y, self.device, "s_y"), _col(s_z, self.device, "s_z")
+        if r_y.numel() != r_x.numel() or s_y.numel() != s_z.numel():
+            raise ValueError("column lengths differ")
+        h = ctypes.c_void_p()
+        info = PlanInfo()
+        _check(self._lib.dim3_partition_ids(self._h, _ptr(r_y), _ptr(r_x), r_y.numel(), _ptr(s_y), _ptr(s_z),
+                                            s_y.numel(), int(n_x), int(n_y), int(n_z), int(theta_z),
+                                            ctypes.byref(h), ctypes.byref(info), _stream(self.device, stream)))
+        return Plan(self, h, info, stream)
+
     def partition(self, r_key, r_val, s_key, s_val, theta_z: int = -1, stream=None) -> "Plan":
         r_key, r_val = _col(r_key, self.device, "r_key"), _col(r_val, self.device, "r_val")
         s_key, s_val = _col(s_key, self.device, "s_key"), _col(s_val, self.device, "s_val")
