@@ -12,6 +12,8 @@ shares no code with that path.
 * ``join_project_ids`` / ``join_count_ids`` / ``map_tuples`` -- Section 2.2's
   skipped mapping (Optimization 1) and multi-attribute mapping
   (``mapping.py``).
+* ``cache_stats`` / ``cache_select`` / ``cache_build`` /
+  ``join_project_cached`` -- partial result caching, Section 3 (``cache.py``).
 * ``plan`` -- the mapping and partition quantities of Algorithm 1 (semi-join
   filtered y dictionary of Section 2.2 "Optimization 2", x/z dictionaries,
   degrees m_x and m_z, |OUT_J|, the dense z set of Section 2.3) written out
@@ -29,5 +31,6 @@ from .core import (  # noqa: F401
     lib_path,
     rank_map,
 )
+from .cache import cache_build, cache_scores, cache_select, cache_stats, join_project_cached  # noqa: F401
 from .mapping import join_count_ids, join_project_ids, map_tuples  # noqa: F401
 from .plan import plan  # noqa: F401
