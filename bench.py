@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--serve-max-tuples", type=int, default=200_000)
     ap.add_argument("--premapped", action="store_true",
                     help="columns given as ids (mapping skipped, dim3_partition_ids); ids made on the host before timing")
+    ap.add_argument("--cache-budget", type=int, default=None,
+                    help="partial result cache of this many entries (Section 3), built before timing")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -290,19 +292,33 @@ def main():
         k, v = kv.split("=")
         ctx.set_option(int(k), int(v))
 
+    cache = None
+    cache_cfg = None
+    if args.cache_budget is not None:
+        assert ranges is None, "--cache-budget works on value columns"
+        t0 = time.perf_counter()
+        cache = ctx.cache_build(*cols, args.cache_budget)
+        torch.cuda.synchronize()
+        cache_cfg = dict(cache.info, budget=args.cache_budget, build_s=time.perf_counter() - t0,
+                         t_sparse=dim3.Context.T_SPARSE, t_dense=dim3.Context.T_DENSE)
+
     def join_call(c, ox, oz):
-        """The public path: one dim3_join_project, or, for pre-mapped ids,
-        dim3_partition_ids + dim3_plan_join_project + dim3_plan_destroy."""
-        if ranges is None:
+        """The public path: one dim3_join_project; for pre-mapped ids
+        dim3_partition_ids, for a cache dim3_partition_cached, each followed
+        by dim3_plan_join_project + dim3_plan_destroy."""
+        if ranges is None and cache is None:
             return ctx.join_project(*c, out_x=ox, out_z=oz)
-        pl = ctx.partition_ids(*c, *ranges)
+        pl = ctx.partition_cached(*c, cache) if cache is not None else ctx.partition_ids(*c, *ranges)
         try:
             return pl.join_project(out_x=ox, out_z=oz)
         finally:
             pl.close()
 
     # size the output once (plan path), then time the one-call path
-    plan = ctx.partition_ids(*cols, *ranges) if ranges else ctx.partition(*cols)
+    if cache is not None:
+        plan = ctx.partition_cached(*cols, cache)
+    else:
+        plan = ctx.partition_ids(*cols, *ranges) if ranges else ctx.partition(*cols)
     info = plan.info
     out_p = int(plan.row_counts().sum().item())
     plan.close()
@@ -398,6 +414,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "mapping": ("skipped: pre-mapped id columns (dim3_partition_ids); output pairs are ids"
                                    if ranges else "order-preserving hash + radix rank (dim3_join_project)"),
+                       "partial_result_cache": cache_cfg,
                        "join_tuples_per_s": info["out_j"] * args.steps * (pairs_all / total_pairs) / busy_max},
             "roofline": roofline,
             "phase_ms": phases,

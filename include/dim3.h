@@ -56,6 +56,7 @@ typedef enum {
 
 typedef struct dim3_ctx dim3_ctx;
 typedef struct dim3_plan dim3_plan;
+typedef struct dim3_cache dim3_cache;
 
 /* Sizes of a partitioned input, returned by dim3_partition (host struct). */
 typedef struct {
@@ -70,7 +71,8 @@ typedef struct {
     int64_t n_y_dense;    /* distinct y of the dense S tuples (K of the DenseEC contraction) */
     int64_t n_s_sparse;   /* S tuples in S_sparse */
     int64_t n_y_bitmap;   /* S_sparse rows held as z-bitmaps (SparseBMM's wide rows) */
-    int64_t out_j;        /* |OUT_J| = sum over y of deg_R(y) * deg_S(y) */
+    int64_t out_j;        /* |OUT_J| = sum over y of deg_R(y) * deg_S(y) (cached z excluded) */
+    int64_t n_z_cached;   /* z served from a partial result cache (Section 3), else 0 */
     int32_t theta_z;      /* degree threshold used: z dense iff m_z >= theta_z */
     int32_t dense_variant;/* DenseEC variant that will run (dim3_dense_variant) */
 } dim3_plan_info;
@@ -238,6 +240,71 @@ DIM3_API int dim3_map_tuples(dim3_ctx *ctx, const int32_t *const *d_cols, int k,
  */
 DIM3_API int dim3_gather_i32(dim3_ctx *ctx, const int32_t *d_src, int64_t n_src, const int32_t *d_idx, int64_t n,
                              int32_t *d_dst, void *stream);
+
+/*
+ * Partial result caching (Section 3). A cache holds, for a set Z_cached of z
+ * values, the x of their results (x, z): per z either the x themselves or,
+ * when they are more than half of X, the complement in X. A plan built with a
+ * cache omits the S tuples of cached z from S_sparse and S_dense and adds the
+ * cached results in the union step, so its results are those of the plain
+ * plan. The cache stays valid while the tables do not change (the caller
+ * rebuilds it otherwise, as the section prescribes).
+ */
+typedef struct {
+    int64_t n_entries;  /* cached z */
+    int64_t n_list;     /* stored x values over all entries */
+    int64_t space;      /* sum of space(z) = 2 + min(k, |X| - k) over the entries */
+    int64_t n_x;        /* |X| of the tables */
+} dim3_cache_info;
+
+/*
+ * dim3_cache_build -- score every z and cache the best within a budget.
+ *   tables        as for dim3_partition (device int32 columns).
+ *   theta_z       the threshold the queries will use (z dense iff m_z >=
+ *                 theta_z; < 0: the context's option), which decides cost(z).
+ *   budget        cache space in entries (Section 3's units: an entry costs
+ *                 2 + min(k, |X| - k), k = the z's result size).
+ *   t_sparse      cost of one join tuple in SparseBMM (seconds or any unit);
+ *   t_dense       cost of one (x, z) evaluation in DenseEC (same unit).
+ *                 cost(z) = n_join(z) * t_sparse for a sparse z, n_join(z) =
+ *                 sum over S(z) of deg_R(y); |X| * t_dense for a dense z.
+ *                 Measured on GB300: about 1.2e-12 s and 1.1e-11 s.
+ * CacheScore(z) = cost(z) / space(z) in double precision; z are taken by
+ * descending score (ties: ascending z) while the running space fits budget.
+ *   *cache_out    receives a device-resident cache; info (may be NULL) its sizes.
+ * Negative budget or cost constants: DIM3_ERR_ARG. Synchronises the stream.
+ */
+DIM3_API int dim3_cache_build(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
+                              const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns, int32_t theta_z,
+                              int64_t budget, double t_sparse, double t_dense, dim3_cache **cache_out,
+                              dim3_cache_info *info, void *stream);
+
+/*
+ * dim3_cache_export -- copy a cache's entries to device buffers sized from
+ * its info: d_z [n_entries] int32 (ascending z values), d_size [n_entries]
+ * int64 (k, or k - |X| for a complement entry), d_complement [n_entries]
+ * uint8 (1 = complement; also marks k = |X|, whose size is 0), d_offsets
+ * [n_entries + 1] int64, d_xs [n_list] int32 (entry e's x values, ascending,
+ * at d_offsets[e] .. d_offsets[e + 1]). Any pointer may be NULL to skip it.
+ */
+DIM3_API int dim3_cache_export(dim3_ctx *ctx, const dim3_cache *cache, int32_t *d_z, int64_t *d_size,
+                               uint8_t *d_complement, int64_t *d_offsets, int32_t *d_xs, void *stream);
+
+DIM3_API int dim3_cache_destroy(dim3_cache *cache);
+
+/*
+ * dim3_partition_cached -- dim3_partition with a cache built on the same
+ * tables: the dictionaries are those of the full tables, the S tuples of
+ * cached z are dropped after mapping, and the plan's Join-Project results
+ * include the cached pairs (info.n_z_cached = entries). Join-Count on such a
+ * plan gives DIM3_ERR_UNSUPPORTED (the cache holds pairs, not counts). A
+ * cache whose values do not occur in the tables, or whose |X| differs, gives
+ * DIM3_ERR_ARG. Synchronises the stream.
+ */
+DIM3_API int dim3_partition_cached(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
+                                   const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns,
+                                   const dim3_cache *cache, int32_t theta_z, dim3_plan **plan_out,
+                                   dim3_plan_info *info, void *stream);
 
 /* Copy of the plan's sizes. */
 DIM3_API int dim3_plan_get_info(const dim3_plan *plan, dim3_plan_info *info);

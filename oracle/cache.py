@@ -96,10 +96,13 @@ def cache_build(r_key, r_val, s_key, s_val, theta_z: int, budget: int, t_sparse:
     st = cache_stats(r_key, r_val, s_key, s_val, theta_z)
     sel = cache_select(st, budget, t_sparse, t_dense)
     x, z, _ = join_project(r_key, r_val, s_key, s_val)
+    by_z = np.lexsort((x, z))  # the result grouped by z, x ascending within a z
+    xg, zg = x[by_z], z[by_z]
     n_x = st.dict_x.size
     sizes, lists, comp = [], [], []
     for i in sel:
-        xs = x[z == st.dict_z[i]]  # canonical order: ascending x
+        lo, hi = np.searchsorted(zg, st.dict_z[i], "left"), np.searchsorted(zg, st.dict_z[i], "right")
+        xs = xg[lo:hi]
         if xs.size > n_x / 2:
             lists.append(np.setdiff1d(st.dict_x, xs))
             sizes.append(xs.size - n_x)

@@ -15,13 +15,16 @@ from .dim3 import (  # noqa: F401
     OPT_BITMAP_ROW_MIN,
     OPT_DENSE_VARIANT,
     OPT_EMIT_ROWS,
+    OPT_ID_CHUNK_MAX,
     OPT_LIGHT_ROW_MAX,
     OPT_THETA_Z,
     OPT_TIMING,
+    OPT_TWO_PASS,
     PHASES,
     Context,
     Dim3Error,
     Plan,
+    ResultCache,
     launch_count,
     lib_path,
     load,

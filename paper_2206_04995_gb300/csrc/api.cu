@@ -67,6 +67,10 @@ struct dim3_plan {
     std::unique_ptr<dimcube::Plan> p;
 };
 
+struct dim3_cache {
+    std::unique_ptr<dimcube::ResultCache> c;
+};
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -311,6 +315,65 @@ int dim3_gather_i32(dim3_ctx* ctx, const int32_t* d_src, int64_t n_src, const in
         DeviceGuard g(ctx->c.device);
         const bool ok = dimcube::gather_i32(d_src, n_src, d_idx, n, d_dst, as_stream(stream));
         DIM3_REQUIRE(ok, DIM3_ERR_ARG, "an index lies outside [0, n_src)");
+    });
+}
+
+int dim3_cache_build(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val, int64_t nr, const int32_t* d_s_key,
+                     const int32_t* d_s_val, int64_t ns, int32_t theta_z, int64_t budget, double t_sparse,
+                     double t_dense, dim3_cache** cache_out, dim3_cache_info* info, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && cache_out, DIM3_ERR_ARG, "null ctx or cache_out");
+        *cache_out = nullptr;
+        check_table(d_r_key, d_r_val, nr, "R");
+        check_table(d_s_key, d_s_val, ns, "S");
+        DeviceGuard g(ctx->c.device);
+        std::unique_ptr<dim3_cache> c(new dim3_cache());
+        c->c.reset(dimcube::build_result_cache(ctx->c, single_input(d_r_key, d_r_val, nr, d_s_key, d_s_val, ns),
+                                               resolve_theta(ctx, theta_z), budget, t_sparse, t_dense,
+                                               as_stream(stream)));
+        if (info) *info = dim3_cache_info{c->c->n_c, c->c->n_list, c->c->space, c->c->n_x};
+        *cache_out = c.release();
+    });
+}
+
+int dim3_cache_export(dim3_ctx* ctx, const dim3_cache* cache, int32_t* d_z, int64_t* d_size, uint8_t* d_complement,
+                      int64_t* d_offsets, int32_t* d_xs, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && cache, DIM3_ERR_ARG, "null ctx or cache");
+        DeviceGuard g(ctx->c.device);
+        const dimcube::ResultCache& c = *cache->c;
+        cudaStream_t s = as_stream(stream);
+        auto cp = [&](void* dst, const dimcube::DevBuf& src, size_t bytes) {
+            if (dst && bytes) DIM3_CUDA(cudaMemcpyAsync(dst, src.p, bytes, cudaMemcpyDeviceToDevice, s));
+        };
+        cp(d_z, c.z, (size_t)c.n_c * 4);
+        cp(d_size, c.size, (size_t)c.n_c * 8);
+        cp(d_complement, c.comp, (size_t)c.n_c);
+        cp(d_offsets, c.off, (size_t)(c.n_c + 1) * 8);
+        cp(d_xs, c.xs, (size_t)c.n_list * 4);
+        DIM3_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int dim3_cache_destroy(dim3_cache* cache) {
+    return guarded([&] { delete cache; });
+}
+
+int dim3_partition_cached(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val, int64_t nr,
+                          const int32_t* d_s_key, const int32_t* d_s_val, int64_t ns, const dim3_cache* cache,
+                          int32_t theta_z, dim3_plan** plan_out, dim3_plan_info* info, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && plan_out && cache, DIM3_ERR_ARG, "null ctx, cache or plan_out");
+        *plan_out = nullptr;
+        check_table(d_r_key, d_r_val, nr, "R");
+        check_table(d_s_key, d_s_val, ns, "S");
+        DeviceGuard g(ctx->c.device);
+        dimcube::PlanInput in = single_input(d_r_key, d_r_val, nr, d_s_key, d_s_val, ns);
+        in.cache = cache->c.get();
+        std::unique_ptr<dim3_plan> pl(new dim3_plan());
+        pl->p.reset(dimcube::build_plan(ctx->c, in, resolve_theta(ctx, theta_z), as_stream(stream)));
+        if (info) *info = pl->p->info;
+        *plan_out = pl.release();
     });
 }
 

@@ -51,7 +51,8 @@ void dense_build_operands(const Ctx& ctx, Plan& p, const uint64_t* keys64, const
     DIM3_REQUIRE(variant >= DIM3_DENSE_TC && variant <= DIM3_DENSE_PROBE, DIM3_ERR_ARG, "unknown DenseEC variant");
     p.info.dense_variant = variant;
     const int64_t n_zd = p.info.n_z_dense, K = p.info.n_y_dense;
-    p.zdw = ceil_div(n_zd, 32);
+    p.zdw_op = ceil_div(n_zd, 32);
+    p.zdw = p.zdw_op;  // widened by a partial result cache after the split
     p.kw = ceil_div(K, 32);
     p.k_pad = ceil_div(K, kTcBlockK) * kTcBlockK;
     p.n_zd_pad = ceil_div(n_zd, kTcTileN) * kTcTileN;
@@ -59,7 +60,7 @@ void dense_build_operands(const Ctx& ctx, Plan& p, const uint64_t* keys64, const
         p.b_bits.alloc((size_t)(n_zd * p.kw) * 4, s);
         DIM3_CUDA(cudaMemsetAsync(p.b_bits.p, 0, p.b_bits.bytes, s));
     } else if (variant == DIM3_DENSE_PROBE) {
-        p.sdt_bits.alloc((size_t)(K * p.zdw) * 4, s);
+        p.sdt_bits.alloc((size_t)(K * p.zdw_op) * 4, s);
         DIM3_CUDA(cudaMemsetAsync(p.sdt_bits.p, 0, p.sdt_bits.bytes, s));
     } else {
         const double bytes = (double)p.n_zd_pad * (double)p.k_pad;
@@ -71,11 +72,11 @@ void dense_build_operands(const Ctx& ctx, Plan& p, const uint64_t* keys64, const
     if (keys64)
         k_dense_operands<uint64_t><<<grid_for(n), kThreads, 0, s>>>(
             keys64, n, bz, zd_index, p.kidx_of_y.as<int32_t>(), variant, p.b_bits.as<uint32_t>(), p.kw,
-            p.sdt_bits.as<uint32_t>(), p.zdw, p.b_tc.as<uint8_t>(), p.k_pad);
+            p.sdt_bits.as<uint32_t>(), p.zdw_op, p.b_tc.as<uint8_t>(), p.k_pad);
     else
         k_dense_operands<uint32_t><<<grid_for(n), kThreads, 0, s>>>(
             keys32, n, bz, zd_index, p.kidx_of_y.as<int32_t>(), variant, p.b_bits.as<uint32_t>(), p.kw,
-            p.sdt_bits.as<uint32_t>(), p.zdw, p.b_tc.as<uint8_t>(), p.k_pad);
+            p.sdt_bits.as<uint32_t>(), p.zdw_op, p.b_tc.as<uint8_t>(), p.k_pad);
     DIM3_LAUNCHED();
 }
 
@@ -166,11 +167,13 @@ __global__ void __launch_bounds__(kThreads) k_dense_popc(const uint32_t* __restr
 }
 
 // ----------------------------------------------------------------- PROBE
-// One CTA per x; each thread owns words of the result row.
+// One CTA per x; each thread owns words of the result row. sdw = words of an
+// S_dense row (the dense z index), zdw = words of a result row (sdw, or more
+// when a partial result cache adds its columns after the dense index).
 template <bool kCount>
 __global__ void __launch_bounds__(128) k_dense_probe(const int64_t* r_rowptr, const int32_t* r_col, const int32_t* kidx,
                                                      int64_t x_begin, int64_t rows, const uint32_t* __restrict__ sdt,
-                                                     int64_t zdw, int64_t n_zd, uint32_t* D, int32_t* C,
+                                                     int64_t sdw, int64_t zdw, int64_t n_zd, uint32_t* D, int32_t* C,
                                                      const int32_t* x_tag, const int64_t* zd_lo) {
     const int64_t xr = blockIdx.x;
     if (xr >= rows) return;
@@ -178,13 +181,13 @@ __global__ void __launch_bounds__(128) k_dense_probe(const int64_t* r_rowptr, co
     const int64_t q0 = r_rowptr[x], q1 = r_rowptr[x + 1];
     // words of the dense indices of x's instance (batches; all words otherwise)
     const int tg = x_tag ? x_tag[x] : 0;
-    const int64_t w0 = x_tag ? (zd_lo[tg] >> 5) : 0, w1 = x_tag ? ((zd_lo[tg + 1] + 31) >> 5) : zdw;
+    const int64_t w0 = x_tag ? (zd_lo[tg] >> 5) : 0, w1 = x_tag ? ((zd_lo[tg + 1] + 31) >> 5) : sdw;
     for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
         if (!kCount) {
             uint32_t acc = 0u;
             for (int64_t q = q0; q < q1; ++q) {
                 const int32_t k = kidx[r_col[q]];
-                if (k >= 0) acc |= sdt[(int64_t)k * zdw + w];
+                if (k >= 0) acc |= sdt[(int64_t)k * sdw + w];
             }
             D[xr * zdw + w] = acc;
         } else {
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(128) k_dense_probe(const int64_t* r_rowptr, co
             for (int64_t q = q0; q < q1; ++q) {
                 const int32_t k = kidx[r_col[q]];
                 if (k < 0) continue;
-                const uint32_t bits = sdt[(int64_t)k * zdw + w];
+                const uint32_t bits = sdt[(int64_t)k * sdw + w];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) c[j] += (bits >> j) & 1u;
             }
@@ -232,12 +235,31 @@ static int64_t upload_block_tiles(const Plan& p, int64_t x_begin, int64_t rows, 
     return (int64_t)tiles.size();
 }
 
+static void dense_product(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int kind, uint32_t* d_bits,
+                          int32_t* d_cnt, cudaStream_t s);
+
 void dense_ec(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int kind, uint32_t* d_bits, int32_t* d_cnt,
               cudaStream_t s) {
     const int64_t n_zd = p.info.n_z_dense;
-    if (rows <= 0 || n_zd <= 0) return;
+    const bool cached = kind == 0 && p.n_zc > 0;
+    if (rows <= 0 || (n_zd <= 0 && !cached)) return;
     const int variant = p.info.dense_variant;
     PhaseScope phase(ctx.stats, PH_DENSE, s);
+    if (cached) {
+        // the cache's columns are filled after the dense product; everything
+        // the product does not write must be zero
+        DIM3_CUDA(cudaMemsetAsync(d_bits, 0, (size_t)(rows * p.zdw) * 4, s));
+        if (n_zd > 0) dense_product(ctx, p, x_begin, rows, kind, d_bits, d_cnt, s);
+        cache_expand(p, x_begin, rows, d_bits, s);
+        return;
+    }
+    dense_product(ctx, p, x_begin, rows, kind, d_bits, d_cnt, s);
+}
+
+static void dense_product(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int kind, uint32_t* d_bits,
+                          int32_t* d_cnt, cudaStream_t s) {
+    const int64_t n_zd = p.info.n_z_dense;
+    const int variant = p.info.dense_variant;
     const bool batch = p.n_inst > 1;
     if (batch) {
         // only the block diagonal is computed: everything else is zero
@@ -250,12 +272,14 @@ void dense_ec(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_t rows, int 
         if (kind == 0)
             k_dense_probe<false><<<(unsigned)rows, 128, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(),
                                                                p.kidx_of_y.as<int32_t>(), x_begin, rows,
-                                                               p.sdt_bits.as<uint32_t>(), p.zdw, n_zd, d_bits, nullptr,
+                                                               p.sdt_bits.as<uint32_t>(), p.zdw_op, p.zdw, n_zd, d_bits,
+                                                               nullptr,
                                                                xt, p.inst_zd_lo.as<int64_t>());
         else
             k_dense_probe<true><<<(unsigned)rows, 128, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(),
                                                               p.kidx_of_y.as<int32_t>(), x_begin, rows,
-                                                              p.sdt_bits.as<uint32_t>(), p.zdw, n_zd, nullptr, d_cnt,
+                                                              p.sdt_bits.as<uint32_t>(), p.zdw_op, p.zdw, n_zd, nullptr,
+                                                              d_cnt,
                                                               xt, p.inst_zd_lo.as<int64_t>());
         DIM3_LAUNCHED();
     } else if (variant == DIM3_DENSE_POPC && batch) {

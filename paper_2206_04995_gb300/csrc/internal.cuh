@@ -28,6 +28,22 @@ void build_value_map(const int32_t* vals, const int32_t* tags, int n_tags, const
 void probe_value_map(const ValueMap& vm, const int32_t* vals, const int32_t* tags, int64_t n, int32_t* ids_out,
                      cudaStream_t s);
 
+// Partial result cache (Section 3): entries for the cached z values
+// (ascending), each holding the x of that z's results, or, when they are more
+// than half of X, the complement in X. Values, not ids, so that a plan built
+// later on the same tables can attach it. Device resident.
+struct ResultCache {
+    int64_t n_x = 0;     // |X| of the tables it was built on
+    int64_t n_c = 0;     // entries
+    int64_t n_list = 0;  // stored x values over all entries
+    int64_t space = 0;   // sum of 2 + min(k, |X| - k) over the entries
+    DevBuf z;            // int32 [n_c]: cached z values, ascending
+    DevBuf size;         // int64 [n_c]: k, or k - |X| for a complement entry
+    DevBuf comp;         // uint8 [n_c]: 1 = complement entry
+    DevBuf off;          // int64 [n_c + 1]: entry e's x values are xs[off[e], off[e + 1])
+    DevBuf xs;           // int32 [n_list]: x values, ascending within an entry
+};
+
 // Input of the plan builder: one instance (tags null, n_inst 1) or a batch of
 // n_inst instances concatenated, row i of R belonging to instance r_tag[i].
 struct PlanInput {
@@ -41,6 +57,9 @@ struct PlanInput {
     // and the mapping step is skipped
     bool premapped = false;
     int64_t n_x = 0, n_y = 0, n_z = 0;
+    // Section 3: omit the cache's z from S_sparse and S_dense and add the
+    // cached results in the union step (single instance, mapped columns)
+    const ResultCache* cache = nullptr;
 };
 
 // -------------------------------------------------------------------- plan
@@ -92,8 +111,20 @@ struct Plan {
     DevBuf kidx_of_y;   // int32 [n_y]: y id -> K index or -1
     DevBuf b_tc;        // uint8 [n_zd_pad][k_pad]: e4m3 0/1, K-major (tensor-core operand)
     DevBuf b_bits;      // uint32 [n_zd][kw]: Bitmap_z over K (AND+popc operand)
-    DevBuf sdt_bits;    // uint32 [n_yd][zdw]: S_dense rows by y over dense index (probe operand)
-    int64_t k_pad = 0, kw = 0, zdw = 0, n_zd_pad = 0;
+    DevBuf sdt_bits;    // uint32 [n_yd][zdw_op]: S_dense rows by y over dense index (probe operand)
+    int64_t k_pad = 0, kw = 0, n_zd_pad = 0;
+    int64_t zdw_op = 0;  // words of the dense z index in the operands
+    // Dense-result rows [rows][zdw]: the dense z index [0, n_z_dense) and, for
+    // a plan with a partial result cache, the cached z at [zc_off, zc_off +
+    // n_zc) (zc_off = n_zd_pad, a whole number of words); zd_list maps every
+    // index to its z id. n_zd_total = zc_off + n_zc (= n_z_dense uncached).
+    int64_t zdw = 0, n_zd_total = 0;
+    int64_t n_zc = 0, zc_off = 0, zc_nlist = 0;
+    DevBuf zc_zid;      // int32 [n_zc]: z id of every cache entry
+    DevBuf zc_cmask;    // uint32 [ceil(n_zc / 32)]: complement entries' bits
+    DevBuf zc_comp;     // uint8 [n_zc]
+    DevBuf zc_xid;      // int32 [zc_nlist]: x ids of the entries' lists
+    DevBuf zc_ent;      // int32 [zc_nlist]: entry of each list element
     // cached row offsets of the last counting pass
     int64_t cache_begin = -1, cache_end = -1;
     int cache_kind = -1;
@@ -165,6 +196,15 @@ int64_t map_tuples(const int32_t* const* cols, int k, uint32_t unsigned_mask, in
                    cudaStream_t s);
 // dst[i] = src[idx[i]]; false (dst[i] = -1 there) when an index is outside [0, n_src).
 bool gather_i32(const int32_t* src, int64_t n_src, const int32_t* idx, int64_t n, int32_t* dst, cudaStream_t s);
+
+// Partial result caching (cache.cu): statistics of the tables, CacheScore
+// selection under a budget (space units), entries; attach to a plan being
+// built; expand into dense-result rows [rows][zdw].
+ResultCache* build_result_cache(const Ctx& ctx, const PlanInput& in, int64_t theta_z, int64_t budget,
+                                double t_sparse, double t_dense, cudaStream_t s);
+void attach_cache_ids(Plan& p, const ResultCache& c, int32_t* sz_id, int64_t ns, cudaStream_t s);
+void finish_cache_index(Plan& p, cudaStream_t s);
+void cache_expand(const Plan& p, int64_t x_begin, int64_t rows, uint32_t* d_bits, cudaStream_t s);
 
 // Value mapping with all scratch in a fixed device array (noalloc.cu).
 void map_noalloc(const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,

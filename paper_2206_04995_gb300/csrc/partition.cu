@@ -298,6 +298,7 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
         DIM3_LAUNCHED();
     }
     p.info.n_z_dense = n_zd;
+    p.n_zd_total = n_zd;
     // dense index range of every instance
     p.inst_zd_lo.alloc((size_t)(p.n_inst + 1) * 8, s);
     p.h_inst_zd_lo.assign(p.n_inst + 1, 0);
@@ -499,6 +500,8 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
 
     DevBuf sy_id, sz_id, ry_id, rx_id, y_tag, z_tag;
     const int32_t *rx = nullptr, *ry = nullptr, *sy = nullptr, *sz = nullptr;
+    DIM3_REQUIRE(!in.cache || (!in.premapped && !batch), DIM3_ERR_ARG,
+                 "a partial result cache attaches to a single instance of mapped columns");
     if (in.premapped) {
         premapped_ids(*p, in, s);
         rx = in.r_val;
@@ -538,6 +541,9 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
                             p->dict_z.as<int32_t>(), z_tag.as<int32_t>(), s);
             p->info.n_z = zmap.n_distinct;
         }
+        // Section 3: the S tuples of cached z leave after mapping, so the
+        // dictionaries (and X) stay those of the full tables
+        if (in.cache) attach_cache_ids(*p, *in.cache, sz_id.as<int32_t>(), ns, s);
         rx = rx_id.as<int32_t>();
         ry = ry_id.as<int32_t>();
         sy = sy_id.as<int32_t>();
@@ -554,6 +560,7 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
         build_s_side<uint32_t>(ctx, *p, sy, sz, ns, by, bz, theta_z, y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
     else
         build_s_side<uint64_t>(ctx, *p, sy, sz, ns, by, bz, theta_z, y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
+    if (in.cache) finish_cache_index(*p, s);
     if (batch) p->y_tag = std::move(y_tag);
     DIM3_CUDA(cudaStreamSynchronize(s));
     return p.release();

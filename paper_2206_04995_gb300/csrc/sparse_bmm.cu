@@ -356,15 +356,14 @@ __global__ void __launch_bounds__(kThreads, kEmit ? 4 : 8) k_xrow_bits(const XRo
             }
         }
         // DenseEC result of this x (disjoint from the sparse z set), over the
-        // dense indices of x's instance
+        // dense indices of x's instance: one thread per index, so the result
+        // word is a broadcast read and the z ids of set bits coalesced reads
         if (a.n_zd > 0) {
             const uint32_t* drow = a.d_bits + xr * a.zdw;
-            for (int64_t w = (a.zd_lo[tg] >> 5) + tid; w < ((a.zd_lo[tg + 1] + 31) >> 5); w += kThreads) {
-                uint32_t word = drow[w];
-                while (word) {
-                    const int b = __ffs(word) - 1;
-                    word &= word - 1;
-                    int32_t z = a.zd_list[w * 32 + b];
+            const int64_t d1 = a.zd_lo[tg + 1];
+            for (int64_t d = a.zd_lo[tg] + tid; d < d1; d += kThreads) {
+                if ((drow[d >> 5] >> (d & 31)) & 1u) {
+                    int32_t z = a.zd_list[d];
                     if (z >= zt0 && z < zt1) {
                         z -= (int32_t)zt0;
                         atomicOr(&bm[z >> 5], 1u << (z & 31));
@@ -713,15 +712,13 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
             }
         }
         if (a.n_zd > 0) {
+            // DenseEC results, one thread per dense index (see k_xrow_bits)
             for (int k = 0; k < ng; ++k) {
                 const uint32_t* drow = a.d_bits + (xr0 + k) * a.zdw;
                 uint32_t* bm = bm_all + k * tile_words;
-                for (int64_t w = tid; w < a.zdw; w += kThreads) {
-                    uint32_t word = drow[w];
-                    while (word) {
-                        const int b = __ffs(word) - 1;
-                        word &= word - 1;
-                        int32_t z = a.zd_list[w * 32 + b];
+                for (int64_t d = tid; d < a.n_zd; d += kThreads) {
+                    if ((drow[d >> 5] >> (d & 31)) & 1u) {
+                        int32_t z = a.zd_list[d];
                         if (z >= zt0 && z < zt1) {
                             z -= (int32_t)zt0;
                             atomicOr(&bm[z >> 5], 1u << (z & 31));
@@ -1007,7 +1004,7 @@ static XRowArgs make_args(const Plan& p, int64_t x_begin, int64_t rows, int kind
     a.z_lo = p.inst_z_lo.as<int64_t>();
     a.zd_lo = p.inst_zd_lo.as<int64_t>();
     a.zdw = p.zdw;
-    a.n_zd = p.info.n_z_dense;
+    a.n_zd = p.n_zd_total;  // dense z index plus a partial result cache's columns
     a.zd_list = p.zd_list.as<int32_t>();
     a.dict_x = p.dict_x.as<int32_t>();
     a.dict_z = p.dict_z.as<int32_t>();
@@ -1114,7 +1111,9 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
     const int64_t rows = x_end - x_begin;
     p.cache_dbits.release();
     p.cache_dcnt.release();
-    if (p.info.n_z_dense > 0 && rows > 0) {
+    DIM3_REQUIRE(kind == 0 || p.n_zc == 0, DIM3_ERR_UNSUPPORTED,
+                 "Join-Count on a plan with a partial result cache (the cache holds pairs, not counts)");
+    if (p.n_zd_total > 0 && rows > 0) {
         if (kind == 0) {
             p.cache_dbits.alloc((size_t)(rows * p.zdw) * 4, s);
             dense_ec(ctx, p, x_begin, rows, 0, p.cache_dbits.as<uint32_t>(), nullptr, s);
@@ -1178,7 +1177,7 @@ static int64_t plan_join_single_pass(const Ctx& ctx, Plan& p, int64_t x_begin, i
                                      int32_t* out_z, int64_t capacity, int64_t* count, cudaStream_t s) {
     const int64_t rows = x_end - x_begin;
     DevBuf dbits;
-    if (p.info.n_z_dense > 0) {
+    if (p.n_zd_total > 0) {
         dbits.alloc((size_t)(rows * p.zdw) * 4, s);
         dense_ec(ctx, p, x_begin, rows, 0, dbits.as<uint32_t>(), nullptr, s);
     }

@@ -48,10 +48,15 @@ class Dim3Error(RuntimeError):
 class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_r", "n_s", "n_r_kept", "n_s_distinct", "n_x", "n_y", "n_z", "n_z_dense", "n_y_dense",
-        "n_s_sparse", "n_y_bitmap", "out_j")] + [("theta_z", ctypes.c_int32), ("dense_variant", ctypes.c_int32)]
+        "n_s_sparse", "n_y_bitmap", "out_j", "n_z_cached")] + [("theta_z", ctypes.c_int32),
+                                                               ("dense_variant", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class CacheInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("n_entries", "n_list", "space", "n_x")]
 
 
 class Instance(ctypes.Structure):
@@ -99,6 +104,12 @@ def load(build_if_missing: bool = True):
                                     ctypes.POINTER(PlanInfo), P], INT),
             "dim3_map_tuples": ([P, P, ctypes.c_int, ctypes.c_uint32, I64, P, P, ctypes.POINTER(I64), P], INT),
             "dim3_gather_i32": ([P, P, I64, P, I64, P, P], INT),
+            "dim3_cache_build": ([P, P, P, I64, P, P, I64, I32, I64, ctypes.c_double, ctypes.c_double,
+                                  ctypes.POINTER(P), ctypes.POINTER(CacheInfo), P], INT),
+            "dim3_cache_export": ([P, P, P, P, P, P, P, P], INT),
+            "dim3_cache_destroy": ([P], INT),
+            "dim3_partition_cached": ([P, P, P, I64, P, P, I64, P, I32, ctypes.POINTER(P), ctypes.POINTER(PlanInfo),
+                                       P], INT),
             "dim3_plan_get_info": ([P, ctypes.POINTER(PlanInfo)], INT),
             "dim3_plan_row_counts": ([P, P, I64, I64, P, P], INT),
             "dim3_plan_join_project": ([P, P, I64, I64, P, P, I64, ctypes.POINTER(I64), P], INT),
@@ -235,6 +246,41 @@ class Context:
                                             ctypes.byref(h), ctypes.byref(info), _stream(self.device, stream)))
         return Plan(self, h, info, stream)
 
+    # Section 3 cost constants measured on GB300 (seconds): one SparseBMM join
+    # tuple, one DenseEC (x, z) evaluation
+    T_SPARSE = 1.2e-12
+    T_DENSE = 1.1e-11
+
+    def cache_build(self, r_key, r_val, s_key, s_val, budget: int, theta_z: int = -1, t_sparse: float = T_SPARSE,
+                    t_dense: float = T_DENSE, stream=None) -> "ResultCache":
+        """Partial result cache of the tables within ``budget`` entries
+        (``dim3_cache_build``)."""
+        r_key, r_val = _col(r_key, self.device, "r_key"), _col(r_val, self.device, "r_val")
+        s_key, s_val = _col(s_key, self.device, "s_key"), _col(s_val, self.device, "s_val")
+        if r_key.numel() != r_val.numel() or s_key.numel() != s_val.numel():
+            raise ValueError("column lengths differ")
+        h = ctypes.c_void_p()
+        info = CacheInfo()
+        _check(self._lib.dim3_cache_build(self._h, _ptr(r_key), _ptr(r_val), r_key.numel(), _ptr(s_key),
+                                          _ptr(s_val), s_key.numel(), int(theta_z), int(budget), float(t_sparse),
+                                          float(t_dense), ctypes.byref(h), ctypes.byref(info),
+                                          _stream(self.device, stream)))
+        return ResultCache(self, h, info)
+
+    def partition_cached(self, r_key, r_val, s_key, s_val, cache: "ResultCache", theta_z: int = -1,
+                         stream=None) -> "Plan":
+        """Plan whose results include ``cache``'s pairs (``dim3_partition_cached``)."""
+        r_key, r_val = _col(r_key, self.device, "r_key"), _col(r_val, self.device, "r_val")
+        s_key, s_val = _col(s_key, self.device, "s_key"), _col(s_val, self.device, "s_val")
+        if r_key.numel() != r_val.numel() or s_key.numel() != s_val.numel():
+            raise ValueError("column lengths differ")
+        h = ctypes.c_void_p()
+        info = PlanInfo()
+        _check(self._lib.dim3_partition_cached(self._h, _ptr(r_key), _ptr(r_val), r_key.numel(), _ptr(s_key),
+                                               _ptr(s_val), s_key.numel(), cache._h, int(theta_z), ctypes.byref(h),
+                                               ctypes.byref(info), _stream(self.device, stream)))
+        return Plan(self, h, info, stream)
+
     def partition(self, r_key, r_val, s_key, s_val, theta_z: int = -1, stream=None) -> "Plan":
         r_key, r_val = _col(r_key, self.device, "r_key"), _col(r_val, self.device, "r_val")
         s_key, s_val = _col(s_key, self.device, "s_key"), _col(s_val, self.device, "s_val")
@@ -352,6 +398,43 @@ class Context:
         if counts:
             return out_x[:n], out_z[:n], out_c[:n]
         return out_x[:n], out_z[:n]
+
+
+class ResultCache:
+    """A device-resident partial result cache (Section 3)."""
+
+    def __init__(self, ctx: Context, handle, info: CacheInfo):
+        self.ctx = ctx
+        self._h = handle
+        self._info = info
+
+    @property
+    def info(self) -> dict:
+        return {n: getattr(self._info, n) for n, _ in self._info._fields_}
+
+    def export(self, stream=None) -> dict:
+        """Entries as device tensors: z, size, complement, offsets, xs."""
+        n, nl, dev = self._info.n_entries, self._info.n_list, self.ctx.device
+        out = {"z": torch.empty(n, dtype=torch.int32, device=dev),
+               "size": torch.empty(n, dtype=torch.int64, device=dev),
+               "complement": torch.empty(n, dtype=torch.uint8, device=dev),
+               "offsets": torch.empty(n + 1, dtype=torch.int64, device=dev),
+               "xs": torch.empty(nl, dtype=torch.int32, device=dev)}
+        _check(self.ctx._lib.dim3_cache_export(self.ctx._h, self._h, *[_ptr(out[k]) for k in
+                                                                     ("z", "size", "complement", "offsets", "xs")],
+                                               _stream(dev, stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.ctx._lib.dim3_cache_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
 
 
 class Plan:
