@@ -14,6 +14,8 @@ shares no code with that path.
   (``mapping.py``).
 * ``cache_stats`` / ``cache_select`` / ``cache_build`` /
   ``join_project_cached`` -- partial result caching, Section 3 (``cache.py``).
+* ``join_aggregate`` / ``groupby_aggregate`` -- Join-Aggregate, Section 4.1,
+  from the materialised join (``aggregate.py``).
 * ``plan`` -- the mapping and partition quantities of Algorithm 1 (semi-join
   filtered y dictionary of Section 2.2 "Optimization 2", x/z dictionaries,
   degrees m_x and m_z, |OUT_J|, the dense z set of Section 2.3) written out
@@ -31,6 +33,7 @@ from .core import (  # noqa: F401
     lib_path,
     rank_map,
 )
+from .aggregate import groupby_aggregate, join_aggregate  # noqa: F401
 from .cache import cache_build, cache_scores, cache_select, cache_stats, join_project_cached  # noqa: F401
 from .mapping import join_count_ids, join_project_ids, map_tuples  # noqa: F401
 from .plan import plan  # noqa: F401
