@@ -94,6 +94,21 @@ typedef enum {
     DIM3_DENSE_PROBE = 3   /* per x, probe each y of R[x] in S_dense (non-SIMD method) */
 } dim3_dense_variant;
 
+/* Join-Aggregate (Section 4.1): the aggregate and the function f(R.v, S.u). */
+typedef enum {
+    DIM3_AGG_COUNT = 0,  /* join tuples of the group (int64) */
+    DIM3_AGG_SUM = 1,    /* sum of f (int64, wrapping modulo 2^64) */
+    DIM3_AGG_MIN = 2,    /* int64 */
+    DIM3_AGG_MAX = 3,    /* int64 */
+    DIM3_AGG_AVG = 4     /* (double)SUM / (double)COUNT */
+} dim3_agg;
+typedef enum {
+    DIM3_FN_MUL = 0,     /* v * u (int64) */
+    DIM3_FN_ADD = 1,     /* v + u */
+    DIM3_FN_LEFT = 2,    /* v */
+    DIM3_FN_RIGHT = 3    /* u */
+} dim3_agg_fn;
+
 /* Context options (dim3_ctx_set_option). */
 typedef enum {
     DIM3_OPT_THETA_Z = 1,       /* z dense iff m_z >= value; <0: tuned (default) */
@@ -305,6 +320,41 @@ DIM3_API int dim3_partition_cached(dim3_ctx *ctx, const int32_t *d_r_key, const 
                                    const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns,
                                    const dim3_cache *cache, int32_t theta_z, dim3_plan **plan_out,
                                    dim3_plan_info *info, void *stream);
+
+/*
+ * dim3_join_aggregate -- Join-Aggregate with group-by attributes from both
+ * tables (Section 4.1): G_{x,z} agg(f(R.v, S.u)) over R(x, y, v) join_y
+ * S(z, y, u). R and S are bags of rows (every pair of rows with equal y is a
+ * join tuple, duplicates included, as in SQL).
+ *   d_r_key, d_r_val, d_r_v [nr] int32 device: R's y, x and v columns.
+ *   d_s_key, d_s_val, d_s_u [ns] int32 device: S's y, z and u columns.
+ *   agg, fn    a dim3_agg and a dim3_agg_fn (fn is ignored for COUNT).
+ *   d_out_x, d_out_z [capacity] int32 device, out: the groups (x, z) with at
+ *              least one join tuple, canonical order (the Join-Project pairs).
+ *   d_out_val  [capacity] device, out: int64 per group, or double for AVG.
+ *   count      host, out: number of groups; always set.
+ * capacity < count: DIM3_ERR_CAPACITY, nothing written (capacity 0 sizes).
+ * Unknown agg or fn: DIM3_ERR_ARG. Synchronises the stream.
+ */
+DIM3_API int dim3_join_aggregate(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, const int32_t *d_r_v,
+                                 int64_t nr, const int32_t *d_s_key, const int32_t *d_s_val, const int32_t *d_s_u,
+                                 int64_t ns, int agg, int fn, int32_t *d_out_x, int32_t *d_out_z, void *d_out_val,
+                                 int64_t capacity, int64_t *count, void *stream);
+
+/*
+ * dim3_groupby_aggregate -- Join-Aggregate with the group-by attribute from
+ * one table (Section 4.1): G_x agg(z) over R(x, y) join_y S(z, y), computed by
+ * the section's rewrite: per-y aggregates of S first (count, sum, min, max of
+ * its z values), then one fold per x over R's rows. Bags as above (COUNT
+ * counts join tuples). To group by z instead, swap the tables.
+ *   d_out_x    [capacity] int32 device, out: every x with a join tuple, ascending.
+ *   d_out_val  [capacity] device, out: int64, or double for AVG.
+ *   count      host, out. Capacity protocol and errors as dim3_join_aggregate.
+ */
+DIM3_API int dim3_groupby_aggregate(dim3_ctx *ctx, const int32_t *d_r_key, const int32_t *d_r_val, int64_t nr,
+                                    const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns, int agg,
+                                    int32_t *d_out_x, void *d_out_val, int64_t capacity, int64_t *count,
+                                    void *stream);
 
 /* Copy of the plan's sizes. */
 DIM3_API int dim3_plan_get_info(const dim3_plan *plan, dim3_plan_info *info);

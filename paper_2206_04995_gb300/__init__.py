@@ -8,10 +8,19 @@ loop and the autotuner built on that ABI.
 """
 
 from .dim3 import (  # noqa: F401
+    AGG_AVG,
+    AGG_COUNT,
+    AGG_MAX,
+    AGG_MIN,
+    AGG_SUM,
     DENSE_AUTO,
     DENSE_POPC,
     DENSE_PROBE,
     DENSE_TC,
+    FN_ADD,
+    FN_LEFT,
+    FN_MUL,
+    FN_RIGHT,
     OPT_BITMAP_ROW_MIN,
     OPT_DENSE_VARIANT,
     OPT_EMIT_ROWS,

@@ -377,6 +377,39 @@ int dim3_partition_cached(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* 
     });
 }
 
+int dim3_join_aggregate(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val, const int32_t* d_r_v,
+                        int64_t nr, const int32_t* d_s_key, const int32_t* d_s_val, const int32_t* d_s_u, int64_t ns,
+                        int agg, int fn, int32_t* d_out_x, int32_t* d_out_z, void* d_out_val, int64_t capacity,
+                        int64_t* count, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && count, DIM3_ERR_ARG, "null ctx or count");
+        *count = 0;
+        check_table(d_r_key, d_r_val, nr, "R");
+        check_table(d_s_key, d_s_val, ns, "S");
+        DIM3_REQUIRE(nr == 0 || d_r_v, DIM3_ERR_ARG, "R: null value column");
+        DIM3_REQUIRE(ns == 0 || d_s_u, DIM3_ERR_ARG, "S: null value column");
+        DIM3_REQUIRE(capacity >= 0, DIM3_ERR_ARG, "negative capacity");
+        DeviceGuard g(ctx->c.device);
+        dimcube::join_aggregate(ctx->c, single_input(d_r_key, d_r_val, nr, d_s_key, d_s_val, ns), d_r_v, d_s_u, agg,
+                                fn, d_out_x, d_out_z, d_out_val, capacity, count, as_stream(stream));
+    });
+}
+
+int dim3_groupby_aggregate(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r_val, int64_t nr,
+                           const int32_t* d_s_key, const int32_t* d_s_val, int64_t ns, int agg, int32_t* d_out_x,
+                           void* d_out_val, int64_t capacity, int64_t* count, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && count, DIM3_ERR_ARG, "null ctx or count");
+        *count = 0;
+        check_table(d_r_key, d_r_val, nr, "R");
+        check_table(d_s_key, d_s_val, ns, "S");
+        DIM3_REQUIRE(capacity >= 0, DIM3_ERR_ARG, "negative capacity");
+        DeviceGuard g(ctx->c.device);
+        dimcube::groupby_aggregate(ctx->c, single_input(d_r_key, d_r_val, nr, d_s_key, d_s_val, ns), agg, d_out_x,
+                                   d_out_val, capacity, count, as_stream(stream));
+    });
+}
+
 int dim3_plan_get_info(const dim3_plan* plan, dim3_plan_info* info) {
     return guarded([&] {
         DIM3_REQUIRE(plan && info, DIM3_ERR_ARG, "null plan or info");

@@ -206,6 +206,16 @@ void attach_cache_ids(Plan& p, const ResultCache& c, int32_t* sz_id, int64_t ns,
 void finish_cache_index(Plan& p, cudaStream_t s);
 void cache_expand(const Plan& p, int64_t x_begin, int64_t rows, uint32_t* d_bits, cudaStream_t s);
 
+// Join-Aggregate (aggregate.cu), Section 4.1: G_{x,z} agg(f(R.v, S.u)) and
+// the one-table G_x agg(z). out_val is int64 (COUNT, SUM, MIN, MAX) or
+// double (AVG). *count = the number of groups (also returned); a smaller
+// capacity throws DIM3_ERR_CAPACITY with nothing written.
+int64_t join_aggregate(const Ctx& ctx, const PlanInput& in, const int32_t* r_v, const int32_t* s_u, int agg, int fn,
+                       int32_t* out_x, int32_t* out_z, void* out_val, int64_t capacity, int64_t* count,
+                       cudaStream_t s);
+int64_t groupby_aggregate(const Ctx& ctx, const PlanInput& in, int agg, int32_t* out_x, void* out_val,
+                          int64_t capacity, int64_t* count, cudaStream_t s);
+
 // Value mapping with all scratch in a fixed device array (noalloc.cu).
 void map_noalloc(const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,
                  cudaStream_t s);

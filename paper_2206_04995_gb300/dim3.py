@@ -27,6 +27,8 @@ DIM3_ERR_UNSUPPORTED = -7
 DENSE_AUTO, DENSE_TC, DENSE_POPC, DENSE_PROBE = 0, 1, 2, 3
 OPT_THETA_Z, OPT_DENSE_VARIANT, OPT_BITMAP_ROW_MIN, OPT_LIGHT_ROW_MAX, OPT_TIMING = 1, 2, 3, 4, 5
 OPT_EMIT_ROWS = 6
+AGG_COUNT, AGG_SUM, AGG_MIN, AGG_MAX, AGG_AVG = 0, 1, 2, 3, 4
+FN_MUL, FN_ADD, FN_LEFT, FN_RIGHT = 0, 1, 2, 3
 OPT_TWO_PASS = 7
 OPT_ID_CHUNK_MAX = 8
 PHASES = {"map": 0, "partition": 1, "dense_ec": 2, "sparse_count": 3, "sparse_emit": 4, "dense_tc": 5}
@@ -104,6 +106,10 @@ def load(build_if_missing: bool = True):
                                     ctypes.POINTER(PlanInfo), P], INT),
             "dim3_map_tuples": ([P, P, ctypes.c_int, ctypes.c_uint32, I64, P, P, ctypes.POINTER(I64), P], INT),
             "dim3_gather_i32": ([P, P, I64, P, I64, P, P], INT),
+            "dim3_join_aggregate": ([P, P, P, P, I64, P, P, P, I64, ctypes.c_int, ctypes.c_int, P, P, P, I64,
+                                     ctypes.POINTER(I64), P], INT),
+            "dim3_groupby_aggregate": ([P, P, P, I64, P, P, I64, ctypes.c_int, P, P, I64, ctypes.POINTER(I64), P],
+                                       INT),
             "dim3_cache_build": ([P, P, P, I64, P, P, I64, I32, I64, ctypes.c_double, ctypes.c_double,
                                   ctypes.POINTER(P), ctypes.POINTER(CacheInfo), P], INT),
             "dim3_cache_export": ([P, P, P, P, P, P, P, P], INT),
@@ -245,6 +251,57 @@ class Context:
                                             s_y.numel(), int(n_x), int(n_y), int(n_z), int(theta_z),
                                             ctypes.byref(h), ctypes.byref(info), _stream(self.device, stream)))
         return Plan(self, h, info, stream)
+
+    # ------------------------------------------------------- Join-Aggregate
+    def join_aggregate(self, r_key, r_val, r_v, s_key, s_val, s_u, agg: int, fn: int = FN_MUL, out=None,
+                       stream=None):
+        """G_{x,z} agg(f(R.v, S.u)) (``dim3_join_aggregate``): (x, z, value),
+        value int64, or float64 for AVG. ``out`` = preallocated (x, z, value)
+        makes it one C call; otherwise a sizing call comes first."""
+        cols = [_col(t, self.device, n) for t, n in ((r_key, "r_key"), (r_val, "r_val"), (r_v, "r_v"),
+                                                      (s_key, "s_key"), (s_val, "s_val"), (s_u, "s_u"))]
+        if not (cols[0].numel() == cols[1].numel() == cols[2].numel()) or not (
+                cols[3].numel() == cols[4].numel() == cols[5].numel()):
+            raise ValueError("column lengths differ")
+        st = _stream(self.device, stream)
+        n = ctypes.c_int64()
+        args = [self._h, _ptr(cols[0]), _ptr(cols[1]), _ptr(cols[2]), cols[0].numel(), _ptr(cols[3]), _ptr(cols[4]),
+                _ptr(cols[5]), cols[3].numel(), int(agg), int(fn)]
+        if out is not None:
+            ox, oz, ov = out
+            _check(self._lib.dim3_join_aggregate(*args, _ptr(ox), _ptr(oz), _ptr(ov), ox.numel(), ctypes.byref(n),
+                                                 st))
+            return ox[: n.value], oz[: n.value], ov[: n.value]
+        rc = self._lib.dim3_join_aggregate(*args, None, None, None, 0, ctypes.byref(n), st)
+        if rc not in (DIM3_OK, DIM3_ERR_CAPACITY):
+            _check(rc)
+        m = n.value
+        x = torch.empty(m, dtype=torch.int32, device=self.device)
+        z = torch.empty(m, dtype=torch.int32, device=self.device)
+        v = torch.empty(m, dtype=torch.float64 if agg == AGG_AVG else torch.int64, device=self.device)
+        if m:
+            _check(self._lib.dim3_join_aggregate(*args, _ptr(x), _ptr(z), _ptr(v), m, ctypes.byref(n), st))
+        return x, z, v
+
+    def groupby_aggregate(self, r_key, r_val, s_key, s_val, agg: int, stream=None):
+        """G_x agg(z) over R(x, y) join S(z, y) (``dim3_groupby_aggregate``): (x, value)."""
+        cols = [_col(t, self.device, n) for t, n in ((r_key, "r_key"), (r_val, "r_val"), (s_key, "s_key"),
+                                                      (s_val, "s_val"))]
+        if cols[0].numel() != cols[1].numel() or cols[2].numel() != cols[3].numel():
+            raise ValueError("column lengths differ")
+        st = _stream(self.device, stream)
+        n = ctypes.c_int64()
+        args = [self._h, _ptr(cols[0]), _ptr(cols[1]), cols[0].numel(), _ptr(cols[2]), _ptr(cols[3]),
+                cols[2].numel(), int(agg)]
+        rc = self._lib.dim3_groupby_aggregate(*args, None, None, 0, ctypes.byref(n), st)
+        if rc not in (DIM3_OK, DIM3_ERR_CAPACITY):
+            _check(rc)
+        m = n.value
+        x = torch.empty(m, dtype=torch.int32, device=self.device)
+        v = torch.empty(m, dtype=torch.float64 if agg == AGG_AVG else torch.int64, device=self.device)
+        if m:
+            _check(self._lib.dim3_groupby_aggregate(*args, _ptr(x), _ptr(v), m, ctypes.byref(n), st))
+        return x, v
 
     # Section 3 cost constants measured on GB300 (seconds): one SparseBMM join
     # tuple, one DenseEC (x, z) evaluation
