@@ -377,7 +377,9 @@ def main():
     # roofline of the dominant kernel: SparseBMM + union + compaction (emitting
     # pass, HBM-bound), or the tensor-core DenseEC product when every z is dense
     peaks = measured_peaks()
-    phases = {k: round(v[0] / max(v[1], 1), 4) for k, v in tm.items() if v[1]}
+    # per-step totals (a phase may hold several launches per step, e.g. the
+    # bitmap rows and the light rows of one pass)
+    phases = {k: round(v[0] / args.steps, 4) for k, v in tm.items() if v[1]}
     tc_ms, tc_n = tm["dense_tc"]
     if tc_n and tc_ms > tm["sparse_emit"][0]:
         tc_s = tc_ms / 1e3 / tc_n
@@ -390,7 +392,7 @@ def main():
                     "traffic": None, "alg_flops_per_launch": flops, "launch_ms": tc_s * 1e3}
     else:
         emit_ms, emit_n = tm["sparse_emit"]
-        emit_s = emit_ms / 1e3 / max(emit_n, 1)
+        emit_s = emit_ms / 1e3 / args.steps  # the whole emitting pass of one step
         alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
         achieved = alg_bytes / emit_s / 1e9
         traffic, tinfo = traffic_for(args.workload)

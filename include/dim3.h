@@ -118,9 +118,11 @@ typedef enum {
     DIM3_OPT_TIMING = 5,        /* nonzero: record CUDA events around each phase (dim3_ctx_timing) */
     DIM3_OPT_EMIT_ROWS = 6,     /* x rows per CTA in the emitting SparseBMM pass: 1, 2, 4; 0: automatic */
     DIM3_OPT_TWO_PASS = 7,      /* nonzero: always count before emitting (no single-pass look-back) */
-    DIM3_OPT_ID_CHUNK_MAX = 8   /* emitting pass: a 4096-z chunk of one x row holding at most this many
+    DIM3_OPT_ID_CHUNK_MAX = 8,  /* emitting pass: a 4096-z chunk of one x row holding at most this many
                                    pairs is written through staged z ids, a denser one group by group;
                                    0: always group by group; <0: default (512); at most 1024 */
+    DIM3_OPT_PATH = 9           /* dim3_join_project / dim3_join_count: 0 (default) f1 of Section 2.6
+                                   chooses, 1 the hybrid DIM^3 path, 2 the classical solution */
 } dim3_option;
 
 /* Phases timed under DIM3_OPT_TIMING. */
@@ -156,6 +158,22 @@ DIM3_API int dim3_ctx_timing(dim3_ctx *ctx, int phase, double *total_ms, int64_t
 
 /* Number of CUDA kernels this library has launched in this process. */
 DIM3_API int dim3_launch_count(int64_t *out);
+
+/*
+ * Strategy selection f1 (Section 2.6): a one-call join under DIM3_OPT_PATH 0
+ * maps y first, counts |OUT_J| of the input bags from the y ids (S rows per
+ * y, summed over R's rows) and evaluates
+ *   f1 = 2 (|R| + |S|) t_map + |OUT_J| t_randRW - |OUT_J| t_hash;
+ * f1 > 0 stops the mapping and runs the classical solution (hash join +
+ * dedup; here a sort-based join and a radix-sort dedup), else the hybrid path
+ * continues with the y ids already made. The constants
+ * are seconds per input row (mapping), per join tuple in SparseBMM and per
+ * join tuple in the classical path; the defaults were measured on GB300.
+ * dim3_ctx_last_path returns the path of the context's last one-call join
+ * (1 hybrid, 2 classical, 0 none yet).
+ */
+DIM3_API int dim3_ctx_set_f1_costs(dim3_ctx *ctx, double t_map, double t_rand, double t_hash);
+DIM3_API int dim3_ctx_last_path(const dim3_ctx *ctx);
 
 /*
  * dim3_map -- order-preserving mapping of one column to dense ids.

@@ -26,6 +26,10 @@ from .dim3 import (  # noqa: F401
     OPT_EMIT_ROWS,
     OPT_ID_CHUNK_MAX,
     OPT_LIGHT_ROW_MAX,
+    OPT_PATH,
+    PATH_AUTO,
+    PATH_CLASSICAL,
+    PATH_HYBRID,
     OPT_THETA_Z,
     OPT_TIMING,
     OPT_TWO_PASS,

@@ -11,6 +11,7 @@
 struct dim3_ctx {
     dimcube::Ctx c;
     dimcube::Stats stats;
+    int last_path = 0;  // path of the last one-call join: 1 hybrid, 2 classical
     ~dim3_ctx() {
         stats.resolve();
     }
@@ -184,6 +185,10 @@ int dim3_ctx_set_option(dim3_ctx* ctx, int option, int64_t value) {
             case DIM3_OPT_LIGHT_ROW_MAX: ctx->c.opt.light_row_max = value; break;
             case DIM3_OPT_TIMING: ctx->stats.on = value != 0; break;
             case DIM3_OPT_TWO_PASS: ctx->c.opt.two_pass = value; break;
+            case DIM3_OPT_PATH:
+                DIM3_REQUIRE(value >= 0 && value <= 2, DIM3_ERR_ARG, "path must be 0 (f1), 1 (hybrid) or 2 (classical)");
+                ctx->c.opt.path = value;
+                break;
             case DIM3_OPT_ID_CHUNK_MAX:
                 DIM3_REQUIRE(value <= 1024, DIM3_ERR_ARG, "id chunk maximum above 1024");
                 ctx->c.opt.id_chunk_max = value;
@@ -197,6 +202,18 @@ int dim3_ctx_set_option(dim3_ctx* ctx, int option, int64_t value) {
         }
     });
 }
+
+int dim3_ctx_set_f1_costs(dim3_ctx* ctx, double t_map, double t_rand, double t_hash) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx, DIM3_ERR_ARG, "null ctx");
+        DIM3_REQUIRE(t_map >= 0.0 && t_rand >= 0.0 && t_hash >= 0.0, DIM3_ERR_ARG, "negative cost constant");
+        ctx->c.opt.f1c[0] = t_map;
+        ctx->c.opt.f1c[1] = t_rand;
+        ctx->c.opt.f1c[2] = t_hash;
+    });
+}
+
+int dim3_ctx_last_path(const dim3_ctx* ctx) { return ctx ? ctx->last_path : 0; }
 
 int dim3_map(dim3_ctx* ctx, const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,
              void* stream) {
@@ -503,9 +520,20 @@ static int join_common(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t* d_r
         check_table(d_s_key, d_s_val, ns, "S");
         DeviceGuard g(ctx->c.device);
         cudaStream_t s = as_stream(stream);
-        std::unique_ptr<dimcube::Plan> p(
-            dimcube::build_plan(ctx->c, single_input(d_r_key, d_r_val, nr, d_s_key, d_s_val, ns),
-                                resolve_theta(ctx, -1), s));
+        const dimcube::PlanInput in = single_input(d_r_key, d_r_val, nr, d_s_key, d_s_val, ns);
+        const int64_t path = ctx->c.opt.path;
+        std::unique_ptr<dimcube::Plan> p;
+        bool classical = path == 2;
+        if (!classical) {
+            // path 0: f1 (Section 2.6), evaluated right after the y mapping,
+            // may hand the join to the classical solution
+            p.reset(dimcube::build_plan(ctx->c, in, resolve_theta(ctx, -1), s, path == 0 ? &classical : nullptr));
+        }
+        ctx->last_path = classical ? 2 : 1;
+        if (classical) {
+            dimcube::classical_join(ctx->c, in, kind, d_out_x, d_out_z, d_out_cnt, capacity, count, s);
+            return;
+        }
         try {
             dimcube::plan_join(ctx->c, *p, 0, p->info.n_x, kind, d_out_x, d_out_z, d_out_cnt, capacity, count, s);
         } catch (...) {

@@ -63,6 +63,11 @@ struct PlanInput {
 };
 
 // -------------------------------------------------------------------- plan
+// f1 constants measured on GB300 (seconds)
+constexpr double kF1TMap = 4.0e-10;
+constexpr double kF1TRand = 1.0e-12;
+constexpr double kF1THash = 2.0e-11;
+
 struct Options {
     int64_t theta_z = -1;
     int64_t dense_variant = DIM3_DENSE_AUTO;
@@ -71,6 +76,10 @@ struct Options {
     int64_t emit_rows = 0;  // x rows per CTA in the emitting pass (0: automatic)
     int64_t two_pass = 0;   // nonzero: always a counting pass before the emitting pass
     int64_t id_chunk_max = -1;  // pairs per 4096-z chunk written through staged ids (<0: 512)
+    int64_t path = 0;           // one-call joins: 0 f1 decides, 1 hybrid, 2 classical
+    // f1 constants (Section 2.6), seconds: t_map per input row, t_randRW per
+    // join tuple of the hybrid path, t_hash per join tuple of the classical path
+    double f1c[3] = {kF1TMap, kF1TRand, kF1THash};
 };
 
 struct Plan {
@@ -125,6 +134,10 @@ struct Plan {
     DevBuf zc_comp;     // uint8 [n_zc]
     DevBuf zc_xid;      // int32 [zc_nlist]: x ids of the entries' lists
     DevBuf zc_ent;      // int32 [zc_nlist]: entry of each list element
+    // light rows (few join tuples on a wide z range): dedup by sorting their
+    // z ids instead of a |Z|-bit SPA; light_n < 0: not decided yet
+    DevBuf light;        // uint8 [n_x]
+    int64_t light_n = -1;
     // cached row offsets of the last counting pass
     int64_t cache_begin = -1, cache_end = -1;
     int cache_kind = -1;
@@ -166,7 +179,11 @@ struct Ctx {
     Options opt;
 };
 
-Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStream_t s);
+// prefer_classical non-null (a single instance of value columns): after the
+// y mapping, evaluate f1 (Section 2.6); when it favours the classical
+// solution, set *prefer_classical and return nullptr without finishing.
+Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStream_t s,
+                 bool* prefer_classical = nullptr);
 
 // Output of a join over an x-id range: counts pass + scan + emit pass.
 // kind 0 = project, 1 = count. Returns the number of pairs; writes only when
@@ -215,6 +232,15 @@ int64_t join_aggregate(const Ctx& ctx, const PlanInput& in, const int32_t* r_v, 
                        cudaStream_t s);
 int64_t groupby_aggregate(const Ctx& ctx, const PlanInput& in, int agg, int32_t* out_x, void* out_val,
                           int64_t capacity, int64_t* count, cudaStream_t s);
+
+// The classical solution (classical.cu): distinct tuples sorted by y, join by
+// binary search, dedup by radix sort (kind 0 project, 1 count); the bag join
+// without dedup; f1 of Section 2.6 (> 0: classical).
+int64_t classical_join(const Ctx& ctx, const PlanInput& in, int kind, int32_t* out_x, int32_t* out_z,
+                       int32_t* out_cnt, int64_t capacity, int64_t* count, cudaStream_t s);
+int64_t bag_join(const Ctx& ctx, const PlanInput& in, int32_t* out_x, int32_t* out_z, int64_t capacity,
+                 int64_t* count, cudaStream_t s);
+double f1_value(int64_t nr, int64_t ns, int64_t out_j, const double* c);
 
 // Value mapping with all scratch in a fixed device array (noalloc.cu).
 void map_noalloc(const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,

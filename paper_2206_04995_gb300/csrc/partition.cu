@@ -486,7 +486,27 @@ static void premapped_ids(Plan& p, const PlanInput& in, cudaStream_t s) {
     }
 }
 
-Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStream_t s) {
+__global__ void k_count_ids(const int32_t* __restrict__ ids, int64_t n, unsigned long long* cnt) {
+    GRID_STRIDE(i, n) {
+        const int32_t v = ids[i];
+        if (v >= 0) atomicAdd(cnt + v, 1ull);
+    }
+}
+
+// sum over R rows (with a y id) of the S rows of that y: |OUT_J| of the bags
+__global__ void k_sum_deg(const int32_t* __restrict__ ids, int64_t n, const unsigned long long* __restrict__ deg,
+                          unsigned long long* total) {
+    __shared__ unsigned long long s_warp[kThreads / 32 + 1];
+    unsigned long long acc = 0;
+    GRID_STRIDE(i, n) {
+        const int32_t v = ids[i];
+        if (v >= 0) acc += deg[v];
+    }
+    acc = block_sum<unsigned long long, kThreads>(acc, s_warp);
+    if (threadIdx.x == 0 && acc) atomicAdd(total, acc);
+}
+
+Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStream_t s, bool* prefer_classical) {
     PhaseScope phase(ctx.stats, PH_PARTITION, s);
     std::unique_ptr<Plan> p(new Plan());
     const int64_t nr = in.nr, ns = in.ns;
@@ -526,6 +546,27 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
                             p->dict_y.as<int32_t>(), y_tag.as<int32_t>(), s);
             p->info.n_y = ymap.n_distinct;
             probe_value_map(ymap, in.r_key, in.r_tag, nr, ry_id.as<int32_t>(), s);
+        }
+        if (prefer_classical) {
+            // f1 (Section 2.6) from the y ids just made: |OUT_J| of the bags
+            const int64_t n_y = p->info.n_y;
+            DevBuf deg, tot;
+            deg.alloc((size_t)std::max<int64_t>(n_y, 1) * 8, s);
+            tot.alloc(8, s);
+            DIM3_CUDA(cudaMemsetAsync(deg.p, 0, deg.bytes, s));
+            DIM3_CUDA(cudaMemsetAsync(tot.p, 0, 8, s));
+            if (ns > 0) {
+                k_count_ids<<<grid_for(ns), kThreads, 0, s>>>(sy_id.as<int32_t>(), ns, deg.as<unsigned long long>());
+                DIM3_LAUNCHED();
+            }
+            if (nr > 0) {
+                k_sum_deg<<<grid_for(nr), kThreads, 0, s>>>(ry_id.as<int32_t>(), nr, deg.as<unsigned long long>(),
+                                                             tot.as<unsigned long long>());
+                DIM3_LAUNCHED();
+            }
+            const int64_t out_j = read_i64(tot.as<int64_t>(), s);
+            *prefer_classical = f1_value(nr, ns, out_j, ctx.opt.f1c) > 0.0;
+            if (*prefer_classical) return nullptr;
         }
         {
             ValueMap xmap;

@@ -67,6 +67,7 @@ struct XRowArgs {
     int stage_ints;
     int id_max;  // a 4096-z chunk with at most this many pairs goes through staged ids
     int flat_max;  // x rows (groups) with at most this many R entries take the one-phase build
+    const uint8_t* light;  // per x id: handled by the light-row kernel (skip here), or null
     const int64_t* off;      // emitting pass: [n_rows + 1]
     int32_t* out_x;
     int32_t* out_z;
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(kThreads, kEmit ? 4 : 8) k_xrow_bits(const XRo
     }
     if (xr >= a.n_rows) return;
     const int64_t x = a.x_begin + xr;
+    if (a.light && a.light[x]) return;  // the light-row kernel counts and writes it
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // z window of x's instance (all of Z for a single instance), from a
@@ -1011,6 +1013,7 @@ static XRowArgs make_args(const Plan& p, int64_t x_begin, int64_t rows, int kind
     a.stage_ints = kWarpStageIds;
     a.id_max = 512;
     a.flat_max = kThreads;
+    a.light = nullptr;
     return a;
 }
 
@@ -1065,6 +1068,173 @@ static XRowArgs prep_args(Plan& p, int64_t x_begin, int64_t rows, int kind, cuda
     return a;
 }
 
+// ------------------------------------------------------------ light rows
+// An x whose join tuples are few (|OUT_J| of the row <= kLightMax) on a wide z
+// range pays more for clearing and scanning a |Z|-bit SPA than for its
+// tuples. One warp per such row gathers the z ids of its join tuples into
+// shared memory, sorts them (bitonic network) and keeps the first of each run:
+// the same deduplicated, ascending z as the SPA gives.
+constexpr int kLightMax = 1024;
+constexpr int64_t kLightMinZ = 65536;  // z range from which light rows pay off
+
+struct LightArgs {
+    const int32_t* rows;  // row numbers (x - x_begin) of the light rows
+    int64_t n, x_begin;
+    const int64_t* r_rowptr;
+    const int32_t* r_col;
+    const int64_t* ss_rowptr;
+    const int32_t* ss_col;
+    const int32_t* dict_x;
+    const int32_t* dict_z;
+    int64_t* cnt;         // counting pass out
+    const int64_t* off;   // emitting pass: row offsets
+    int32_t* out_x;
+    int32_t* out_z;
+};
+
+template <bool kEmit>
+__global__ void __launch_bounds__(kThreads) k_light_rows(const LightArgs a) {
+    __shared__ int32_t s_buf[kWarps][kLightMax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t* buf = s_buf[warp];
+    const unsigned lt = lanemask_lt();
+    for (int64_t i = blockIdx.x * (int64_t)kWarps + warp; i < a.n; i += (int64_t)gridDim.x * kWarps) {
+        const int64_t xr = a.rows[i], x = a.x_begin + xr;
+        int n = 0;
+        for (int64_t q = a.r_rowptr[x]; q < a.r_rowptr[x + 1]; ++q) {
+            const int32_t y = a.r_col[q];
+            const int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+            for (int64_t j = s0 + lane; j < s1; j += 32) buf[n + (int)(j - s0)] = a.ss_col[j];
+            n += (int)(s1 - s0);
+        }
+        int pw = 1;
+        while (pw < n) pw <<= 1;
+        for (int t = n + lane; t < pw; t += 32) buf[t] = INT32_MAX;
+        __syncwarp();
+        for (int k = 2; k <= pw; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = lane; t < (pw >> 1); t += 32) {
+                    const int lo = (t / j) * 2 * j + (t % j), hi = lo + j;
+                    const int32_t u = buf[lo], v = buf[hi];
+                    if ((u > v) == ((lo & k) == 0)) {
+                        buf[lo] = v;
+                        buf[hi] = u;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        int64_t o = kEmit ? a.off[xr] : 0;
+        int run = 0;
+        for (int base = 0; base < n; base += 32) {
+            const int t = base + lane;
+            const int32_t v = t < n ? buf[t] : 0;
+            const bool first = t < n && (t == 0 || buf[t - 1] != v);
+            const unsigned bal = __ballot_sync(kFull, first);
+            if (kEmit && first) {
+                const int64_t at = o + run + __popc(bal & lt);
+                a.out_x[at] = a.dict_x[x];
+                a.out_z[at] = a.dict_z[v];
+            }
+            run += __popc(bal);
+        }
+        if (!kEmit && lane == 0) a.cnt[xr] = run;
+        __syncwarp();
+    }
+}
+
+__global__ void k_light_flags(const int64_t* __restrict__ outj_x, int64_t n_x, int64_t lim, uint8_t* light) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n_x; x += (int64_t)gridDim.x * blockDim.x)
+        light[x] = outj_x[x] <= lim ? 1 : 0;
+}
+
+__global__ void k_light_range(const uint8_t* __restrict__ light, int64_t x_begin, int64_t rows, int32_t* flag) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = light[x_begin + r];
+}
+
+__global__ void k_light_list(const int32_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t rows,
+                             int32_t* list) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
+        if (flag[r]) list[pos[r]] = (int32_t)r;
+}
+
+static unsigned blocks_for(int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kThreads), 152 * 16));
+}
+
+__global__ void k_count_flags(const uint8_t* __restrict__ f, int64_t n, unsigned long long* total) {
+    __shared__ unsigned long long s_warp[kThreads / 32 + 1];
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += f[i];
+    c = block_sum<unsigned long long, kThreads>(c, s_warp);
+    if (threadIdx.x == 0 && c) atomicAdd(total, c);
+}
+
+// Decide once per plan whether light rows apply: a single instance, no dense
+// or cached columns (their bits would have to join the sort), a z range of at
+// least kLightMinZ, and either a z-tiled plan or a quarter of the rows light
+// (otherwise the one-row kernel and the two passes that light rows require
+// cost the heavy rows more than the light rows save). Returns the flags or null.
+static const uint8_t* ensure_light(const Ctx& ctx, Plan& p, cudaStream_t s) {
+    if (p.light_n < 0) {
+        p.light_n = 0;
+        const int64_t lim = ctx.opt.light_row_max < 0 ? kLightMax : std::min<int64_t>(ctx.opt.light_row_max, kLightMax);
+        if (lim > 0 && p.n_inst == 1 && p.n_zd_total == 0 && p.info.n_z >= kLightMinZ && p.info.n_x > 0) {
+            p.light.alloc((size_t)p.info.n_x, s);
+            k_light_flags<<<blocks_for(p.info.n_x), kThreads, 0, s>>>(p.outj_x.as<int64_t>(), p.info.n_x, lim,
+                                                                     p.light.as<uint8_t>());
+            DIM3_LAUNCHED();
+            DevBuf tot;
+            tot.alloc(8, s);
+            DIM3_CUDA(cudaMemsetAsync(tot.p, 0, 8, s));
+            k_count_flags<<<blocks_for(p.info.n_x), kThreads, 0, s>>>(p.light.as<uint8_t>(), p.info.n_x,
+                                                                     tot.as<unsigned long long>());
+            DIM3_LAUNCHED();
+            const int64_t n_light = read_i64(tot.as<int64_t>(), s);
+            const bool tiled = p.zw > kMaxTileWords;
+            if (n_light > 0 && (tiled || 4 * n_light >= p.info.n_x)) p.light_n = n_light;
+            else p.light.release();
+        }
+    }
+    return p.light_n > 0 ? p.light.as<uint8_t>() : nullptr;
+}
+
+// the light rows of [x_begin, x_begin + rows): counting (cnt) or emitting (off)
+static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* cnt, const int64_t* off,
+                         int32_t* out_x, int32_t* out_z, cudaStream_t s) {
+    DevBuf flag, pos, list;
+    flag.alloc((size_t)rows * 4, s);
+    pos.alloc((size_t)(rows + 1) * 8, s);
+    k_light_range<<<blocks_for(rows), kThreads, 0, s>>>(p.light.as<uint8_t>(), x_begin, rows, flag.as<int32_t>());
+    DIM3_LAUNCHED();
+    exclusive_scan_i32_to_i64(flag.as<int32_t>(), pos.as<int64_t>(), rows, s);
+    const int64_t n = read_i64(pos.as<int64_t>() + rows, s);
+    if (n == 0) return;
+    list.alloc((size_t)n * 4, s);
+    k_light_list<<<blocks_for(rows), kThreads, 0, s>>>(flag.as<int32_t>(), pos.as<int64_t>(), rows, list.as<int32_t>());
+    DIM3_LAUNCHED();
+    LightArgs la{};
+    la.rows = list.as<int32_t>();
+    la.n = n;
+    la.x_begin = x_begin;
+    la.r_rowptr = p.r_rowptr.as<int64_t>();
+    la.r_col = p.r_col.as<int32_t>();
+    la.ss_rowptr = p.ss_rowptr.as<int64_t>();
+    la.ss_col = p.ss_col.as<int32_t>();
+    la.dict_x = p.dict_x.as<int32_t>();
+    la.dict_z = p.dict_z.as<int32_t>();
+    la.cnt = cnt;
+    la.off = off;
+    la.out_x = out_x;
+    la.out_z = out_z;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kWarps), 152 * 8));
+    if (off) k_light_rows<true><<<g, kThreads, 0, s>>>(la);
+    else k_light_rows<false><<<g, kThreads, 0, s>>>(la);
+    DIM3_LAUNCHED();
+}
+
 static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, cudaStream_t s) {
     if (a.n_rows <= 0 || a.n_z <= 0) return;
     setup_attrs(ctx);
@@ -1074,7 +1244,7 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
     if (kind == 0) {
         const size_t sm = bits_smem(a.tile_bits, emit, a.stage_ints);
         // several rows per CTA share one z window, so batches use one row per CTA
-        const int grp = (emit && a.x_tag == nullptr) ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
+        const int grp = (emit && a.x_tag == nullptr && !a.light) ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
         if (emit && grp > 1) {
             const size_t smg = (size_t)kWarps * kWarpStage * 4 + (size_t)grp * (size_t)(a.tile_bits / 32) * 4;
             const unsigned gg = (unsigned)ceil_div(a.n_rows, grp);
@@ -1133,7 +1303,12 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
             a.d_bits = p.cache_dbits.as<uint32_t>();
             a.d_cnt = p.cache_dcnt.as<int32_t>();
             a.cnt = cnt.as<int64_t>();
+            a.light = kind == 0 ? ensure_light(ctx, p, s) : nullptr;
             launch_rows(ctx, a, kind, false, s);
+            if (a.light) {
+                PhaseScope phase(ctx.stats, PH_COUNT, s);
+                launch_light(p, x_begin, rows, cnt.as<int64_t>(), nullptr, nullptr, nullptr, s);
+            }
         }
     }
     exclusive_scan_i64(cnt.as<int64_t>(), p.cache_off.as<int64_t>(), rows, s);
@@ -1235,7 +1410,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
     check_range(p, x_begin, x_end);
     const bool cached = p.cache_begin == x_begin && p.cache_end == x_end && p.cache_kind == kind;
     if (!cached && kind == 0 && capacity > 0 && out_x && out_z && x_end > x_begin && p.info.n_z > 0 &&
-        p.info.n_r_kept > 0 && p.zw <= kMaxTileWords && !ctx.opt.two_pass)
+        p.info.n_r_kept > 0 && p.zw <= kMaxTileWords && !ctx.opt.two_pass && !ensure_light(ctx, p, s))
         return plan_join_single_pass(ctx, p, x_begin, x_end, out_x, out_z, capacity, count, s);
     ensure_counts(ctx, p, x_begin, x_end, kind, s);
     const int64_t rows = x_end - x_begin;
@@ -1256,7 +1431,12 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
                              (kind ? reinterpret_cast<uintptr_t>(out_cnt) : 0);
         a.vec_ok = (al & 15u) == 0;
         set_stage(ctx, p, a, total);
+        a.light = kind == 0 ? ensure_light(ctx, p, s) : nullptr;
         launch_rows(ctx, a, kind, true, s);
+        if (a.light) {
+            PhaseScope phase(ctx.stats, PH_EMIT, s);
+            launch_light(p, x_begin, rows, nullptr, a.off, out_x, out_z, s);
+        }
     }
     DIM3_CUDA(cudaStreamSynchronize(s));
     return total;

@@ -31,6 +31,8 @@ AGG_COUNT, AGG_SUM, AGG_MIN, AGG_MAX, AGG_AVG = 0, 1, 2, 3, 4
 FN_MUL, FN_ADD, FN_LEFT, FN_RIGHT = 0, 1, 2, 3
 OPT_TWO_PASS = 7
 OPT_ID_CHUNK_MAX = 8
+OPT_PATH = 9
+PATH_AUTO, PATH_HYBRID, PATH_CLASSICAL = 0, 1, 2
 PHASES = {"map": 0, "partition": 1, "dense_ec": 2, "sparse_count": 3, "sparse_emit": 4, "dense_tc": 5}
 
 TABLES = {
@@ -106,6 +108,8 @@ def load(build_if_missing: bool = True):
                                     ctypes.POINTER(PlanInfo), P], INT),
             "dim3_map_tuples": ([P, P, ctypes.c_int, ctypes.c_uint32, I64, P, P, ctypes.POINTER(I64), P], INT),
             "dim3_gather_i32": ([P, P, I64, P, I64, P, P], INT),
+            "dim3_ctx_set_f1_costs": ([P, ctypes.c_double, ctypes.c_double, ctypes.c_double], INT),
+            "dim3_ctx_last_path": ([P], INT),
             "dim3_join_aggregate": ([P, P, P, P, I64, P, P, P, I64, ctypes.c_int, ctypes.c_int, P, P, P, I64,
                                      ctypes.POINTER(I64), P], INT),
             "dim3_groupby_aggregate": ([P, P, P, I64, P, P, I64, ctypes.c_int, P, P, I64, ctypes.POINTER(I64), P],
@@ -251,6 +255,14 @@ class Context:
                                             s_y.numel(), int(n_x), int(n_y), int(n_z), int(theta_z),
                                             ctypes.byref(h), ctypes.byref(info), _stream(self.device, stream)))
         return Plan(self, h, info, stream)
+
+    def set_f1_costs(self, t_map: float, t_rand: float, t_hash: float):
+        """Constants of f1 (Section 2.6), seconds."""
+        _check(self._lib.dim3_ctx_set_f1_costs(self._h, float(t_map), float(t_rand), float(t_hash)))
+
+    def last_path(self) -> int:
+        """Path of the last one-call join: 1 hybrid, 2 classical."""
+        return int(self._lib.dim3_ctx_last_path(self._h))
 
     # ------------------------------------------------------- Join-Aggregate
     def join_aggregate(self, r_key, r_val, r_v, s_key, s_val, s_u, agg: int, fn: int = FN_MUL, out=None,

@@ -17,12 +17,14 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ctx():
     c = dim3.Context(0)
+    c.set_option(dim3.OPT_PATH, dim3.PATH_HYBRID)  # these tests target the hybrid kernels
     yield c
     c.close()
 
 
 def fresh_ctx(opts):
     c = dim3.Context(0)
+    c.set_option(dim3.OPT_PATH, dim3.PATH_HYBRID)
     for k, v in opts.items():
         c.set_option(k, v)
     return c
@@ -334,4 +336,38 @@ def test_id_chunk_threshold_range():
     c = fresh_ctx({})
     with pytest.raises(dim3.Dim3Error):
         c.set_option(8, 1025)
+    c.close()
+
+
+def _wide_sparse(seed, n, ny):
+    rng = np.random.default_rng(seed)
+    return gen.Instance("wide_sparse", rng.integers(0, ny, n).astype(np.int32),
+                        rng.integers(-10**7, 10**7, n).astype(np.int32), rng.integers(0, ny, n).astype(np.int32),
+                        rng.integers(-10**7, 10**7, n).astype(np.int32))
+
+
+@pytest.fixture(scope="module")
+def wide_insts():
+    insts = (_wide_sparse(71, 200_000, 50_000), gen.chung_lu_self(np.random.default_rng(72), 100_000, 200_000, 2.1))
+    return [(inst, *oracle.join_project(inst.r_key, inst.r_val, inst.s_key, inst.s_val)[:2]) for inst in insts]
+
+
+@pytest.mark.parametrize("light_max", [-1, 0, 5, 1024])
+def test_light_rows(light_max, wide_insts):
+    """Rows with few join tuples on a wide z range are deduplicated by sorting
+    (any threshold gives the SPA's result): uniform sparse tables, a power-law
+    graph with hubs (heavy rows) among light rows, both passes and x ranges."""
+    c = fresh_ctx({4: light_max})
+    for inst, ox, oz in wide_insts:
+        gx, gz = project(c, inst)
+        assert np.array_equal(gx, ox) and np.array_equal(gz, oz), inst.name
+        plan = c.partition(*inst_dev(inst))
+        n_x = plan.info["n_x"]
+        xs, zs = [], []
+        for a, b in ((0, n_x // 2), (n_x // 2, n_x)):
+            x, z = plan.join_project(a, b)
+            xs.append(host(x))
+            zs.append(host(z))
+        plan.close()
+        assert np.array_equal(np.concatenate(xs), ox) and np.array_equal(np.concatenate(zs), oz)
     c.close()
