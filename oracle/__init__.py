@@ -16,6 +16,8 @@ shares no code with that path.
   ``join_project_cached`` -- partial result caching, Section 3 (``cache.py``).
 * ``join_aggregate`` / ``groupby_aggregate`` -- Join-Aggregate, Section 4.1,
   from the materialised join (``aggregate.py``).
+* ``line_join_project`` / ``chain_sizes`` / ``mjp_dp`` -- multi-way joins
+  with projection and the deduplication-placement DP, Section 4.2 (``mjp.py``).
 * ``plan`` -- the mapping and partition quantities of Algorithm 1 (semi-join
   filtered y dictionary of Section 2.2 "Optimization 2", x/z dictionaries,
   degrees m_x and m_z, |OUT_J|, the dense z set of Section 2.3) written out
@@ -35,5 +37,7 @@ from .core import (  # noqa: F401
 )
 from .aggregate import groupby_aggregate, join_aggregate  # noqa: F401
 from .cache import cache_build, cache_scores, cache_select, cache_stats, join_project_cached  # noqa: F401
+from .mjp import chain_sizes, line_join_project  # noqa: F401
+from .mjp import dp as mjp_dp  # noqa: F401
 from .mapping import join_count_ids, join_project_ids, map_tuples  # noqa: F401
 from .plan import plan  # noqa: F401
