@@ -59,6 +59,9 @@ def parse_args():
     ap.add_argument("--aggregate", default=None,
                     help="AGG:FN, e.g. sum:mul: time the Join-Aggregate (Section 4.1) on the workload, "
                          "values uniform in [-100, 100)")
+    ap.add_argument("--mjp", type=int, default=0,
+                    help="k: time the k-hop line query Pi(E join ... join E) (Section 4.2) on the workload's "
+                         "edges, with the DP's deduplication placement and the two baseline plans")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -266,6 +269,9 @@ def main():
         return
     if args.aggregate:
         run_aggregate(args, rank, world, local_rank)
+        return
+    if args.mjp:
+        run_mjp(args, rank, world, local_rank)
         return
 
     import torch
@@ -682,6 +688,77 @@ def run_aggregate(args, rank, world, local_rank):
             "config": {"workload": inst.name, "aggregate": args.aggregate, "groups": n, "n_r": inst.nr,
                        "n_s": inst.ns, "l2": "flushed between steps (256 MiB write outside the step events)"},
             "phase_ms": {k: round(a / max(b, 1), 4) for k, (a, b) in tm.items() if b},
+            "gpu_launches": launches, "clocks": clocks,
+        }), flush=True)
+    ctx.close()
+
+
+def run_mjp(args, rank, world, local_rank):
+    """k-hop line query over the workload's R as an edge list (x -> y):
+    exact chain sizes, the DP's deduplication placement (Section 4.2), and
+    the time of that plan against deduplicating after every join and only
+    after the last (skipped when its bag would not fit in memory). Result
+    pairs per second of the DP's plan."""
+    import torch
+
+    import paper_2206_04995_gb300 as dim3
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    inst = make_workload(args.workload, rank, args.scale)
+    a = torch.from_numpy(np.ascontiguousarray(inst.r_val, np.int32)).to(dev)
+    b = torch.from_numpy(np.ascontiguousarray(inst.r_key, np.int32)).to(dev)
+    k = args.mjp
+    tables = [(a, b)] * k
+    ctx = dim3.Context(local_rank)
+    t0 = time.perf_counter()
+    out_j, out_p = ctx.mjp_sizes(tables)
+    sizes_s = time.perf_counter() - t0
+    n_edges = float(np.unique(np.stack([inst.r_val, inst.r_key], 1), axis=0).shape[0])
+    dedup, est = dim3.Context.mjp_plan([n_edges] * k, out_j, out_p)
+    n = int(out_p[-1])
+    out = (torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def timed(flags):
+        for _ in range(args.warmup):
+            ctx.mjp_execute(tables, flags, out=out)
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(args.steps):
+            flush.fill_(i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x, _ = ctx.mjp_execute(tables, flags, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            assert x.numel() == n
+            ms.append(e0.elapsed_time(e1))
+        return sum(ms) / len(ms)
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = dim3.launch_count()
+    dp_ms = timed(dedup)
+    launches = dim3.launch_count() - l0
+    clocks = sampler.stop()
+    plans = {"dp": {"dedup": dedup, "ms": dp_ms, "estimate": est}}
+    every = [False] + [True] * (k - 1)
+    plans["every_join"] = {"dedup": every, "ms": dp_ms if every == dedup else timed(every)}
+    last = [False] * (k - 1) + [True]
+    bag = max(out_j[:-1]) if k > 1 else 0.0
+    if bag * 16 < 0.5 * torch.cuda.get_device_properties(dev).total_memory:
+        plans["last_only"] = {"dedup": last, "ms": dp_ms if last == dedup else timed(last)}
+    else:
+        plans["last_only"] = {"dedup": last, "ms": None, "skipped": f"bag of {bag:.3g} pairs"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": n / (dp_ms / 1e3), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dp_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{inst.name} {k}-hop line query", "edges": n_edges, "out_j": out_j,
+                       "out_p": out_p, "sizes_s": sizes_s, "plans": plans,
+                       "l2": "flushed between steps (256 MiB write outside the step events)"},
             "gpu_launches": launches, "clocks": clocks,
         }), flush=True)
     ctx.close()

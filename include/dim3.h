@@ -85,6 +85,13 @@ typedef struct {
     int64_t ns;
 } dim3_instance;
 
+/* One relation R_i(x_i, x_{i+1}) of a multi-way join (device int32 columns). */
+typedef struct {
+    const int32_t *d_a;  /* x_i */
+    const int32_t *d_b;  /* x_{i+1} */
+    int64_t n;
+} dim3_edge_table;
+
 /* DenseEC bitmap-intersection variants (Algorithm 3; the choice is the role
  * of f3 in Section 2.6). All give identical results. */
 typedef enum {
@@ -373,6 +380,36 @@ DIM3_API int dim3_groupby_aggregate(dim3_ctx *ctx, const int32_t *d_r_key, const
                                     const int32_t *d_s_key, const int32_t *d_s_val, int64_t ns, int agg,
                                     int32_t *d_out_x, void *d_out_val, int64_t capacity, int64_t *count,
                                     void *stream);
+
+/*
+ * Multi-way joins with projection, MJP (Section 4.2): the line query
+ *   Pi_{x_1, x_{k+1}}(R_1(x_1, x_2) join R_2(x_2, x_3) join ... join R_k(x_k, x_{k+1}))
+ * over a left-deep plan, relations as sets.
+ *
+ * dim3_mjp_sizes -- |OUT_J_i| (join paths through R_1 .. R_i) and |OUT_P_i|
+ * (distinct (x_1, x_{i+1})) for i = 1..k, exact (path counts in double,
+ * exact below 2^53); out_j, out_p host arrays of k entries.
+ *
+ * dim3_mjp_plan -- the dynamic programme of Section 4.2 on the sizes:
+ *   DP_1 = 0, DP_i = min_{j<i} DP_j + sum_{h=j+1}^{i-1} JoinCost_h + JPCost_i,
+ * input sizes after a deduplication at j scaled by |OUT_P_j| / |OUT_J_j|; with
+ *   JoinCost(l, r, out)  = c[0] (l + r) + c[1] out             (bag join)
+ *   JPCost(l, r, oj, op) = c[2] (l + r) + c[3] oj + c[4] op    (Join-Project).
+ * Ties take the smaller j. dedup[i] = 1 when a deduplication follows the
+ * join with table i (0-based; dedup[0] = 0, dedup[k-1] = 1); *cost = DP_k.
+ * Host only (no context, no device work).
+ *
+ * dim3_mjp_execute -- run a placement: joins flagged in dedup are Join-
+ * Projects of this library, the others bag joins (every running pair joins).
+ * The result pairs (x_1, x_{k+1}) in canonical order go to d_out_x, d_out_z;
+ * capacity protocol as dim3_join_project. dedup[k-1] must be 1.
+ */
+DIM3_API int dim3_mjp_sizes(dim3_ctx *ctx, int k, const dim3_edge_table *tables, double *out_j, double *out_p,
+                            void *stream);
+DIM3_API int dim3_mjp_plan(int k, const double *r_size, const double *out_j, const double *out_p,
+                           const double *c, int *dedup, double *cost);
+DIM3_API int dim3_mjp_execute(dim3_ctx *ctx, int k, const dim3_edge_table *tables, const int *dedup,
+                              int32_t *d_out_x, int32_t *d_out_z, int64_t capacity, int64_t *count, void *stream);
 
 /* Copy of the plan's sizes. */
 DIM3_API int dim3_plan_get_info(const dim3_plan *plan, dim3_plan_info *info);

@@ -37,40 +37,47 @@ def _edges(t):
 
 
 def line_join_project(tables):
-    """(x_1, x_{k+1}) pairs of the line query, canonical order."""
+    """(x_1, x_{k+1}) pairs of the line query, canonical (signed) order."""
     a, b = _edges(tables[0])
+    if len(tables) == 1:
+        order = np.lexsort((b, a))
+        a, b = a[order], b[order]
+        keep = np.ones(a.size, bool)
+        keep[1:] = (a[1:] != a[:-1]) | (b[1:] != b[:-1])
+        return a[keep], b[keep]
     x, z = a, b
     for t in tables[1:]:
         ta, tb = _edges(t)
         x, z, _ = join_project(z, x, ta, tb)  # R(x = x_1, y = current end), S(z = next, y = x_i)
-    packed = np.unique((x.astype(np.int64) << 32) | (z.astype(np.int64) & 0xFFFFFFFF))
-    return (packed >> 32).astype(np.int32), (packed & 0xFFFFFFFF).astype(np.uint32).view(np.int32)
+    return x, z
+
+
+def _distinct_edges(t):
+    a, b = _edges(t)
+    e = np.unique((a.astype(np.int64) << 32) | (b.astype(np.int64) & 0xFFFFFFFF))
+    return (e >> 32).astype(np.int32), (e & 0xFFFFFFFF).astype(np.uint32).view(np.int32)
 
 
 def chain_sizes(tables):
     """(out_j, out_p) lists of length k (float64)."""
-    ta, tb = _edges(tables[0])
-    r1 = np.unique((ta.astype(np.int64) << 32) | (tb.astype(np.int64) & 0xFFFFFFFF))
-    start = (r1 & 0xFFFFFFFF).astype(np.uint32).view(np.int32)  # the x_2 of each R_1 tuple
-    firsts = (r1 >> 32).astype(np.int32)
-    out_j = [float(r1.size)]
-    out_p = [float(r1.size)]
-    # bag sizes: number of join paths, by counting paths per end value
-    ends, counts = np.unique(start, return_counts=True)
-    paths = dict(zip(ends.tolist(), counts.astype(np.float64).tolist()))
-    x, z = firsts, start
+    ea, eb = _distinct_edges(tables[0])
+    out_j = [float(ea.size)]
+    out_p = [float(ea.size)]
+    # bag sizes: the number of join paths ending at each value, carried along
+    # every table's edges (integer sums, exact in float64 below 2^53)
+    vals, counts = np.unique(eb, return_counts=True)
+    counts = counts.astype(np.float64)
+    x, z = ea, eb
     for t in tables[1:]:
-        a, b = _edges(t)
-        e = np.unique((a.astype(np.int64) << 32) | (b.astype(np.int64) & 0xFFFFFFFF))
-        ea = (e >> 32).astype(np.int32)
-        eb = (e & 0xFFFFFFFF).astype(np.uint32).view(np.int32)
-        nxt = {}
-        for u, v in zip(ea.tolist(), eb.tolist()):
-            if u in paths:
-                nxt[v] = nxt.get(v, 0.0) + paths[u]
-        paths = nxt
-        out_j.append(float(sum(paths.values())))
-        x, z, _ = join_project(z, x, a, b)
+        ua, ub = _distinct_edges(t)
+        pos = np.searchsorted(vals, ua)
+        ok = (pos < vals.size) & (vals[np.minimum(pos, max(vals.size - 1, 0))] == ua) if vals.size else \
+            np.zeros(ua.size, bool)
+        w = counts[pos[ok]]
+        vals, inv = np.unique(ub[ok], return_inverse=True)
+        counts = np.bincount(inv, weights=w, minlength=vals.size)
+        out_j.append(float(counts.sum()))
+        x, z, _ = join_project(z, x, *_edges(t))
         out_p.append(float(x.size))
     return out_j, out_p
 

@@ -427,6 +427,42 @@ int dim3_groupby_aggregate(dim3_ctx* ctx, const int32_t* d_r_key, const int32_t*
     });
 }
 
+static void check_edges(int k, const dim3_edge_table* t) {
+    DIM3_REQUIRE(k >= 1 && t, DIM3_ERR_ARG, "need at least one table");
+    for (int i = 0; i < k; ++i) check_table(t[i].d_a, t[i].d_b, t[i].n, "R_i");
+}
+
+int dim3_mjp_sizes(dim3_ctx* ctx, int k, const dim3_edge_table* tables, double* out_j, double* out_p, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && out_j && out_p, DIM3_ERR_ARG, "null ctx or output");
+        check_edges(k, tables);
+        DeviceGuard g(ctx->c.device);
+        dimcube::mjp_sizes(ctx->c, k, tables, out_j, out_p, as_stream(stream));
+    });
+}
+
+int dim3_mjp_plan(int k, const double* r_size, const double* out_j, const double* out_p, const double* c, int* dedup,
+                  double* cost) {
+    return guarded([&] {
+        DIM3_REQUIRE(k >= 1 && r_size && out_j && out_p && c && dedup, DIM3_ERR_ARG, "null argument");
+        for (int i = 0; i < 5; ++i) DIM3_REQUIRE(c[i] >= 0.0, DIM3_ERR_ARG, "negative cost constant");
+        const double v = dimcube::mjp_dp(k, r_size, out_j, out_p, c, dedup);
+        if (cost) *cost = v;
+    });
+}
+
+int dim3_mjp_execute(dim3_ctx* ctx, int k, const dim3_edge_table* tables, const int* dedup, int32_t* d_out_x,
+                     int32_t* d_out_z, int64_t capacity, int64_t* count, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx && count && dedup, DIM3_ERR_ARG, "null ctx, dedup or count");
+        DIM3_REQUIRE(capacity >= 0, DIM3_ERR_ARG, "negative capacity");
+        *count = 0;
+        check_edges(k, tables);
+        DeviceGuard g(ctx->c.device);
+        dimcube::mjp_execute(ctx->c, k, tables, dedup, d_out_x, d_out_z, capacity, count, as_stream(stream));
+    });
+}
+
 int dim3_plan_get_info(const dim3_plan* plan, dim3_plan_info* info) {
     return guarded([&] {
         DIM3_REQUIRE(plan && info, DIM3_ERR_ARG, "null plan or info");

@@ -33,8 +33,9 @@ __global__ void k_pack_yv(const int32_t* __restrict__ y, const int32_t* __restri
     GRID_STRIDE(i, n) keys[i] = ((uint64_t)flip(y[i]) << 32) | flip(v[i]);
 }
 
-// the distinct (y, value) tuples of a table, ascending
-static int64_t sorted_tuples(const int32_t* y, const int32_t* v, int64_t n, DevBuf& out, cudaStream_t s) {
+// the (y, value) tuples of a table, ascending; distinct unless keep_dups
+static int64_t sorted_tuples(const int32_t* y, const int32_t* v, int64_t n, DevBuf& out, cudaStream_t s,
+                             bool keep_dups = false) {
     DevBuf keys, alt;
     keys.alloc((size_t)std::max<int64_t>(n, 1) * 8, s);
     alt.alloc((size_t)std::max<int64_t>(n, 1) * 8, s);
@@ -43,6 +44,10 @@ static int64_t sorted_tuples(const int32_t* y, const int32_t* v, int64_t n, DevB
         DIM3_LAUNCHED();
     }
     radix_sort_u64(keys.as<uint64_t>(), nullptr, alt.as<uint64_t>(), nullptr, n, 64, s);
+    if (keep_dups) {
+        out = std::move(keys);
+        return n;
+    }
     out.alloc((size_t)std::max<int64_t>(n, 1) * 8, s);
     return n > 0 ? unique_sorted_u64(keys.as<uint64_t>(), out.as<uint64_t>(), n, s) : 0;
 }
@@ -86,8 +91,8 @@ struct JoinSides {
     int64_t nr = 0, ns = 0, out_j = 0;
 };
 
-static void join_sides(const PlanInput& in, JoinSides& j, cudaStream_t s) {
-    j.nr = sorted_tuples(in.r_key, in.r_val, in.nr, j.rk, s);
+static void join_sides(const PlanInput& in, JoinSides& j, cudaStream_t s, bool r_bag = false) {
+    j.nr = sorted_tuples(in.r_key, in.r_val, in.nr, j.rk, s, r_bag);
     j.ns = sorted_tuples(in.s_key, in.s_val, in.ns, j.sk, s);
     DevBuf cnt;
     j.lo.alloc((size_t)std::max<int64_t>(j.nr, 1) * 8, s);
@@ -168,20 +173,40 @@ int64_t classical_join(const Ctx& ctx, const PlanInput& in, int kind, int32_t* o
     return n_out;
 }
 
-int64_t bag_join(const Ctx& ctx, const PlanInput& in, int32_t* out_x, int32_t* out_z, int64_t capacity,
-                 int64_t* count, cudaStream_t s) {
+__global__ void k_unpack_pairs(const uint64_t* __restrict__ k, int64_t n, int32_t* a, int32_t* b) {
+    GRID_STRIDE(i, n) {
+        a[i] = unflip((uint32_t)(k[i] >> 32));
+        b[i] = unflip((uint32_t)k[i]);
+    }
+}
+
+int64_t distinct_pairs(const int32_t* a, const int32_t* b, int64_t n, int32_t* out_a, int32_t* out_b,
+                       int64_t capacity, int64_t* count, cudaStream_t s) {
+    DevBuf keys;
+    const int64_t m = sorted_tuples(a, b, n, keys, s);  // keyed (a, b): canonical order
+    if (count) *count = m;
+    if (m > capacity)
+        throw Error(DIM3_ERR_CAPACITY, "output capacity " + std::to_string(capacity) + " < result size " +
+                                           std::to_string(m));
+    if (m > 0) {
+        DIM3_REQUIRE(out_a && out_b, DIM3_ERR_ARG, "null output buffer");
+        k_unpack_pairs<<<grid_for(m), kThreads, 0, s>>>(keys.as<uint64_t>(), m, out_a, out_b);
+        DIM3_LAUNCHED();
+    }
+    DIM3_CUDA(cudaStreamSynchronize(s));
+    return m;
+}
+
+int64_t bag_join_into(const Ctx& ctx, const PlanInput& in, DevBuf& out_x, DevBuf& out_z, cudaStream_t s) {
     PhaseScope phase(ctx.stats, PH_EMIT, s);
     JoinSides j;
-    join_sides(in, j, s);
-    if (count) *count = j.out_j;
-    if (j.out_j > capacity)
-        throw Error(DIM3_ERR_CAPACITY, "output capacity " + std::to_string(capacity) + " < result size " +
-                                           std::to_string(j.out_j));
+    join_sides(in, j, s, true);
+    out_x.alloc((size_t)std::max<int64_t>(j.out_j, 1) * 4, s);
+    out_z.alloc((size_t)std::max<int64_t>(j.out_j, 1) * 4, s);
     if (j.out_j > 0) {
-        DIM3_REQUIRE(out_x && out_z, DIM3_ERR_ARG, "null output buffer");
         k_join_emit<<<warp_grid(j.nr), kThreads, 0, s>>>(j.rk.as<uint64_t>(), j.nr, j.sk.as<uint64_t>(),
-                                                          j.lo.as<int64_t>(), j.off.as<int64_t>(), nullptr, out_x,
-                                                          out_z);
+                                                          j.lo.as<int64_t>(), j.off.as<int64_t>(), nullptr,
+                                                          out_x.as<int32_t>(), out_z.as<int32_t>());
         DIM3_LAUNCHED();
     }
     DIM3_CUDA(cudaStreamSynchronize(s));

@@ -234,13 +234,24 @@ int64_t groupby_aggregate(const Ctx& ctx, const PlanInput& in, int agg, int32_t*
                           int64_t capacity, int64_t* count, cudaStream_t s);
 
 // The classical solution (classical.cu): distinct tuples sorted by y, join by
-// binary search, dedup by radix sort (kind 0 project, 1 count); the bag join
-// without dedup; f1 of Section 2.6 (> 0: classical).
+// binary search, dedup by radix sort (kind 0 project, 1 count); f1 of Section
+// 2.6 (> 0: classical).
 int64_t classical_join(const Ctx& ctx, const PlanInput& in, int kind, int32_t* out_x, int32_t* out_z,
                        int32_t* out_cnt, int64_t capacity, int64_t* count, cudaStream_t s);
-int64_t bag_join(const Ctx& ctx, const PlanInput& in, int32_t* out_x, int32_t* out_z, int64_t capacity,
-                 int64_t* count, cudaStream_t s);
 double f1_value(int64_t nr, int64_t ns, int64_t out_j, const double* c);
+// the bag join (R's rows all kept, S distinct, results not deduplicated) into
+// buffers it allocates; returns the number of pairs
+int64_t bag_join_into(const Ctx& ctx, const PlanInput& in, DevBuf& out_x, DevBuf& out_z, cudaStream_t s);
+// the distinct (a, b) pairs of two columns, canonical order
+int64_t distinct_pairs(const int32_t* a, const int32_t* b, int64_t n, int32_t* out_a, int32_t* out_b,
+                       int64_t capacity, int64_t* count, cudaStream_t s);
+
+// Multi-way joins with projection (mjp.cu), Section 4.2: the deduplication-
+// placement DP (host), exact chain sizes, and the execution of a placement.
+double mjp_dp(int k, const double* r_size, const double* out_j, const double* out_p, const double* c, int* dedup);
+void mjp_sizes(const Ctx& ctx, int k, const dim3_edge_table* t, double* out_j, double* out_p, cudaStream_t s);
+int64_t mjp_execute(const Ctx& ctx, int k, const dim3_edge_table* t, const int* dedup, int32_t* out_x,
+                    int32_t* out_z, int64_t capacity, int64_t* count, cudaStream_t s);
 
 // Value mapping with all scratch in a fixed device array (noalloc.cu).
 void map_noalloc(const int32_t* d_vals, int64_t n, int32_t* d_ids, int32_t* d_dict, int64_t* n_distinct,

@@ -59,6 +59,11 @@ class PlanInfo(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class EdgeTable(ctypes.Structure):
+    """dim3_edge_table: one relation R_i(x_i, x_{i+1}) of a multi-way join."""
+    _fields_ = [("d_a", ctypes.c_void_p), ("d_b", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
 class CacheInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_entries", "n_list", "space", "n_x")]
 
@@ -114,6 +119,9 @@ def load(build_if_missing: bool = True):
                                      ctypes.POINTER(I64), P], INT),
             "dim3_groupby_aggregate": ([P, P, P, I64, P, P, I64, ctypes.c_int, P, P, I64, ctypes.POINTER(I64), P],
                                        INT),
+            "dim3_mjp_sizes": ([P, ctypes.c_int, P, P, P, P], INT),
+            "dim3_mjp_plan": ([ctypes.c_int, P, P, P, P, P, P], INT),
+            "dim3_mjp_execute": ([P, ctypes.c_int, P, P, P, P, I64, ctypes.POINTER(I64), P], INT),
             "dim3_cache_build": ([P, P, P, I64, P, P, I64, I32, I64, ctypes.c_double, ctypes.c_double,
                                   ctypes.POINTER(P), ctypes.POINTER(CacheInfo), P], INT),
             "dim3_cache_export": ([P, P, P, P, P, P, P, P], INT),
@@ -314,6 +322,62 @@ class Context:
         if m:
             _check(self._lib.dim3_groupby_aggregate(*args, _ptr(x), _ptr(v), m, ctypes.byref(n), st))
         return x, v
+
+    # ------------------------------------------------------------------ MJP
+    # Section 4.2 cost constants (seconds): bag join per input row and per
+    # result pair, Join-Project per input row, per join tuple, per result pair
+    MJP_COSTS = (3.0e-10, 4.0e-11, 4.0e-10, 1.0e-12, 1.5e-12)
+
+    def _edges(self, tables):
+        cols = []
+        arr = (EdgeTable * len(tables))()
+        for i, (a, b) in enumerate(tables):
+            a, b = _col(a, self.device, f"R{i + 1}.a"), _col(b, self.device, f"R{i + 1}.b")
+            if a.numel() != b.numel():
+                raise ValueError(f"table {i + 1}: column lengths differ")
+            cols.append((a, b))
+            arr[i] = EdgeTable(a.data_ptr() if a.numel() else None, b.data_ptr() if b.numel() else None, a.numel())
+        return arr, cols
+
+    def mjp_sizes(self, tables, stream=None):
+        """Exact |OUT_J_i| and |OUT_P_i| of the line query (``dim3_mjp_sizes``)."""
+        arr, _keep = self._edges(tables)
+        k = len(tables)
+        oj, op = (ctypes.c_double * k)(), (ctypes.c_double * k)()
+        _check(self._lib.dim3_mjp_sizes(self._h, k, arr, oj, op, _stream(self.device, stream)))
+        return list(oj), list(op)
+
+    @staticmethod
+    def mjp_plan(r_size, out_j, out_p, costs=MJP_COSTS):
+        """Deduplication placement of Section 4.2's DP (``dim3_mjp_plan``):
+        (dedup flags, estimated cost)."""
+        k = len(r_size)
+        D = ctypes.c_double * k
+        dedup = (ctypes.c_int * k)()
+        cost = ctypes.c_double()
+        _check(load().dim3_mjp_plan(k, D(*r_size), D(*out_j), D(*out_p), (ctypes.c_double * 5)(*costs), dedup,
+                                    ctypes.byref(cost)))
+        return [bool(v) for v in dedup], cost.value
+
+    def mjp_execute(self, tables, dedup, out=None, stream=None):
+        """Run a placement of the line query (``dim3_mjp_execute``): (x_1, x_{k+1})."""
+        arr, _keep = self._edges(tables)
+        k = len(tables)
+        flags = (ctypes.c_int * k)(*[int(bool(v)) for v in dedup])
+        st = _stream(self.device, stream)
+        n = ctypes.c_int64()
+        if out is None:
+            rc = self._lib.dim3_mjp_execute(self._h, k, arr, flags, None, None, 0, ctypes.byref(n), st)
+            if rc not in (DIM3_OK, DIM3_ERR_CAPACITY):
+                _check(rc)
+            out = (torch.empty(n.value, dtype=torch.int32, device=self.device),
+                   torch.empty(n.value, dtype=torch.int32, device=self.device))
+            if n.value == 0:
+                return out
+        x, z = out
+        _check(self._lib.dim3_mjp_execute(self._h, k, arr, flags, _ptr(x), _ptr(z), min(x.numel(), z.numel()),
+                                          ctypes.byref(n), st))
+        return x[: n.value], z[: n.value]
 
     # Section 3 cost constants measured on GB300 (seconds): one SparseBMM join
     # tuple, one DenseEC (x, z) evaluation

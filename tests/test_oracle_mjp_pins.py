@@ -19,7 +19,7 @@ import oracle.mjp as om
 
 def rand_tables(seed, k, n=12, span=5):
     rng = np.random.default_rng(seed)
-    return [(rng.integers(0, span, n), rng.integers(0, span, n)) for _ in range(k)]
+    return [(rng.integers(-span, span, n), rng.integers(-span, span, n)) for _ in range(k)]
 
 
 def brute_paths(tables):
