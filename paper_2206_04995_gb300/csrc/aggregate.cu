@@ -26,7 +26,14 @@
 
 namespace dimcube {
 
-constexpr int kAggTile = 2048;  // z per SPA tile: 2 x 16 KiB of int64 accumulators (static shared memory)
+// z per SPA tile: 2048 (16 KiB of int64, 32 KiB for AVG's pairs; six CTAs
+// per SM) for ranges up to 2^18 z, else 8192 (fewer tiles per row on a wide
+// range, empty ones skipped)
+constexpr int kAggTile = 2048;
+constexpr int kAggTileWide = 8192;
+constexpr int64_t kAggWideZ = int64_t(1) << 18;
+constexpr int kAggLight = 512;            // join tuples of a light row (sorted in shared memory)
+constexpr int kAggLightWarps = 4;         // light rows: warps per CTA
 
 static unsigned grid_for(int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kThreads), 152 * 16));
@@ -167,6 +174,7 @@ struct AggArgs {
     const int32_t* dict_x;
     const int32_t* dict_z;
     const int64_t* off;
+    const uint8_t* light;  // per x: handled by the light-row kernel (or null)
     int agg, fn;
     int32_t* out_x;
     int32_t* out_z;
@@ -201,77 +209,210 @@ __device__ __forceinline__ int64_t contrib_ext(int fn, bool want_min, int64_t rm
     }
 }
 
+// the contribution of one join path group (R entry q, S entry j) to its z
+struct Contribution {
+    int64_t v;   // SUM / COUNT / AVG sum part, or the MIN / MAX extreme
+    int64_t c;   // AVG: count part
+};
+
+__device__ __forceinline__ Contribution contribution(const AggArgs& a, int64_t q, int64_t j) {
+    Contribution r{0, 0};
+    const int64_t cr = a.rc[q];
+    if (a.agg == DIM3_AGG_COUNT) {
+        r.v = mul_wrap(cr, a.sc[j]);
+    } else if (a.agg == DIM3_AGG_SUM || a.agg == DIM3_AGG_AVG) {
+        r.v = contrib_sum(a.fn, cr, a.rs[q], a.sc[j], a.su[j]);
+        r.c = mul_wrap(cr, a.sc[j]);
+    } else {
+        r.v = contrib_ext(a.fn, a.agg == DIM3_AGG_MIN, a.rmn[q], a.rmx[q], a.smn[j], a.smx[j]);
+    }
+    return r;
+}
+
+__device__ __forceinline__ void combine_smem(int agg, int64_t* acc, int64_t* acc2, int i, const Contribution& c) {
+    if (agg == DIM3_AGG_MIN) {
+        atomicMin(reinterpret_cast<long long*>(acc + i), (long long)c.v);
+    } else if (agg == DIM3_AGG_MAX) {
+        atomicMax(reinterpret_cast<long long*>(acc + i), (long long)c.v);
+    } else {
+        atomicAdd(reinterpret_cast<unsigned long long*>(acc + i), (unsigned long long)c.v);
+        if (agg == DIM3_AGG_AVG) atomicAdd(reinterpret_cast<unsigned long long*>(acc2 + i), (unsigned long long)c.c);
+    }
+}
+
+// Heavy rows: one CTA per x, an SPA of kAggTile z per pass (dynamic shared
+// memory: accumulators, AVG counts, presence bits). Rows flagged light skip.
+// Emission: a scan of the tile's presence words gives every word its output
+// position; each warp then writes its words lane by bit, so a dense word
+// becomes 32 consecutive outputs.
+template <bool kWide>
 __global__ void __launch_bounds__(kThreads) k_xrow_agg(const AggArgs a) {
-    __shared__ int64_t acc[kAggTile];
-    __shared__ int64_t acc2[kAggTile];  // AVG: count
-    __shared__ uint32_t pres[kAggTile / 32];
+    constexpr int tile = kWide ? kAggTileWide : kAggTile;
+    extern __shared__ __align__(16) int64_t agg_smem[];
+    int64_t* acc = agg_smem;
+    int64_t* acc2 = acc + tile;  // AVG only
+    uint32_t* pres = reinterpret_cast<uint32_t*>(acc + (a.agg == DIM3_AGG_AVG ? 2 * tile : tile));
     __shared__ int64_t s_warp[kThreads / 32 + 1];
+    __shared__ int32_t s_pre[tile / 32 + 1];
     const int64_t x = blockIdx.x;
+    if (a.light && a.light[x]) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
     const int64_t init = a.agg == DIM3_AGG_MIN ? INT64_MAX : (a.agg == DIM3_AGG_MAX ? INT64_MIN : 0);
     int64_t out_pos = a.off[x];
     const int32_t xv = a.dict_x[x];
-    for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += kAggTile) {
-        const int64_t zt1 = min64(zt0 + kAggTile, a.n_z);
+    for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += tile) {
+        const int64_t zt1 = min64(zt0 + (int64_t)tile, a.n_z);
         const int tz = (int)(zt1 - zt0);
+        const bool part = zt0 > 0 || zt1 < a.n_z;
+        if (kWide && part) {  // skip a tile none of the row's S rows reaches
+            int any = 0;
+            if (lane == 0) {
+                for (int64_t q = r0 + warp; q < r1 && !any; q += kThreads / 32) {
+                    const int32_t y = a.r_col[q];
+                    const int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+                    const int64_t b0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
+                    any = b0 < s1 && a.ss_col[b0] < zt1;
+                }
+            }
+            if (!__syncthreads_or(any)) continue;
+        }
         for (int i = tid; i < tz; i += kThreads) {
             acc[i] = init;
-            acc2[i] = 0;
+            if (a.agg == DIM3_AGG_AVG) acc2[i] = 0;
         }
-        for (int i = tid; i < kAggTile / 32; i += kThreads) pres[i] = 0u;
+        for (int i = tid; i < (tz + 31) / 32; i += kThreads) pres[i] = 0u;
         __syncthreads();
         // one warp per distinct (x, y) of R_CSR; lanes walk S_sparse row y
         for (int64_t q = r0 + warp; q < r1; q += kThreads / 32) {
             const int32_t y = a.r_col[q];
-            const int64_t cr = a.rc[q], sr = a.rs[q];
-            const int64_t rmn = a.rmn[q], rmx = a.rmx[q];
             int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
-            if (zt0 > 0 || zt1 < a.n_z) {
+            if (part) {
                 s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
                 s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
             }
             for (int64_t j = s0 + lane; j < s1; j += 32) {
                 const int z = a.ss_col[j] - (int)zt0;
                 atomicOr(&pres[z >> 5], 1u << (z & 31));
-                if (a.agg == DIM3_AGG_COUNT) {
-                    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[z]), (unsigned long long)mul_wrap(cr, a.sc[j]));
-                } else if (a.agg == DIM3_AGG_SUM || a.agg == DIM3_AGG_AVG) {
-                    atomicAdd(reinterpret_cast<unsigned long long*>(&acc[z]),
-                              (unsigned long long)contrib_sum(a.fn, cr, sr, a.sc[j], a.su[j]));
-                    if (a.agg == DIM3_AGG_AVG)
-                        atomicAdd(reinterpret_cast<unsigned long long*>(&acc2[z]),
-                                  (unsigned long long)mul_wrap(cr, a.sc[j]));
-                } else {
-                    const bool mn = a.agg == DIM3_AGG_MIN;
-                    const int64_t c = contrib_ext(a.fn, mn, rmn, rmx, a.smn[j], a.smx[j]);
-                    if (mn) atomicMin(reinterpret_cast<long long*>(&acc[z]), (long long)c);
-                    else atomicMax(reinterpret_cast<long long*>(&acc[z]), (long long)c);
-                }
+                combine_smem(a.agg, acc, acc2, z, contribution(a, q, j));
             }
         }
         __syncthreads();
         // emit the groups of this tile in z order
-        const int nw = (tz + 31) >> 5;
-        for (int w0 = 0; w0 < nw; w0 += kThreads) {
-            const int w = w0 + tid;
-            uint32_t bits = w < nw ? pres[w] : 0u;
+        const int nw = (tz + 31) >> 5;  // <= kThreads
+        {
+            const uint32_t bits = tid < nw ? pres[tid] : 0u;
             int64_t total;
             const int64_t pre = block_exclusive_scan<int64_t, kThreads>(__popc(bits), &total, s_warp);
-            int64_t o = out_pos + pre;
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int zi = (w << 5) + b;
+            if (tid < nw) s_pre[tid] = (int32_t)pre;
+            __syncthreads();
+            const unsigned lt = lanemask_lt();
+            for (int w = warp; w < nw; w += kThreads / 32) {
+                const uint32_t word = pres[w];
+                if (!((word >> lane) & 1u)) continue;
+                const int64_t o = out_pos + s_pre[w] + __popc(word & lt);
+                const int zi = (w << 5) + lane;
                 a.out_x[o] = xv;
                 a.out_z[o] = a.dict_z[zt0 + zi];
                 if (a.agg == DIM3_AGG_AVG) a.out_f[o] = (double)acc[zi] / (double)acc2[zi];
                 else a.out_i[o] = acc[zi];
-                ++o;
             }
             out_pos += total;
         }
         __syncthreads();
+    }
+}
+
+// Light rows (at most kAggLight join tuples): one warp per x gathers its
+// tuples as (z id, tuple number) keys, sorts them (bitonic), numbers the
+// distinct z and accumulates every tuple's contribution at its z's number.
+constexpr int kAggLightWarpBytes = kAggLight * (8 + 8 + 8 + 4 + 4 + 4);  // key, acc, acc2, q, j, rank
+
+__global__ void __launch_bounds__(kAggLightWarps * 32) k_light_agg(const AggArgs a, const int32_t* rows, int64_t n) {
+    extern __shared__ __align__(16) uint64_t light_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* key = light_smem + (size_t)warp * (kAggLightWarpBytes / 8);
+    int64_t* acc = reinterpret_cast<int64_t*>(key + kAggLight);
+    int64_t* acc2 = acc + kAggLight;
+    int32_t* tq = reinterpret_cast<int32_t*>(acc2 + kAggLight);
+    int32_t* tj = tq + kAggLight;
+    int32_t* rank = tj + kAggLight;
+    const unsigned lt = lanemask_lt();
+    const int64_t init = a.agg == DIM3_AGG_MIN ? INT64_MAX : (a.agg == DIM3_AGG_MAX ? INT64_MIN : 0);
+    for (int64_t i = blockIdx.x * (int64_t)kAggLightWarps + warp; i < n; i += (int64_t)gridDim.x * kAggLightWarps) {
+        const int64_t x = rows[i];
+        int m = 0;
+        for (int64_t q = a.r_rowptr[x]; q < a.r_rowptr[x + 1]; ++q) {
+            const int32_t y = a.r_col[q];
+            const int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+            for (int64_t j = s0 + lane; j < s1; j += 32) {
+                const int t = m + (int)(j - s0);
+                key[t] = ((uint64_t)(uint32_t)a.ss_col[j] << 32) | (uint32_t)t;
+                tq[t] = (int32_t)q;
+                tj[t] = (int32_t)j;
+            }
+            m += (int)(s1 - s0);
+        }
+        int pw = 1;
+        while (pw < m) pw <<= 1;
+        for (int t = m + lane; t < pw; t += 32) key[t] = ~0ull;
+        __syncwarp();
+        for (int k = 2; k <= pw; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = lane; t < (pw >> 1); t += 32) {
+                    const int lo = (t / j) * 2 * j + (t % j), hi = lo + j;
+                    const uint64_t u = key[lo], v = key[hi];
+                    if ((u > v) == ((lo & k) == 0)) {
+                        key[lo] = v;
+                        key[hi] = u;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // number the distinct z (run starts 0, 1, ...; every element takes
+        // its run's number by a running max), initialise their accumulators
+        int groups = 0, carry = -1;
+        for (int base = 0; base < m; base += 32) {
+            const int t = base + lane;
+            const bool first = t < m && (t == 0 || (key[t - 1] >> 32) != (key[t] >> 32));
+            const unsigned bal = __ballot_sync(kFull, first);
+            const int g = groups + __popc(bal & lt);
+            if (first) {
+                acc[g] = init;
+                acc2[g] = 0;
+            }
+            int r = first ? g : -1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(kFull, r, o);
+                if (lane >= o) r = max(r, u);
+            }
+            r = max(r, carry);
+            if (t < m) rank[t] = r;
+            carry = __shfl_sync(kFull, r, 31);
+            groups += __popc(bal);
+        }
+        __syncwarp();
+        for (int t = lane; t < m; t += 32) {
+            const int src = (int)(uint32_t)key[t];
+            combine_smem(a.agg, acc, acc2, rank[t], contribution(a, tq[src], tj[src]));
+        }
+        __syncwarp();
+        const int64_t o = a.off[x];
+        const int32_t xv = a.dict_x[x];
+        for (int base = 0; base < m; base += 32) {
+            const int t = base + lane;
+            const bool first = t < m && (t == 0 || (key[t - 1] >> 32) != (key[t] >> 32));
+            if (first) {
+                const int g = rank[t];
+                a.out_x[o + g] = xv;
+                a.out_z[o + g] = a.dict_z[(int64_t)(key[t] >> 32)];
+                if (a.agg == DIM3_AGG_AVG) a.out_f[o + g] = (double)acc[g] / (double)acc2[g];
+                else a.out_i[o + g] = acc[g];
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -353,6 +494,33 @@ static void row_ids(const Plan& p, const PlanInput& in, DevBuf& ry, DevBuf& rx, 
     }
 }
 
+__global__ void k_light_agg_flags(const int64_t* __restrict__ outj_x, int64_t n_x, uint8_t* light, int32_t* flag) {
+    GRID_STRIDE(x, n_x) {
+        const bool l = outj_x[x] <= kAggLight;
+        light[x] = l ? 1 : 0;
+        flag[x] = l ? 1 : 0;
+    }
+}
+
+__global__ void k_light_agg_list(const int32_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t n,
+                                 int32_t* rows) {
+    GRID_STRIDE(x, n) {
+        if (flag[x]) rows[pos[x]] = (int32_t)x;
+    }
+}
+
+static void set_agg_attrs(const Ctx& ctx) {
+    static bool done[64] = {false};
+    bool& d = done[ctx.device & 63];
+    if (d) return;
+    const int heavy = kAggTileWide * 16 + (kAggTileWide / 32) * 4;
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_agg<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, heavy));
+    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_agg<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, heavy));
+    DIM3_CUDA(cudaFuncSetAttribute(k_light_agg, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kAggLightWarps * kAggLightWarpBytes));
+    d = true;
+}
+
 int64_t join_aggregate(const Ctx& ctx, const PlanInput& in, const int32_t* r_v, const int32_t* s_u, int agg, int fn,
                        int32_t* out_x, int32_t* out_z, void* out_val, int64_t capacity, int64_t* count,
                        cudaStream_t s) {
@@ -406,8 +574,38 @@ int64_t join_aggregate(const Ctx& ctx, const PlanInput& in, const int32_t* r_v, 
     a.out_z = out_z;
     a.out_i = agg == DIM3_AGG_AVG ? nullptr : static_cast<int64_t*>(out_val);
     a.out_f = agg == DIM3_AGG_AVG ? static_cast<double*>(out_val) : nullptr;
-    k_xrow_agg<<<(unsigned)n_x, kThreads, 0, s>>>(a);
+    // light rows: at most kAggLight join tuples (outj_x counts them exactly:
+    // every z is on the list path)
+    DevBuf light, lflag, lpos, lrows;
+    light.alloc((size_t)n_x, s);
+    lflag.alloc((size_t)n_x * 4, s);
+    lpos.alloc((size_t)(n_x + 1) * 8, s);
+    k_light_agg_flags<<<grid_for(n_x), kThreads, 0, s>>>(p->outj_x.as<int64_t>(), n_x, light.as<uint8_t>(),
+                                                          lflag.as<int32_t>());
     DIM3_LAUNCHED();
+    exclusive_scan_i32_to_i64(lflag.as<int32_t>(), lpos.as<int64_t>(), n_x, s);
+    const int64_t n_light = read_i64(lpos.as<int64_t>() + n_x, s);
+    a.light = n_light > 0 ? light.as<uint8_t>() : nullptr;
+    set_agg_attrs(ctx);
+    const bool wide = a.n_z >= kAggWideZ;
+    const int tile = wide ? kAggTileWide : kAggTile;
+    const size_t smem = (size_t)tile * (agg == DIM3_AGG_AVG ? 16 : 8) + (size_t)(tile / 32) * 4;
+    if (n_light < n_x) {
+        if (wide) k_xrow_agg<true><<<(unsigned)n_x, kThreads, smem, s>>>(a);
+        else k_xrow_agg<false><<<(unsigned)n_x, kThreads, smem, s>>>(a);
+        DIM3_LAUNCHED();
+    }
+    if (n_light > 0) {
+        lrows.alloc((size_t)n_light * 4, s);
+        k_light_agg_list<<<grid_for(n_x), kThreads, 0, s>>>(lflag.as<int32_t>(), lpos.as<int64_t>(), n_x,
+                                                             lrows.as<int32_t>());
+        DIM3_LAUNCHED();
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_light, kAggLightWarps),
+                                                                            152 * 32));
+        k_light_agg<<<g, kAggLightWarps * 32, (size_t)kAggLightWarps * kAggLightWarpBytes, s>>>(a, lrows.as<int32_t>(),
+                                                                                            n_light);
+        DIM3_LAUNCHED();
+    }
     DIM3_CUDA(cudaStreamSynchronize(s));
     return total;
 }
