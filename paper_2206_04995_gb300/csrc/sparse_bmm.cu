@@ -516,13 +516,15 @@ __global__ void __launch_bounds__(kThreads, kEmit ? 4 : 8) k_xrow_bits(const XRo
 // Emitting pass for G consecutive x rows per CTA. The rows' SPA bitmaps are
 // built together (their R_CSR rows are adjacent, so one flattened entry list
 // feeds the warps), and each 1024-entry slice of the z dictionary is loaded
-// once into registers (lane l holds entries 32 j + l) and used for all G rows,
-// which divides the dictionary's L2 traffic and the block barriers per row by G.
+// into registers half a slice at a time (lane l holds entries 32 j + l of 16
+// words j) and used for all G rows, which divides the dictionary's L2 traffic
+// and the block barriers per row by G; a half (at most 512 pairs) is staged
+// and flushed, so the per-warp stage is 528 entries.
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
-    int32_t* stage = reinterpret_cast<int32_t*>(smem);  // kWarps x kWarpStage
-    uint32_t* bm_all = smem + kWarps * kWarpStage;      // G bitmaps of tile_words words
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);  // kWarps x kWarpStageIds
+    uint32_t* bm_all = smem + kWarps * kWarpStageIds;   // G bitmaps of tile_words words
     __shared__ int32_t s_list[kThreads];
     __shared__ int32_t s_lk[kThreads];
     __shared__ int32_t s_ny[kThreads];
@@ -784,7 +786,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
             wpos[k] = (k < ng ? out_pos[k] : 0) + before;
             if (k < ng) out_pos[k] += all;
         }
-        int32_t* st = stage + warp * kWarpStage;
+        int32_t* st = stage + warp * kWarpStageIds;
         const int64_t zlim = a.n_z - zt0;
         for (int g = g0; write && g < g1; ++g) {
             const int w = (g << 5) + lane;
@@ -796,47 +798,65 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
                 any |= word[k] != 0u;
             }
             if (!__any_sync(kFull, any)) continue;
-            int32_t dreg[32];
-            bool loaded = false;  // warp-uniform
             const int64_t gb = (int64_t)g << 10;
             const int32_t* dz = a.dict_z + zt0 + gb;
+            int excl[G], total[G], half0[G];
+            bool dense = false;
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 const int c = __popc(word[k]);
                 const int incl = warp_inclusive_scan(c);
-                const int total_g = __shfl_sync(kFull, incl, 31);
-                if (total_g == 0) continue;
-                const int excl = incl - c;
-                const int sh = (int)(wpos[k] & 3);
-                if (total_g <= 64) {
+                total[k] = __shfl_sync(kFull, incl, 31);
+                half0[k] = __shfl_sync(kFull, incl, 15);
+                excl[k] = incl - c;
+                if (total[k] > 64) {
+                    dense = true;
+                } else if (total[k] > 0) {
                     // few bits: each lane writes its own word's bits
-                    int pos = sh + excl;
+                    const int sh = (int)(wpos[k] & 3);
+                    int pos = sh + excl[k];
                     uint32_t wv = word[k];
                     while (wv) {
                         const int b = __ffs(wv) - 1;
                         wv &= wv - 1;
                         st[pos++] = __ldg(dz + (lane << 5) + b);
                     }
-                } else {
-                    if (!loaded) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int64_t idx = gb + (j << 5) + lane;
-                            dreg[j] = idx < zlim ? __ldg(a.dict_z + zt0 + idx) : 0;
-                        }
-                        loaded = true;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const uint32_t wj = __shfl_sync(kFull, word[k], j);
-                        const int pj = __shfl_sync(kFull, excl, j);
-                        if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = dreg[j];
-                    }
+                    __syncwarp();
+                    flush_warp(a.out_z + (wpos[k] - sh), st, sh, total[k], a.vec_ok);
+                    __syncwarp();
+                    wpos[k] += total[k];
                 }
-                __syncwarp();
-                flush_warp(a.out_z + (wpos[k] - sh), st, sh, total_g, a.vec_ok);
-                __syncwarp();
-                wpos[k] += total_g;
+            }
+            if (!dense) continue;
+            // dense rows: the group's dictionary slice is read once per half
+            // (lane l holds entry 32 j + l of the 16 words j) and shared by
+            // the rows; each half (at most 512 pairs) is staged and flushed
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int32_t dreg[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int64_t idx = gb + ((16 * h + i) << 5) + lane;
+                    dreg[i] = idx < zlim ? __ldg(a.dict_z + zt0 + idx) : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    if (total[k] <= 64) continue;
+                    const int base = h ? half0[k] : 0;
+                    const int cnt = h ? total[k] - half0[k] : half0[k];
+                    if (cnt == 0) continue;
+                    const int sh = (int)(wpos[k] & 3);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const uint32_t wj = __shfl_sync(kFull, word[k], 16 * h + i);
+                        const int pj = __shfl_sync(kFull, excl[k], 16 * h + i) - base;
+                        if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = dreg[i];
+                    }
+                    __syncwarp();
+                    flush_warp(a.out_z + (wpos[k] - sh), st, sh, cnt, a.vec_ok);
+                    __syncwarp();
+                    wpos[k] += cnt;
+                }
             }
         }
         __syncthreads();
@@ -1019,11 +1039,13 @@ static XRowArgs make_args(const Plan& p, int64_t x_begin, int64_t rows, int kind
 
 // x rows per CTA of the emitting pass: the option if set (1, 2 or 4), else 2
 // when the two bitmaps keep the CTA under 112 KiB of shared memory, else 1.
-// (Measured on the 1M x 1M Zipf workload: 1 row 8.8 ms, 2 rows 7.6 ms,
-// 4 rows 8.1 ms; four rows need 100 registers and fit only two CTAs per SM.)
+// (Measured on the 1M x 1M Zipf workload with the half-group dictionary: one
+// pass 2 rows 7.82 ms, 4 rows 8.20 ms; two rows take 64 registers and 43 KiB,
+// four CTAs per SM. Capping them at 48 registers for a fifth CTA made the
+// kernel 12.98 ms.)
 static int emit_rows_per_cta(const Ctx& ctx, int64_t tile_bits) {
     const int64_t want = ctx.opt.emit_rows;
-    const int64_t stage = (int64_t)kWarps * kWarpStage * 4, bm = (tile_bits / 32) * 4;
+    const int64_t stage = (int64_t)kWarps * kWarpStageIds * 4, bm = (tile_bits / 32) * 4;
     const int64_t cap = (int64_t)ctx.smem_optin - 4096;
     auto fits = [&](int64_t g, int64_t lim) { return stage + g * bm <= lim; };
     if (want == 1 || want == 2 || want == 4) return fits(want, cap) ? (int)want : 1;
@@ -1246,7 +1268,7 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
         // several rows per CTA share one z window, so batches use one row per CTA
         const int grp = (emit && a.x_tag == nullptr && !a.light) ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
         if (emit && grp > 1) {
-            const size_t smg = (size_t)kWarps * kWarpStage * 4 + (size_t)grp * (size_t)(a.tile_bits / 32) * 4;
+            const size_t smg = (size_t)kWarps * kWarpStageIds * 4 + (size_t)grp * (size_t)(a.tile_bits / 32) * 4;
             const unsigned gg = (unsigned)ceil_div(a.n_rows, grp);
             static int cur2[64] = {0}, cur4[64] = {0};
             int* cur = (grp == 2 ? cur2 : cur4) + (ctx.device & 63);
