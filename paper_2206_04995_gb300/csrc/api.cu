@@ -80,6 +80,7 @@ template <class F>
 int guarded(F&& f) {
     try {
         f();
+        dimcube::raise_if_wait_fault();
         g_last_error.clear();
         return DIM3_OK;
     } catch (const dimcube::Error& e) {

@@ -96,8 +96,16 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
 void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s);
 int64_t read_i64(const int64_t* d, cudaStream_t s);  // synchronising read of one device value
+// A bounded device wait that gives up stores 1 to this process-wide flag
+// (pinned, mapped host memory); raise_if_wait_fault(), called after
+// synchronisations (read_i64, the end of every C-ABI call), turns it into
+// DIM3_ERR_TIMEOUT once and clears it.
+int* wait_fault_flag();
+void raise_if_wait_fault();
 // LSD radix sort of n keys (32- or 64-bit) on their low `bits` bits, with an
 // optional uint32 payload. Results end in keys/vals (the alt buffers are scratch).
+// Stable; one-sweep passes (a tile that waits on its predecessors for more than
+// 2 s gives up and sets the wait-fault flag).
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                     int64_t n, int bits, cudaStream_t s);
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,

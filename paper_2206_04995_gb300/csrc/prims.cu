@@ -2,6 +2,7 @@
 // pointers. They carry no Join-Project arithmetic; the mapping and partition
 // steps are built from them.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "device.cuh"
@@ -104,121 +105,232 @@ int64_t read_i64(const int64_t* d, cudaStream_t s) {
     int64_t h = 0;
     DIM3_CUDA(cudaMemcpyAsync(&h, d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DIM3_CUDA(cudaStreamSynchronize(s));
+    raise_if_wait_fault();
     return h;
 }
 
 // ------------------------------------------------------------ radix sort
-// LSD radix sort, 8-bit digits. Per pass: a per-tile digit histogram, an
-// exclusive scan of the digit-major histogram table (global digit offsets per
-// tile), and a stable scatter. Ranks inside a tile come from warp-level
-// __match_any_sync groups and per-warp digit counters in shared memory, so the
-// scatter is stable (element order: tile, warp, chunk, lane).
+// LSD radix sort with 8-bit digits in the one-sweep form (Adinets and Merrill,
+// "Onesweep: A Faster Least Significant Digit Radix Sort for GPUs", 2022): one
+// kernel counts the digits of every pass at once; then each pass is ONE kernel
+// whose tiles (taken in dispatch order from a ticket) rank their keys, publish
+// their per-digit counts, find the counts of the tiles before them by
+// decoupled look-back (one thread per digit), reorder the tile by digit in
+// shared memory and write each digit's run contiguously. Ranks inside a tile
+// come from __match_any_sync groups and per-warp digit counters, so every pass
+// is stable (element order: tile, warp, chunk, lane).
 constexpr int kRadixIpt = 16;
 constexpr int kRadixTile = kThreads * kRadixIpt;
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxPasses = 8;
+constexpr uint64_t kSortWaitNs = 2000000000ull;  // give up on a predecessor tile after 2 s
 
-template <typename K>
-__global__ void __launch_bounds__(kThreads) k_radix_hist(const K* keys, int64_t n, int shift,
-                                                         int32_t* hist, int64_t nb) {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-    for (int i = threadIdx.x; i < kRadixTile; i += kThreads) {
-        int64_t idx = base + i;
-        bool valid = idx < n;
-        unsigned d = valid ? (unsigned)((keys[idx] >> shift) & 255u) : 256u;
-        unsigned peers = __match_any_sync(kFull, d);
-        if (valid && (int)lane_id() == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = (int32_t)h[threadIdx.x];
+namespace {
+std::once_flag g_fault_once;
+int* g_fault_host = nullptr;  // pinned, mapped: device stores are read by the host after a sync
+int* g_fault_dev = nullptr;   // the device's address of the same word
+}  // namespace
+
+int* wait_fault_flag() {
+    std::call_once(g_fault_once, [] {
+        void* h = nullptr;
+        void* d = nullptr;
+        if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
+            cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (h) cudaFreeHost(h);
+            return;
+        }
+        *static_cast<volatile int*>(h) = 0;
+        g_fault_host = static_cast<int*>(h);
+        g_fault_dev = static_cast<int*>(d);
+    });
+    DIM3_REQUIRE(g_fault_dev, DIM3_ERR_NOMEM, "pinned allocation of the wait-fault flag failed");
+    return g_fault_dev;
 }
 
-template <typename K, bool kVals>
-__global__ void __launch_bounds__(kThreads) k_radix_scatter(const K* __restrict__ keys,
-                                                            const uint32_t* __restrict__ vals,
-                                                            K* __restrict__ okeys,
-                                                            uint32_t* __restrict__ ovals, int64_t n,
-                                                            int shift, const int64_t* offs, int64_t nb) {
-    __shared__ uint32_t wcount[kWarps][256];
-    __shared__ int64_t base[256];
-    for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&wcount[0][0])[i] = 0;
-    base[threadIdx.x] = offs[(int64_t)threadIdx.x * nb + blockIdx.x];
+void raise_if_wait_fault() {
+    if (!g_fault_host) return;
+    volatile int* f = g_fault_host;
+    if (*f) {
+        *f = 0;
+        throw Error(DIM3_ERR_TIMEOUT, "a device-side wait on another thread block gave up after 2 s");
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_os_hist(const K* __restrict__ keys, int64_t n, int passes,
+                                                      unsigned long long* ghist) {
+    __shared__ uint32_t h[kMaxPasses][256];
+    for (int i = threadIdx.x; i < kMaxPasses * 256; i += kThreads) (&h[0][0])[i] = 0;
     __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const K k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(unsigned)(k >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t v = h[p][threadIdx.x];
+        if (v) atomicAdd(&ghist[p * 256 + threadIdx.x], (unsigned long long)v);
+    }
+}
+
+// status[tile * 256 + digit]: flag in the top two bits (0 none yet, 1 the
+// tile's own count, 2 the inclusive count over tiles 0..tile), count below.
+// status_next (the buffer of the following pass) is cleared tile by tile.
+template <typename K, bool kVals>
+__global__ void __launch_bounds__(kThreads) k_os_pass(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                                      K* __restrict__ okeys, uint32_t* __restrict__ ovals, int64_t n,
+                                                      int pass, const unsigned long long* __restrict__ ghist,
+                                                      unsigned long long* status, unsigned long long* status_next,
+                                                      unsigned long long* ticket, int* fault) {
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    K* s_keys = reinterpret_cast<K*>(os_smem);
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(os_smem + (size_t)kRadixTile * sizeof(K));
+    __shared__ uint32_t wcount[kWarps][256];
+    __shared__ int64_t s_goff[256];
+    __shared__ uint32_t s_lstart[256];
+    __shared__ uint32_t s_w32[kWarps + 1];
+    __shared__ unsigned long long s_w64[kWarps + 1];
+    __shared__ int64_t s_tile;
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(ticket, 1ull);
+    for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&wcount[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int shift = 8 * pass;
     const unsigned lane = lane_id();
     const unsigned warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    const int64_t wbase = (int64_t)blockIdx.x * kRadixTile + (int64_t)warp * (kRadixTile / kWarps);
+    const int64_t tbase = t * kRadixTile;
+    const int64_t wbase = tbase + (int64_t)warp * (kRadixTile / kWarps);
     K k[kRadixIpt];
     uint32_t v[kRadixIpt];
     uint32_t rk[kRadixIpt];
-    unsigned dg[kRadixIpt];
 #pragma unroll
     for (int j = 0; j < kRadixIpt; ++j) {
-        int64_t idx = wbase + j * 32 + lane;
-        bool valid = idx < n;
+        const int64_t idx = wbase + j * 32 + lane;
+        const bool valid = idx < n;
         k[j] = valid ? keys[idx] : K(0);
         if (kVals) v[j] = valid ? vals[idx] : 0u;
-        unsigned d = valid ? (unsigned)((k[j] >> shift) & 255u) : 256u;
-        unsigned peers = __match_any_sync(kFull, d);
-        int leader = __ffs(peers) - 1;
+        const unsigned d = valid ? ((unsigned)(k[j] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const int leader = __ffs(peers) - 1;
         uint32_t before = 0;
         if (valid && (int)lane == leader) {
             before = wcount[warp][d];
             wcount[warp][d] = before + (uint32_t)__popc(peers);
         }
         before = __shfl_sync(kFull, before, leader);
-        rk[j] = before + (uint32_t)__popc(peers & lt);
-        dg[j] = d;
+        rk[j] = valid ? before + (uint32_t)__popc(peers & lt) : 0xffffffffu;
         __syncwarp();
     }
     __syncthreads();
-    {
-        const int d = threadIdx.x;
-        uint32_t run = 0;
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            uint32_t t = wcount[w][d];
-            wcount[w][d] = run;
-            run += t;
-        }
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = wcount[w][d];
+        wcount[w][d] = cnt;
+        cnt += c;
     }
+    // publish this tile's count of digit d before anything else
+    unsigned long long* my = status + t * 256 + d;
+    atomicExch(my, (t == 0 ? kLbInc : kLbAgg) | (unsigned long long)cnt);
+    if (status_next) status_next[t * 256 + d] = 0ull;
+    uint32_t ltot;
+    const uint32_t lstart = block_exclusive_scan<uint32_t, kThreads>(cnt, &ltot, s_w32);
+    unsigned long long gtot;
+    const unsigned long long gbase = block_exclusive_scan<unsigned long long, kThreads>(ghist[pass * 256 + d], &gtot, s_w64);
+    // decoupled look-back over the tiles before this one, digit d only
+    int64_t prefix = 0;
+    if (t > 0) {
+        int64_t j = t - 1;
+        const uint64_t t0 = global_ns();
+        uint32_t polls = 0;
+        while (j >= 0) {
+            const unsigned long long w = ld_relaxed_u64(status + j * 256 + d);
+            const unsigned long long f = w >> 62;
+            if (f == 0ull) {
+                if ((++polls & 63u) == 0u && global_ns() - t0 > kSortWaitNs) {
+                    *static_cast<volatile int*>(fault) = 1;
+                    break;
+                }
+                continue;
+            }
+            prefix += (int64_t)(w & kLbVal);
+            if (f == 2ull) break;
+            --j;
+        }
+        atomicExch(my, kLbInc | (unsigned long long)(prefix + cnt));
+    }
+    s_goff[d] = (int64_t)gbase + prefix - (int64_t)lstart;
+    s_lstart[d] = lstart;
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kRadixIpt; ++j) {
-        if (dg[j] < 256u) {
-            int64_t pos = base[dg[j]] + wcount[warp][dg[j]] + rk[j];
-            okeys[pos] = k[j];
-            if (kVals) ovals[pos] = v[j];
+        if (rk[j] != 0xffffffffu) {
+            const unsigned dg = (unsigned)(k[j] >> shift) & 255u;
+            const uint32_t li = s_lstart[dg] + wcount[warp][dg] + rk[j];
+            s_keys[li] = k[j];
+            if (kVals) s_vals[li] = v[j];
         }
+    }
+    __syncthreads();
+    const int tn = (int)min64((int64_t)kRadixTile, n - tbase);
+    for (int i = threadIdx.x; i < tn; i += kThreads) {
+        const K key = s_keys[i];
+        const int64_t pos = s_goff[(unsigned)(key >> shift) & 255u] + i;
+        okeys[pos] = key;
+        if (kVals) ovals[pos] = s_vals[i];
     }
 }
 
+template <typename K, bool kVals>
+static void os_pass_launch(const K* src, const uint32_t* sv, K* dst, uint32_t* dv, int64_t n, int pass,
+                           const unsigned long long* ghist, unsigned long long* st, unsigned long long* st_next,
+                           unsigned long long* ticket, int* fault, cudaStream_t s) {
+    constexpr size_t smem = (size_t)kRadixTile * (sizeof(K) + (kVals ? 4 : 0));
+    static bool attr_done[64] = {false};
+    int dev = 0;
+    DIM3_CUDA(cudaGetDevice(&dev));
+    if (!attr_done[dev & 63]) {
+        DIM3_CUDA(cudaFuncSetAttribute(k_os_pass<K, kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_done[dev & 63] = true;
+    }
+    k_os_pass<K, kVals><<<(unsigned)ceil_div(n, kRadixTile), kThreads, smem, s>>>(src, sv, dst, dv, n, pass, ghist, st,
+                                                                                  st_next, ticket, fault);
+    DIM3_LAUNCHED();
+}
+
 template <typename K>
-static void radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, int64_t n,
-                            int bits, cudaStream_t s) {
+static void radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int bits,
+                            cudaStream_t s) {
     if (n <= 1 || bits <= 0) return;
-    const int64_t nb = ceil_div(n, kRadixTile);
-    DevBuf hist, offs;
-    hist.alloc((size_t)nb * 256 * sizeof(int32_t), s);
-    offs.alloc(((size_t)nb * 256 + 1) * sizeof(int64_t), s);
-    const int passes = (bits + 7) / 8;
+    const int passes = std::min<int>((bits + 7) / 8, (int)sizeof(K));
+    const int64_t tiles = ceil_div(n, kRadixTile);
+    int* fault = wait_fault_flag();
+    // scratch: tickets [kMaxPasses], digit counts [kMaxPasses][256], two status buffers [tiles][256]
+    const size_t head = (size_t)kMaxPasses * (1 + 256);
+    const size_t stw = (size_t)tiles * 256;
+    DevBuf scratch;
+    scratch.alloc((head + 2 * stw) * sizeof(unsigned long long), s);
+    unsigned long long* ticket = scratch.as<unsigned long long>();
+    unsigned long long* ghist = ticket + kMaxPasses;
+    unsigned long long* st[2] = {ghist + (size_t)kMaxPasses * 256, ghist + (size_t)kMaxPasses * 256 + stw};
+    DIM3_CUDA(cudaMemsetAsync(scratch.p, 0, (head + stw) * sizeof(unsigned long long), s));
+    const unsigned hg = (unsigned)std::min<int64_t>(ceil_div(n, kThreads * 8), (int64_t)kSms * 8);
+    k_os_hist<K><<<hg, kThreads, 0, s>>>(keys, n, passes, ghist);
+    DIM3_LAUNCHED();
     K* src = keys;
     K* dst = keys_alt;
     uint32_t* sv = vals;
     uint32_t* dv = vals_alt;
     for (int p = 0; p < passes; ++p) {
-        k_radix_hist<K><<<(unsigned)nb, kThreads, 0, s>>>(src, n, 8 * p, hist.as<int32_t>(), nb);
-        DIM3_LAUNCHED();
-        exclusive_scan_i32_to_i64(hist.as<int32_t>(), offs.as<int64_t>(), nb * 256, s);
+        unsigned long long* next = p + 1 < passes ? st[(p + 1) & 1] : nullptr;
         if (vals)
-            k_radix_scatter<K, true><<<(unsigned)nb, kThreads, 0, s>>>(src, sv, dst, dv, n, 8 * p,
-                                                                       offs.as<int64_t>(), nb);
+            os_pass_launch<K, true>(src, sv, dst, dv, n, p, ghist, st[p & 1], next, ticket + p, fault, s);
         else
-            k_radix_scatter<K, false><<<(unsigned)nb, kThreads, 0, s>>>(src, nullptr, dst, nullptr, n,
-                                                                        8 * p, offs.as<int64_t>(), nb);
-        DIM3_LAUNCHED();
+            os_pass_launch<K, false>(src, nullptr, dst, nullptr, n, p, ghist, st[p & 1], next, ticket + p, fault, s);
         std::swap(src, dst);
         std::swap(sv, dv);
     }
