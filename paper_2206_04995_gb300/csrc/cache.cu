@@ -147,7 +147,7 @@ void finish_cache_index(Plan& p, cudaStream_t s) {
     p.zd_list = std::move(zl);
     p.h_inst_zd_lo.assign(2, 0);
     p.h_inst_zd_lo[1] = total;
-    DIM3_CUDA(cudaMemcpyAsync(p.inst_zd_lo.p, p.h_inst_zd_lo.data(), 16, cudaMemcpyHostToDevice, s));
+    store_i64_pair(p.inst_zd_lo.as<int64_t>(), 0, total, s);
     const int64_t n_w = ceil_div(p.n_zc, 32);
     p.zc_cmask.alloc((size_t)std::max<int64_t>(n_w, 1) * 4, s);
     if (n_w > 0) {

@@ -95,7 +95,12 @@ struct DevBuf {
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);  // out[n+1]
 void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s);
+// p[0] = a, p[1] = b in stream order (no host synchronisation, unlike a copy
+// from pageable host memory)
+void store_i64_pair(int64_t* p, int64_t a, int64_t b, cudaStream_t s);
 int64_t read_i64(const int64_t* d, cudaStream_t s);  // synchronising read of one device value
+// h[i] = *d[i] for i < n (n <= 16) with ONE synchronisation
+void read_i64_n(const int64_t* const* d, int n, int64_t* h, cudaStream_t s);
 // A bounded device wait that gives up stores 1 to this process-wide flag
 // (pinned, mapped host memory); raise_if_wait_fault(), called after
 // synchronisations (read_i64, the end of every C-ABI call), turns it into
@@ -105,14 +110,19 @@ void raise_if_wait_fault();
 // LSD radix sort of n keys (32- or 64-bit) on their low `bits` bits, with an
 // optional uint32 payload. Results end in keys/vals (the alt buffers are scratch).
 // Stable; one-sweep passes (a tile that waits on its predecessors for more than
-// 2 s gives up and sets the wait-fault flag).
+// 2 s gives up and sets the wait-fault flag). With n_dev, the count is
+// min(n, *n_dev) read on the device (n then only bounds it), so no host read
+// has to precede the sort.
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                    int64_t n, int bits, cudaStream_t s);
+                    int64_t n, int bits, cudaStream_t s, const int64_t* n_dev = nullptr);
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                    int64_t n, int bits, cudaStream_t s);
+                    int64_t n, int bits, cudaStream_t s, const int64_t* n_dev = nullptr);
 // Drop adjacent duplicates of sorted keys; returns the count (synchronising).
-int64_t unique_sorted_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
-int64_t unique_sorted_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s);
+// With n_dev the input is in[0, min(n, *n_dev)).
+int64_t unique_sorted_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s,
+                          const int64_t* n_dev = nullptr);
+int64_t unique_sorted_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s,
+                          const int64_t* n_dev = nullptr);
 // rowptr[r] = first index i with (keys[i] >> shift) >= r, for r = 0..n_rows
 void rowptr_from_sorted_u32(const uint32_t* keys, int64_t n, int shift, int64_t n_rows,
                             int64_t* rowptr, cudaStream_t s);

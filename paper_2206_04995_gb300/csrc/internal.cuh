@@ -12,8 +12,9 @@ namespace dimcube {
 struct ValueMap {
     DevBuf table;  // uint64 slots: 0 = empty, else (1 << 32) | uint32(value)
     DevBuf rank;   // uint32 per slot: rank of the slot's value
+    DevBuf count;  // int64: the distinct count on the device
     uint32_t mask = 0;
-    int64_t n_distinct = 0;
+    int64_t n_distinct = 0;  // -1 until read (resolve_counts)
 };
 
 // Map vals[0..n) (rows with pred[i] < 0 are skipped and get id -1).
@@ -22,8 +23,14 @@ void build_value_map(const int32_t* vals, const int32_t* pred, int64_t n, ValueM
                      int32_t* ids_out, int32_t* dict_out, cudaStream_t s);
 // Batched form: row i belongs to instance tags[i] (0 <= tag < n_tags); ids
 // rank the (instance, value) pairs; dict_tag_out[id] = the id's instance.
+// With read_count false the distinct count is left on the device
+// (n_distinct = -1) for resolve_counts.
 void build_value_map(const int32_t* vals, const int32_t* tags, int n_tags, const int32_t* pred, int64_t n,
-                     ValueMap& vm, int32_t* ids_out, int32_t* dict_out, int32_t* dict_tag_out, cudaStream_t s);
+                     ValueMap& vm, int32_t* ids_out, int32_t* dict_out, int32_t* dict_tag_out, cudaStream_t s,
+                     bool read_count = true);
+// Reads the unresolved distinct counts of maps[0..n_maps) and, if extra is not
+// null, *extra into *extra_out, with one synchronisation.
+int64_t resolve_counts(ValueMap* const* maps, int n_maps, const int64_t* extra, int64_t* extra_out, cudaStream_t s);
 // ids_out[i] = id of (tags[i], vals[i]) in vm (tags may be null), or -1 if absent.
 void probe_value_map(const ValueMap& vm, const int32_t* vals, const int32_t* tags, int64_t n, int32_t* ids_out,
                      cudaStream_t s);

@@ -82,8 +82,9 @@ __global__ void k_hash_collect(const unsigned long long* table, int64_t cap, K* 
 }
 
 template <typename K>
-__global__ void k_hash_rank(const K* skeys, const uint32_t* sslots, int64_t d, uint32_t* rank, int32_t* dict_out,
-                            int32_t* dict_tag_out) {
+__global__ void k_hash_rank(const K* skeys, const uint32_t* sslots, int64_t d, const int64_t* d_dev, uint32_t* rank,
+                            int32_t* dict_out, int32_t* dict_tag_out) {
+    if (d_dev) d = min64(d, *d_dev);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < d;
          p += (int64_t)gridDim.x * blockDim.x) {
         rank[sslots[p]] = (uint32_t)p;
@@ -128,35 +129,62 @@ static unsigned grid_for(int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kThreads), 152 * 16));
 }
 
+// With read_count the distinct count is read at once (one synchronisation);
+// otherwise it stays on the device (vm.count) and the sort and the ranking
+// take it from there, so that several maps can share one host read.
 template <typename K>
 static void collect_sort_rank(ValueMap& vm, int64_t cap, int64_t n, int tag_bits, int32_t* dict_out,
-                              int32_t* dict_tag_out, cudaStream_t s) {
-    DevBuf counter, keys, sl, keys_alt, sl_alt;
-    counter.alloc(8, s);
-    DIM3_CUDA(cudaMemsetAsync(counter.p, 0, 8, s));
+                              int32_t* dict_tag_out, bool read_count, cudaStream_t s) {
+    DevBuf keys, sl, keys_alt, sl_alt;
+    vm.count.alloc(8, s);
+    DIM3_CUDA(cudaMemsetAsync(vm.count.p, 0, 8, s));
     keys.alloc((size_t)n * sizeof(K), s);
     sl.alloc((size_t)n * 4, s);
     k_hash_collect<K><<<grid_for(cap), kThreads, 0, s>>>(vm.table.as<unsigned long long>(), cap, keys.as<K>(),
-                                                          sl.as<uint32_t>(), counter.as<unsigned long long>());
+                                                          sl.as<uint32_t>(), vm.count.as<unsigned long long>());
     DIM3_LAUNCHED();
-    const int64_t d = read_i64(counter.as<int64_t>(), s);
-    DIM3_REQUIRE(d >= 0 && d <= n, DIM3_ERR_CUDA, "value map: inconsistent distinct count");
-    vm.n_distinct = d;
+    int64_t d = n;  // bound (distinct values <= rows)
+    const int64_t* d_dev = vm.count.as<int64_t>();
+    vm.n_distinct = -1;
+    if (read_count) {
+        d = read_i64(d_dev, s);
+        DIM3_REQUIRE(d >= 0 && d <= n, DIM3_ERR_CUDA, "value map: inconsistent distinct count");
+        vm.n_distinct = d;
+        d_dev = nullptr;
+    }
     keys_alt.alloc((size_t)std::max<int64_t>(d, 1) * sizeof(K), s);
     sl_alt.alloc((size_t)std::max<int64_t>(d, 1) * 4, s);
     if constexpr (sizeof(K) == 4)
         radix_sort_u32(keys.as<uint32_t>(), sl.as<uint32_t>(), keys_alt.as<uint32_t>(), sl_alt.as<uint32_t>(), d, 32,
-                       s);
+                       s, d_dev);
     else
         radix_sort_u64(keys.as<uint64_t>(), sl.as<uint32_t>(), keys_alt.as<uint64_t>(), sl_alt.as<uint32_t>(), d,
-                       32 + tag_bits, s);
-    k_hash_rank<K><<<grid_for(d), kThreads, 0, s>>>(keys.as<K>(), sl.as<uint32_t>(), d, vm.rank.as<uint32_t>(),
+                       32 + tag_bits, s, d_dev);
+    k_hash_rank<K><<<grid_for(d), kThreads, 0, s>>>(keys.as<K>(), sl.as<uint32_t>(), d, d_dev, vm.rank.as<uint32_t>(),
                                                      dict_out, dict_tag_out);
     DIM3_LAUNCHED();
 }
 
+int64_t resolve_counts(ValueMap* const* maps, int n_maps, const int64_t* extra, int64_t* extra_out, cudaStream_t s) {
+    const int64_t* src[8];
+    int64_t got[8];
+    int k = 0;
+    for (int i = 0; i < n_maps; ++i)
+        if (maps[i]->n_distinct < 0) src[k++] = maps[i]->count.as<int64_t>();
+    const int n_counts = k;
+    if (extra) src[k++] = extra;
+    if (k == 0) return 0;
+    read_i64_n(src, k, got, s);
+    k = 0;
+    for (int i = 0; i < n_maps; ++i)
+        if (maps[i]->n_distinct < 0) maps[i]->n_distinct = got[k++];
+    if (extra) *extra_out = got[n_counts];
+    return n_counts;
+}
+
 void build_value_map(const int32_t* vals, const int32_t* tags, int n_tags, const int32_t* pred, int64_t n,
-                     ValueMap& vm, int32_t* ids_out, int32_t* dict_out, int32_t* dict_tag_out, cudaStream_t s) {
+                     ValueMap& vm, int32_t* ids_out, int32_t* dict_out, int32_t* dict_tag_out, cudaStream_t s,
+                     bool read_count) {
     int64_t cap = 64;
     while (cap < 2 * n) cap <<= 1;
     DIM3_REQUIRE(cap <= (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "column too long for the value map");
@@ -172,9 +200,9 @@ void build_value_map(const int32_t* vals, const int32_t* tags, int n_tags, const
                                                     slots.as<uint32_t>());
     DIM3_LAUNCHED();
     if (tags && n_tags > 1)
-        collect_sort_rank<uint64_t>(vm, cap, n, bits_for(n_tags), dict_out, dict_tag_out, s);
+        collect_sort_rank<uint64_t>(vm, cap, n, bits_for(n_tags), dict_out, dict_tag_out, read_count, s);
     else
-        collect_sort_rank<uint32_t>(vm, cap, n, 0, dict_out, dict_tag_out, s);
+        collect_sort_rank<uint32_t>(vm, cap, n, 0, dict_out, dict_tag_out, read_count, s);
     k_gather_rank<<<grid_for(n), kThreads, 0, s>>>(slots.as<uint32_t>(), n, vm.rank.as<uint32_t>(), ids_out);
     DIM3_LAUNCHED();
 }

@@ -193,18 +193,20 @@ static void sort_unique_pairs(const int32_t* a, const int32_t* b, int64_t n, int
                                                           counter.as<unsigned long long>());
         DIM3_LAUNCHED();
     }
-    const int64_t m = read_i64(counter.as<int64_t>(), s);
-    alt.alloc((size_t)std::max<int64_t>(m, 1) * sizeof(K), s);
+    // the count of packed pairs stays on the device: sort and unique take it
+    // from there, and the one host read is the unique count
+    const int64_t* m_dev = counter.as<int64_t>();
+    alt.alloc((size_t)std::max<int64_t>(n, 1) * sizeof(K), s);
     if constexpr (sizeof(K) == 4)
-        radix_sort_u32(keys.as<uint32_t>(), nullptr, alt.as<uint32_t>(), nullptr, m, bits, s);
+        radix_sort_u32(keys.as<uint32_t>(), nullptr, alt.as<uint32_t>(), nullptr, n, bits, s, m_dev);
     else
-        radix_sort_u64(keys.as<uint64_t>(), nullptr, alt.as<uint64_t>(), nullptr, m, bits, s);
+        radix_sort_u64(keys.as<uint64_t>(), nullptr, alt.as<uint64_t>(), nullptr, n, bits, s, m_dev);
     // unique into alt, then keep alt
     int64_t u;
     if constexpr (sizeof(K) == 4)
-        u = unique_sorted_u32(keys.as<uint32_t>(), alt.as<uint32_t>(), m, s);
+        u = unique_sorted_u32(keys.as<uint32_t>(), alt.as<uint32_t>(), n, s, m_dev);
     else
-        u = unique_sorted_u64(keys.as<uint64_t>(), alt.as<uint64_t>(), m, s);
+        u = unique_sorted_u64(keys.as<uint64_t>(), alt.as<uint64_t>(), n, s, m_dev);
     out.keys = std::move(alt);
     out.n = u;
 }
@@ -264,18 +266,21 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
     }
 
     // join tuples per x and |OUT_J|
+    DevBuf outj_sc;
     p.outj_x.alloc((size_t)std::max<int64_t>(n_x, 1) * 8, s);
     if (n_x > 0) {
         k_outj_x<<<grid_for(n_x * 32), kThreads, 0, s>>>(p.r_rowptr.as<int64_t>(), p.r_col.as<int32_t>(), n_x,
                                                      p.deg_s.as<int32_t>(), p.outj_x.as<int64_t>());
         DIM3_LAUNCHED();
-        DevBuf sc;
-        sc.alloc((size_t)(n_x + 1) * 8, s);
-        exclusive_scan_i64(p.outj_x.as<int64_t>(), sc.as<int64_t>(), n_x, s);
-        p.info.out_j = read_i64(sc.as<int64_t>() + n_x, s);
+        // |OUT_J| is read together with the next host read (below)
+        outj_sc.alloc((size_t)(n_x + 1) * 8, s);
+        exclusive_scan_i64(p.outj_x.as<int64_t>(), outj_sc.as<int64_t>(), n_x, s);
     } else {
-        p.info.out_j = 0;
+        outj_sc.alloc(8, s);
+        DIM3_CUDA(cudaMemsetAsync(outj_sc.p, 0, 8, s));
     }
+    const int64_t* outj_dev = outj_sc.as<int64_t>() + (n_x > 0 ? n_x : 0);
+    bool outj_read = false;
 
     // intersection-free split: z dense iff m_z >= theta
     if (theta < 0) theta = INT32_MAX;  // tuned choice made by the caller; default all sparse
@@ -286,12 +291,23 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
     zpos.alloc((size_t)(n_z + 1) * 8, s);
     zd_index.alloc((size_t)std::max<int64_t>(n_z, 1) * 4, s);
     int64_t n_zd = 0;
-    if (n_z > 0) {
+    // m_z counts distinct S tuples, so theta above their number leaves every z
+    // sparse: no flags, no scan, no host read
+    const bool any_dense = theta <= sp.n;
+    if (n_z > 0 && !any_dense) {
+        DIM3_CUDA(cudaMemsetAsync(p.dense_z.p, 0, (size_t)n_z, s));
+        p.zd_list.alloc(4, s);
+    } else if (n_z > 0) {
         k_dense_flags<<<grid_for(n_z), kThreads, 0, s>>>(p.m_z.as<int32_t>(), n_z, theta, p.dense_z.as<uint8_t>(),
                                                           zflag.as<int32_t>());
         DIM3_LAUNCHED();
         exclusive_scan_i32_to_i64(zflag.as<int32_t>(), zpos.as<int64_t>(), n_z, s);
-        n_zd = read_i64(zpos.as<int64_t>() + n_z, s);
+        const int64_t* src[2] = {zpos.as<int64_t>() + n_z, outj_dev};
+        int64_t got[2];
+        read_i64_n(src, 2, got, s);
+        n_zd = got[0];
+        p.info.out_j = got[1];
+        outj_read = true;
         p.zd_list.alloc((size_t)std::max<int64_t>(n_zd, 1) * 4, s);
         k_zd_list<<<grid_for(n_z), kThreads, 0, s>>>(zflag.as<int32_t>(), zpos.as<int64_t>(), n_z,
                                                       p.zd_list.as<int32_t>(), zd_index.as<int32_t>());
@@ -316,15 +332,20 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
         DIM3_CUDA(cudaStreamSynchronize(s));
     } else {
         for (int t = 1; t <= p.n_inst; ++t) p.h_inst_zd_lo[t] = n_zd;
-        DIM3_CUDA(cudaMemcpyAsync(p.inst_zd_lo.p, p.h_inst_zd_lo.data(), (size_t)(p.n_inst + 1) * 8,
-                                  cudaMemcpyHostToDevice, s));
-        DIM3_CUDA(cudaStreamSynchronize(s));
+        if (p.n_inst == 1) {
+            store_i64_pair(p.inst_zd_lo.as<int64_t>(), 0, n_zd, s);
+        } else {
+            DIM3_CUDA(cudaMemcpyAsync(p.inst_zd_lo.p, p.h_inst_zd_lo.data(), (size_t)(p.n_inst + 1) * 8,
+                                      cudaMemcpyHostToDevice, s));
+            DIM3_CUDA(cudaStreamSynchronize(s));
+        }
     }
 
-    // S_sparse: the distinct tuples of sparse z, still sorted by (y, z)
-    DevBuf sflag, spos, skeys;
-    int64_t n_ss = 0;
-    if (sp.n > 0) {
+    // S_sparse: the distinct tuples of sparse z, still sorted by (y, z) (all
+    // of them when no z is dense)
+    DevBuf sflag, spos, skeys_buf;
+    int64_t n_ss = n_zd > 0 ? 0 : sp.n;
+    if (sp.n > 0 && n_zd > 0) {
         sflag.alloc((size_t)sp.n * 4, s);
         spos.alloc((size_t)(sp.n + 1) * 8, s);
         k_sparse_flags<K><<<grid_for(sp.n), kThreads, 0, s>>>(keys, sp.n, zmask, p.dense_z.as<uint8_t>(),
@@ -334,19 +355,23 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
         n_ss = read_i64(spos.as<int64_t>() + sp.n, s);
     }
     p.info.n_s_sparse = n_ss;
-    skeys.alloc((size_t)std::max<int64_t>(n_ss, 1) * sizeof(K), s);
-    if (n_ss > 0) {
-        k_compact<K><<<grid_for(sp.n), kThreads, 0, s>>>(keys, sp.n, sflag.as<int32_t>(), spos.as<int64_t>(),
-                                                          skeys.as<K>());
-        DIM3_LAUNCHED();
+    const K* skeys = keys;
+    if (n_zd > 0) {
+        skeys_buf.alloc((size_t)std::max<int64_t>(n_ss, 1) * sizeof(K), s);
+        if (n_ss > 0) {
+            k_compact<K><<<grid_for(sp.n), kThreads, 0, s>>>(keys, sp.n, sflag.as<int32_t>(), spos.as<int64_t>(),
+                                                              skeys_buf.as<K>());
+            DIM3_LAUNCHED();
+        }
+        skeys = skeys_buf.as<K>();
     }
     p.ss_col.alloc((size_t)std::max<int64_t>(n_ss, 1) * 4, s);
     p.ss_rowptr.alloc((size_t)(n_y + 1) * 8, s);
     if (n_ss > 0) {
-        k_split_low<K><<<grid_for(n_ss), kThreads, 0, s>>>(skeys.as<K>(), n_ss, zmask, p.ss_col.as<int32_t>());
+        k_split_low<K><<<grid_for(n_ss), kThreads, 0, s>>>(skeys, n_ss, zmask, p.ss_col.as<int32_t>());
         DIM3_LAUNCHED();
     }
-    rowptr_sorted<K>(skeys.as<K>(), n_ss, bz, n_y, p.ss_rowptr.as<int64_t>(), s);
+    rowptr_sorted<K>(skeys, n_ss, bz, n_y, p.ss_rowptr.as<int64_t>(), s);
 
     // wide S_sparse rows held as z-bitmaps over the z window of their
     // instance (all of Z for a single instance): a row is wide when it holds
@@ -373,11 +398,16 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
                                                             yflag.as<int32_t>(), words.as<int64_t>());
             DIM3_LAUNCHED();
             exclusive_scan_i64(words.as<int64_t>(), wpos.as<int64_t>(), n_y, s);
-            n_words = read_i64(wpos.as<int64_t>() + n_y, s);
+            exclusive_scan_i32_to_i64(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y, s);
+            const int64_t* src[3] = {wpos.as<int64_t>() + n_y, ypos.as<int64_t>() + n_y, outj_dev};
+            int64_t got[3];
+            read_i64_n(src, outj_read ? 2 : 3, got, s);
+            n_words = got[0];
+            n_bm = got[1];
+            if (!outj_read) p.info.out_j = got[2];
+            outj_read = true;
             if (n_words <= budget_words) break;
         }
-        exclusive_scan_i32_to_i64(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y, s);
-        n_bm = read_i64(ypos.as<int64_t>() + n_y, s);
         k_index_from_flags<<<grid_for(n_y), kThreads, 0, s>>>(yflag.as<int32_t>(), ypos.as<int64_t>(), n_y,
                                                                p.bm_row_of_y.as<int32_t>());
         DIM3_LAUNCHED();
@@ -389,11 +419,12 @@ static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const in
         p.bm_off.alloc(8, s);
         DIM3_CUDA(cudaMemsetAsync(p.bm_off.p, 0, 8, s));
     }
+    if (!outj_read) p.info.out_j = read_i64(outj_dev, s);
     p.info.n_y_bitmap = n_bm;
     p.ss_bits.alloc((size_t)std::max<int64_t>(n_words, 1) * 4, s);
     if (n_bm > 0) {
         DIM3_CUDA(cudaMemsetAsync(p.ss_bits.p, 0, (size_t)n_words * 4, s));
-        k_fill_row_bits<K><<<grid_for(n_ss), kThreads, 0, s>>>(skeys.as<K>(), n_ss, bz, zmask,
+        k_fill_row_bits<K><<<grid_for(n_ss), kThreads, 0, s>>>(skeys, n_ss, bz, zmask,
                                                                 p.bm_row_of_y.as<int32_t>(), p.bm_off.as<int64_t>(),
                                                                 y_tag, p.inst_z_lo.as<int64_t>(),
                                                                 p.ss_bits.as<uint32_t>());
@@ -436,8 +467,12 @@ static void instance_ranges(const int32_t* tag_dev, int64_t n, int n_inst, DevBu
         DIM3_CUDA(cudaStreamSynchronize(s));
     } else {
         for (int t = 1; t <= n_inst; ++t) lo[t] = n;
-        DIM3_CUDA(cudaMemcpyAsync(lo_dev.p, lo.data(), (size_t)(n_inst + 1) * 8, cudaMemcpyHostToDevice, s));
-        DIM3_CUDA(cudaStreamSynchronize(s));
+        if (n_inst == 1) {
+            store_i64_pair(lo_dev.as<int64_t>(), 0, n, s);
+        } else {
+            DIM3_CUDA(cudaMemcpyAsync(lo_dev.p, lo.data(), (size_t)(n_inst + 1) * 8, cudaMemcpyHostToDevice, s));
+            DIM3_CUDA(cudaStreamSynchronize(s));
+        }
     }
 }
 
@@ -486,10 +521,17 @@ static void premapped_ids(Plan& p, const PlanInput& in, cudaStream_t s) {
     }
 }
 
+// cnt[v] += occurrences of v; lanes holding the same id add once (skewed
+// columns put many equal ids in one warp)
 __global__ void k_count_ids(const int32_t* __restrict__ ids, int64_t n, unsigned long long* cnt) {
-    GRID_STRIDE(i, n) {
-        const int32_t v = ids[i];
-        if (v >= 0) atomicAdd(cnt + v, 1ull);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t iters = (n + stride - 1) / stride;
+    const unsigned lane = threadIdx.x & 31u;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int32_t v = i < n ? ids[i] : -1;
+        const unsigned peers = __match_any_sync(kFull, v);
+        if (v >= 0 && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(cnt + v, (unsigned long long)__popc(peers));
     }
 }
 
@@ -538,20 +580,20 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
             z_tag.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
             p->x_tag.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
         }
+        // The three maps leave their distinct counts on the device; they are
+        // read together (with f1's |OUT_J| when that is asked for).
+        ValueMap ymap, xmap, zmap;
         {
             // y from S.y; R tuples whose y is absent from S.y get id -1 (dropped)
-            ValueMap ymap;
             p->dict_y.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
             build_value_map(in.s_key, in.s_tag, p->n_inst, nullptr, ns, ymap, sy_id.as<int32_t>(),
-                            p->dict_y.as<int32_t>(), y_tag.as<int32_t>(), s);
-            p->info.n_y = ymap.n_distinct;
+                            p->dict_y.as<int32_t>(), y_tag.as<int32_t>(), s, false);
             probe_value_map(ymap, in.r_key, in.r_tag, nr, ry_id.as<int32_t>(), s);
         }
         if (prefer_classical) {
             // f1 (Section 2.6) from the y ids just made: |OUT_J| of the bags
-            const int64_t n_y = p->info.n_y;
             DevBuf deg, tot;
-            deg.alloc((size_t)std::max<int64_t>(n_y, 1) * 8, s);
+            deg.alloc((size_t)std::max<int64_t>(ns, 1) * 8, s);  // y ids < |Y| <= |S|
             tot.alloc(8, s);
             DIM3_CUDA(cudaMemsetAsync(deg.p, 0, deg.bytes, s));
             DIM3_CUDA(cudaMemsetAsync(tot.p, 0, 8, s));
@@ -564,24 +606,26 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
                                                              tot.as<unsigned long long>());
                 DIM3_LAUNCHED();
             }
-            const int64_t out_j = read_i64(tot.as<int64_t>(), s);
+            int64_t out_j = 0;
+            ValueMap* ym = &ymap;
+            resolve_counts(&ym, 1, tot.as<int64_t>(), &out_j, s);
             *prefer_classical = f1_value(nr, ns, out_j, ctx.opt.f1c) > 0.0;
             if (*prefer_classical) return nullptr;
         }
-        {
-            ValueMap xmap;
-            p->dict_x.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
-            build_value_map(in.r_val, in.r_tag, p->n_inst, ry_id.as<int32_t>(), nr, xmap, rx_id.as<int32_t>(),
-                            p->dict_x.as<int32_t>(), p->x_tag.as<int32_t>(), s);
-            p->info.n_x = xmap.n_distinct;
-        }
-        {
-            ValueMap zmap;
-            p->dict_z.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-            build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(),
-                            p->dict_z.as<int32_t>(), z_tag.as<int32_t>(), s);
-            p->info.n_z = zmap.n_distinct;
-        }
+        p->dict_x.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+        build_value_map(in.r_val, in.r_tag, p->n_inst, ry_id.as<int32_t>(), nr, xmap, rx_id.as<int32_t>(),
+                        p->dict_x.as<int32_t>(), p->x_tag.as<int32_t>(), s, false);
+        p->dict_z.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+        build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(),
+                        p->dict_z.as<int32_t>(), z_tag.as<int32_t>(), s, false);
+        ValueMap* maps[3] = {&ymap, &xmap, &zmap};
+        resolve_counts(maps, 3, nullptr, nullptr, s);
+        DIM3_REQUIRE(ymap.n_distinct >= 0 && ymap.n_distinct <= ns && xmap.n_distinct >= 0 &&
+                         xmap.n_distinct <= nr && zmap.n_distinct >= 0 && zmap.n_distinct <= ns,
+                     DIM3_ERR_CUDA, "value map: inconsistent distinct count");
+        p->info.n_y = ymap.n_distinct;
+        p->info.n_x = xmap.n_distinct;
+        p->info.n_z = zmap.n_distinct;
         // Section 3: the S tuples of cached z leave after mapping, so the
         // dictionaries (and X) stay those of the full tables
         if (in.cache) attach_cache_ids(*p, *in.cache, sz_id.as<int32_t>(), ns, s);

@@ -101,11 +101,52 @@ void fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t s) {
     DIM3_LAUNCHED();
 }
 
-int64_t read_i64(const int64_t* d, cudaStream_t s) {
-    int64_t h = 0;
-    DIM3_CUDA(cudaMemcpyAsync(&h, d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+__global__ void k_store_pair(int64_t* p, int64_t a, int64_t b) {
+    if (threadIdx.x == 0) {
+        p[0] = a;
+        p[1] = b;
+    }
+}
+
+void store_i64_pair(int64_t* p, int64_t a, int64_t b, cudaStream_t s) {
+    k_store_pair<<<1, 32, 0, s>>>(p, a, b);
+    DIM3_LAUNCHED();
+}
+
+// Pinned staging for synchronising reads: a copy into pageable memory would
+// block on its own, so several values could not share one synchronisation.
+constexpr int kReadSlots = 16;
+static int64_t* read_slots() {
+    thread_local struct Slots {
+        int64_t* p = nullptr;
+        ~Slots() {
+            if (p) cudaFreeHost(p);
+        }
+    } slots;
+    if (!slots.p) {
+        void* h = nullptr;
+        if (cudaHostAlloc(&h, kReadSlots * sizeof(int64_t), cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(DIM3_ERR_NOMEM, "pinned allocation of the read slots failed");
+        }
+        slots.p = static_cast<int64_t*>(h);
+    }
+    return slots.p;
+}
+
+void read_i64_n(const int64_t* const* d, int n, int64_t* h, cudaStream_t s) {
+    DIM3_REQUIRE(n >= 0 && n <= kReadSlots, DIM3_ERR_ARG, "too many values in one read");
+    int64_t* slot = read_slots();
+    for (int i = 0; i < n; ++i)
+        DIM3_CUDA(cudaMemcpyAsync(slot + i, d[i], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DIM3_CUDA(cudaStreamSynchronize(s));
     raise_if_wait_fault();
+    for (int i = 0; i < n; ++i) h[i] = slot[i];
+}
+
+int64_t read_i64(const int64_t* d, cudaStream_t s) {
+    int64_t h = 0;
+    read_i64_n(&d, 1, &h, s);
     return h;
 }
 
@@ -159,9 +200,10 @@ void raise_if_wait_fault() {
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_os_hist(const K* __restrict__ keys, int64_t n, int passes,
-                                                      unsigned long long* ghist) {
+__global__ void __launch_bounds__(kThreads) k_os_hist(const K* __restrict__ keys, int64_t n, const int64_t* n_dev,
+                                                      int passes, unsigned long long* ghist) {
     __shared__ uint32_t h[kMaxPasses][256];
+    if (n_dev) n = min64(n, *n_dev);
     for (int i = threadIdx.x; i < kMaxPasses * 256; i += kThreads) (&h[0][0])[i] = 0;
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
@@ -181,7 +223,8 @@ __global__ void __launch_bounds__(kThreads) k_os_hist(const K* __restrict__ keys
 template <typename K, bool kVals>
 __global__ void __launch_bounds__(kThreads) k_os_pass(const K* __restrict__ keys, const uint32_t* __restrict__ vals,
                                                       K* __restrict__ okeys, uint32_t* __restrict__ ovals, int64_t n,
-                                                      int pass, const unsigned long long* __restrict__ ghist,
+                                                      const int64_t* n_dev, int pass,
+                                                      const unsigned long long* __restrict__ ghist,
                                                       unsigned long long* status, unsigned long long* status_next,
                                                       unsigned long long* ticket, int* fault) {
     extern __shared__ __align__(16) unsigned char os_smem[];
@@ -197,6 +240,10 @@ __global__ void __launch_bounds__(kThreads) k_os_pass(const K* __restrict__ keys
     for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) (&wcount[0][0])[i] = 0;
     __syncthreads();
     const int64_t t = s_tile;
+    // with a device-side count the grid covers the largest count; tiles past
+    // the actual one have nothing to do and nobody waits on them
+    if (n_dev) n = min64(n, *n_dev);
+    if (t * kRadixTile >= n) return;
     const int shift = 8 * pass;
     const unsigned lane = lane_id();
     const unsigned warp = threadIdx.x >> 5;
@@ -241,25 +288,37 @@ __global__ void __launch_bounds__(kThreads) k_os_pass(const K* __restrict__ keys
     const uint32_t lstart = block_exclusive_scan<uint32_t, kThreads>(cnt, &ltot, s_w32);
     unsigned long long gtot;
     const unsigned long long gbase = block_exclusive_scan<unsigned long long, kThreads>(ghist[pass * 256 + d], &gtot, s_w64);
-    // decoupled look-back over the tiles before this one, digit d only
+    // decoupled look-back over the tiles before this one, digit d only; the
+    // words of kLbBatch predecessors are loaded at once, so a walk through
+    // tiles that have only published their own counts costs one load latency
+    // per kLbBatch tiles (before tile -1 reads as an inclusive zero)
+    constexpr int kLbBatch = 8;
     int64_t prefix = 0;
     if (t > 0) {
         int64_t j = t - 1;
         const uint64_t t0 = global_ns();
         uint32_t polls = 0;
-        while (j >= 0) {
-            const unsigned long long w = ld_relaxed_u64(status + j * 256 + d);
-            const unsigned long long f = w >> 62;
-            if (f == 0ull) {
-                if ((++polls & 63u) == 0u && global_ns() - t0 > kSortWaitNs) {
-                    *static_cast<volatile int*>(fault) = 1;
-                    break;
-                }
-                continue;
+        while (true) {
+            unsigned long long w[kLbBatch];
+#pragma unroll
+            for (int q = 0; q < kLbBatch; ++q) w[q] = j - q >= 0 ? ld_relaxed_u64(status + (j - q) * 256 + d) : kLbInc;
+            int used = 0;
+            bool done = false;
+#pragma unroll
+            for (int q = 0; q < kLbBatch; ++q) {
+                if (done || used < q) continue;  // stop at the first word not yet published
+                const unsigned long long f = w[q] >> 62;
+                if (f == 0ull) continue;
+                prefix += (int64_t)(w[q] & kLbVal);
+                used = q + 1;
+                done = f == 2ull;
             }
-            prefix += (int64_t)(w & kLbVal);
-            if (f == 2ull) break;
-            --j;
+            if (done) break;
+            j -= used;
+            if (used == 0 && (++polls & 63u) == 0u && global_ns() - t0 > kSortWaitNs) {
+                *static_cast<volatile int*>(fault) = 1;
+                break;
+            }
         }
         atomicExch(my, kLbInc | (unsigned long long)(prefix + cnt));
     }
@@ -286,7 +345,8 @@ __global__ void __launch_bounds__(kThreads) k_os_pass(const K* __restrict__ keys
 }
 
 template <typename K, bool kVals>
-static void os_pass_launch(const K* src, const uint32_t* sv, K* dst, uint32_t* dv, int64_t n, int pass,
+static void os_pass_launch(const K* src, const uint32_t* sv, K* dst, uint32_t* dv, int64_t n, const int64_t* n_dev,
+                           int pass,
                            const unsigned long long* ghist, unsigned long long* st, unsigned long long* st_next,
                            unsigned long long* ticket, int* fault, cudaStream_t s) {
     constexpr size_t smem = (size_t)kRadixTile * (sizeof(K) + (kVals ? 4 : 0));
@@ -297,14 +357,14 @@ static void os_pass_launch(const K* src, const uint32_t* sv, K* dst, uint32_t* d
         DIM3_CUDA(cudaFuncSetAttribute(k_os_pass<K, kVals>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_done[dev & 63] = true;
     }
-    k_os_pass<K, kVals><<<(unsigned)ceil_div(n, kRadixTile), kThreads, smem, s>>>(src, sv, dst, dv, n, pass, ghist, st,
-                                                                                  st_next, ticket, fault);
+    k_os_pass<K, kVals><<<(unsigned)ceil_div(n, kRadixTile), kThreads, smem, s>>>(src, sv, dst, dv, n, n_dev, pass, ghist,
+                                                                                  st, st_next, ticket, fault);
     DIM3_LAUNCHED();
 }
 
 template <typename K>
 static void radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, int64_t n, int bits,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int64_t* n_dev) {
     if (n <= 1 || bits <= 0) return;
     const int passes = std::min<int>((bits + 7) / 8, (int)sizeof(K));
     const int64_t tiles = ceil_div(n, kRadixTile);
@@ -319,7 +379,7 @@ static void radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
     unsigned long long* st[2] = {ghist + (size_t)kMaxPasses * 256, ghist + (size_t)kMaxPasses * 256 + stw};
     DIM3_CUDA(cudaMemsetAsync(scratch.p, 0, (head + stw) * sizeof(unsigned long long), s));
     const unsigned hg = (unsigned)std::min<int64_t>(ceil_div(n, kThreads * 8), (int64_t)kSms * 8);
-    k_os_hist<K><<<hg, kThreads, 0, s>>>(keys, n, passes, ghist);
+    k_os_hist<K><<<hg, kThreads, 0, s>>>(keys, n, n_dev, passes, ghist);
     DIM3_LAUNCHED();
     K* src = keys;
     K* dst = keys_alt;
@@ -328,9 +388,10 @@ static void radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
     for (int p = 0; p < passes; ++p) {
         unsigned long long* next = p + 1 < passes ? st[(p + 1) & 1] : nullptr;
         if (vals)
-            os_pass_launch<K, true>(src, sv, dst, dv, n, p, ghist, st[p & 1], next, ticket + p, fault, s);
+            os_pass_launch<K, true>(src, sv, dst, dv, n, n_dev, p, ghist, st[p & 1], next, ticket + p, fault, s);
         else
-            os_pass_launch<K, false>(src, nullptr, dst, nullptr, n, p, ghist, st[p & 1], next, ticket + p, fault, s);
+            os_pass_launch<K, false>(src, nullptr, dst, nullptr, n, n_dev, p, ghist, st[p & 1], next, ticket + p, fault,
+                                     s);
         std::swap(src, dst);
         std::swap(sv, dv);
     }
@@ -342,20 +403,21 @@ static void radix_sort_impl(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals
 }
 
 void radix_sort_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                    int bits, cudaStream_t s) {
-    radix_sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, bits, s);
+                    int bits, cudaStream_t s, const int64_t* n_dev) {
+    radix_sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, bits, s, n_dev);
 }
 void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                    int bits, cudaStream_t s) {
-    radix_sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, s);
+                    int bits, cudaStream_t s, const int64_t* n_dev) {
+    radix_sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, s, n_dev);
 }
 
 // ------------------------------------------------------------------ unique
 template <typename K>
-__global__ void k_unique_flags(const K* in, int64_t n, int32_t* flags) {
+__global__ void k_unique_flags(const K* in, int64_t n, const int64_t* m_dev, int32_t* flags) {
+    const int64_t m = m_dev ? min64(n, *m_dev) : n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        flags[i] = (i == 0 || in[i] != in[i - 1]) ? 1 : 0;
+        flags[i] = (i < m && (i == 0 || in[i] != in[i - 1])) ? 1 : 0;
 }
 
 template <typename K>
@@ -366,13 +428,13 @@ __global__ void k_unique_scatter(const K* in, int64_t n, const int32_t* flags, c
 }
 
 template <typename K>
-static int64_t unique_impl(const K* in, K* out, int64_t n, cudaStream_t s) {
+static int64_t unique_impl(const K* in, K* out, int64_t n, cudaStream_t s, const int64_t* n_dev) {
     if (n == 0) return 0;
     DevBuf flags, pos;
     flags.alloc((size_t)n * sizeof(int32_t), s);
     pos.alloc(((size_t)n + 1) * sizeof(int64_t), s);
     unsigned g = (unsigned)std::min<int64_t>(ceil_div(n, kThreads), 8192);
-    k_unique_flags<K><<<g, kThreads, 0, s>>>(in, n, flags.as<int32_t>());
+    k_unique_flags<K><<<g, kThreads, 0, s>>>(in, n, n_dev, flags.as<int32_t>());
     DIM3_LAUNCHED();
     exclusive_scan_i32_to_i64(flags.as<int32_t>(), pos.as<int64_t>(), n, s);
     k_unique_scatter<K><<<g, kThreads, 0, s>>>(in, n, flags.as<int32_t>(), pos.as<int64_t>(), out);
@@ -380,36 +442,35 @@ static int64_t unique_impl(const K* in, K* out, int64_t n, cudaStream_t s) {
     return read_i64(pos.as<int64_t>() + n, s);
 }
 
-int64_t unique_sorted_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
-    return unique_impl<uint32_t>(in, out, n, s);
+int64_t unique_sorted_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s, const int64_t* n_dev) {
+    return unique_impl<uint32_t>(in, out, n, s, n_dev);
 }
-int64_t unique_sorted_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s) {
-    return unique_impl<uint64_t>(in, out, n, s);
+int64_t unique_sorted_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s, const int64_t* n_dev) {
+    return unique_impl<uint64_t>(in, out, n, s, n_dev);
 }
 
 // ----------------------------------------------------------------- rowptr
+// Position i (0..n) writes rowptr[r] = i for the rows r in (row(i-1), row(i)]
+// (row(-1) = -1, row(n) = n_rows): one coalesced pass over the keys, every
+// row pointer written once; rows without keys take the next row's start.
 template <typename K>
 __global__ void k_rowptr(const K* keys, int64_t n, int shift, int64_t n_rows, int64_t* rowptr) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= n_rows;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        int64_t lo = 0, hi = n;
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)(keys[mid] >> shift) < r) lo = mid + 1; else hi = mid;
-        }
-        rowptr[r] = lo;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t prev = i == 0 ? -1 : min64((int64_t)(keys[i - 1] >> shift), n_rows);
+        const int64_t cur = i == n ? n_rows : min64((int64_t)(keys[i] >> shift), n_rows);
+        for (int64_t r = prev + 1; r <= cur; ++r) rowptr[r] = i;
     }
 }
 
 void rowptr_from_sorted_u32(const uint32_t* keys, int64_t n, int shift, int64_t n_rows, int64_t* rowptr,
                             cudaStream_t s) {
-    unsigned g = (unsigned)std::min<int64_t>(ceil_div(n_rows + 1, kThreads), 8192);
+    unsigned g = (unsigned)std::min<int64_t>(ceil_div(n + 1, kThreads), 8192);
     k_rowptr<uint32_t><<<g, kThreads, 0, s>>>(keys, n, shift, n_rows, rowptr);
     DIM3_LAUNCHED();
 }
 void rowptr_from_sorted_u64(const uint64_t* keys, int64_t n, int shift, int64_t n_rows, int64_t* rowptr,
                             cudaStream_t s) {
-    unsigned g = (unsigned)std::min<int64_t>(ceil_div(n_rows + 1, kThreads), 8192);
+    unsigned g = (unsigned)std::min<int64_t>(ceil_div(n + 1, kThreads), 8192);
     k_rowptr<uint64_t><<<g, kThreads, 0, s>>>(keys, n, shift, n_rows, rowptr);
     DIM3_LAUNCHED();
 }
