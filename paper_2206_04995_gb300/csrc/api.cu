@@ -14,6 +14,9 @@ struct dim3_ctx {
     int last_path = 0;  // path of the last one-call join: 1 hybrid, 2 classical
     ~dim3_ctx() {
         stats.resolve();
+        if (c.aux) cudaStreamDestroy(c.aux);
+        if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+        if (c.ev_join) cudaEventDestroy(c.ev_join);
     }
 };
 
@@ -165,6 +168,9 @@ int dim3_ctx_create(dim3_ctx** out, int device) {
         DIM3_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
         uint64_t thr = UINT64_MAX;
         DIM3_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        DIM3_CUDA(cudaStreamCreateWithFlags(&c->c.aux, cudaStreamNonBlocking));
+        DIM3_CUDA(cudaEventCreateWithFlags(&c->c.ev_fork, cudaEventDisableTiming));
+        DIM3_CUDA(cudaEventCreateWithFlags(&c->c.ev_join, cudaEventDisableTiming));
         *out = c.release();
     });
 }

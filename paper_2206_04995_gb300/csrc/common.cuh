@@ -88,6 +88,9 @@ struct DevBuf {
         bytes = 0;
     }
     template <class T> T* as() const { return static_cast<T*>(p); }
+    // free in stream st's order from now on (after st has been made to wait
+    // for the stream the buffer was last used on)
+    void adopt(cudaStream_t st) { s = st; }
 };
 
 // ---------------------------------------------------------------- launchers
@@ -123,6 +126,12 @@ int64_t unique_sorted_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStre
                           const int64_t* n_dev = nullptr);
 int64_t unique_sorted_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s,
                           const int64_t* n_dev = nullptr);
+// Enqueue-only forms: no host read; the count is left on the device at the
+// returned address (inside pos, which the caller keeps alive).
+const int64_t* unique_sorted_u32_async(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s,
+                                       const int64_t* n_dev, DevBuf& pos);
+const int64_t* unique_sorted_u64_async(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s,
+                                       const int64_t* n_dev, DevBuf& pos);
 // rowptr[r] = first index i with (keys[i] >> shift) >= r, for r = 0..n_rows
 void rowptr_from_sorted_u32(const uint32_t* keys, int64_t n, int shift, int64_t n_rows,
                             int64_t* rowptr, cudaStream_t s);

@@ -179,6 +179,10 @@ struct PhaseScope {
 
 struct Ctx {
     Stats* stats = nullptr;  // owned by the ABI context
+    // second stream for independent steps (the z map runs beside the y and x
+    // maps), with the events that fork work onto it and join it back
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     int sm_count = 152;
     int smem_optin = 227 * 1024;

@@ -181,34 +181,57 @@ struct SortedPairs {
     int64_t n = 0;
 };
 
+// Distinct packed pairs, sorted, with their count still on the device
+// (everything enqueued, nothing read back).
 template <typename K>
-static void sort_unique_pairs(const int32_t* a, const int32_t* b, int64_t n, int shift, int bits,
-                              SortedPairs<K>& out, cudaStream_t s) {
-    DevBuf keys, alt, counter;
-    keys.alloc((size_t)std::max<int64_t>(n, 1) * sizeof(K), s);
-    counter.alloc(8, s);
-    DIM3_CUDA(cudaMemsetAsync(counter.p, 0, 8, s));
+struct PendingPairs {
+    DevBuf keys, alt, counter, pos;
+    const int64_t* count = nullptr;
+    void adopt(cudaStream_t st) {
+        keys.adopt(st);
+        alt.adopt(st);
+        counter.adopt(st);
+        pos.adopt(st);
+    }
+};
+
+template <typename K>
+static void sort_unique_pairs_enqueue(const int32_t* a, const int32_t* b, int64_t n, int shift, int bits,
+                                      PendingPairs<K>& pp, cudaStream_t s) {
+    pp.keys.alloc((size_t)std::max<int64_t>(n, 1) * sizeof(K), s);
+    pp.counter.alloc(8, s);
+    DIM3_CUDA(cudaMemsetAsync(pp.counter.p, 0, 8, s));
     if (n > 0) {
-        k_pack_pairs<K><<<grid_for(n), kThreads, 0, s>>>(a, b, n, shift, keys.as<K>(),
-                                                          counter.as<unsigned long long>());
+        k_pack_pairs<K><<<grid_for(n), kThreads, 0, s>>>(a, b, n, shift, pp.keys.template as<K>(),
+                                                          pp.counter.template as<unsigned long long>());
         DIM3_LAUNCHED();
     }
     // the count of packed pairs stays on the device: sort and unique take it
-    // from there, and the one host read is the unique count
-    const int64_t* m_dev = counter.as<int64_t>();
-    alt.alloc((size_t)std::max<int64_t>(n, 1) * sizeof(K), s);
-    if constexpr (sizeof(K) == 4)
-        radix_sort_u32(keys.as<uint32_t>(), nullptr, alt.as<uint32_t>(), nullptr, n, bits, s, m_dev);
-    else
-        radix_sort_u64(keys.as<uint64_t>(), nullptr, alt.as<uint64_t>(), nullptr, n, bits, s, m_dev);
-    // unique into alt, then keep alt
-    int64_t u;
-    if constexpr (sizeof(K) == 4)
-        u = unique_sorted_u32(keys.as<uint32_t>(), alt.as<uint32_t>(), n, s, m_dev);
-    else
-        u = unique_sorted_u64(keys.as<uint64_t>(), alt.as<uint64_t>(), n, s, m_dev);
-    out.keys = std::move(alt);
-    out.n = u;
+    // from there
+    const int64_t* m_dev = pp.counter.template as<int64_t>();
+    pp.alt.alloc((size_t)std::max<int64_t>(n, 1) * sizeof(K), s);
+    if constexpr (sizeof(K) == 4) {
+        radix_sort_u32(pp.keys.template as<uint32_t>(), nullptr, pp.alt.template as<uint32_t>(), nullptr, n, bits, s, m_dev);
+        pp.count = unique_sorted_u32_async(pp.keys.template as<uint32_t>(), pp.alt.template as<uint32_t>(), n, s, m_dev, pp.pos);
+    } else {
+        radix_sort_u64(pp.keys.template as<uint64_t>(), nullptr, pp.alt.template as<uint64_t>(), nullptr, n, bits, s, m_dev);
+        pp.count = unique_sorted_u64_async(pp.keys.template as<uint64_t>(), pp.alt.template as<uint64_t>(), n, s, m_dev, pp.pos);
+    }
+}
+
+// One host read: the unique pairs end in out (the unique keys are in alt).
+template <typename K>
+static void sort_unique_pairs_finish(PendingPairs<K>& pp, SortedPairs<K>& out, cudaStream_t s) {
+    out.n = read_i64(pp.count, s);
+    out.keys = std::move(pp.alt);
+}
+
+template <typename K>
+static void sort_unique_pairs(const int32_t* a, const int32_t* b, int64_t n, int shift, int bits,
+                              SortedPairs<K>& out, cudaStream_t s) {
+    PendingPairs<K> pp;
+    sort_unique_pairs_enqueue<K>(a, b, n, shift, bits, pp, s);
+    sort_unique_pairs_finish<K>(pp, out, s);
 }
 
 template <typename K>
@@ -238,14 +261,19 @@ static void build_r_side(Plan& p, const int32_t* rx_id, const int32_t* ry_id, in
 }
 
 // S side: everything that depends on the distinct S tuples sorted by (y, z).
+// pending: the (y, z) pairs already sorted (on any stream that s has been
+// made to wait for), or null to sort them here.
 template <typename K>
 static void build_s_side(const Ctx& ctx, Plan& p, const int32_t* sy_id, const int32_t* sz_id, int64_t ns,
                          int by, int bz, int64_t theta, const int32_t* y_tag_dev, const int32_t* z_tag_dev,
-                         cudaStream_t s) {
+                         cudaStream_t s, PendingPairs<K>* pending = nullptr) {
     const int64_t n_y = p.info.n_y, n_z = p.info.n_z, n_x = p.info.n_x;
     const K zmask = (K)((K(1) << bz) - 1);
     SortedPairs<K> sp;
-    sort_unique_pairs<K>(sy_id, sz_id, ns, bz, by + bz, sp, s);
+    if (pending)
+        sort_unique_pairs_finish<K>(*pending, sp, s);
+    else
+        sort_unique_pairs<K>(sy_id, sz_id, ns, bz, by + bz, sp, s);
     p.info.n_s_distinct = sp.n;
     const K* keys = sp.keys.template as<K>();
 
@@ -548,6 +576,55 @@ __global__ void k_sum_deg(const int32_t* __restrict__ ids, int64_t n, const unsi
     if (threadIdx.x == 0 && acc) atomicAdd(total, acc);
 }
 
+// Makes stream s wait on an event recorded on another stream: at join(), or
+// when it goes out of scope (also while an exception unwinds).
+struct StreamJoin {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    void arm(cudaStream_t st, cudaEvent_t e) {
+        s = st;
+        ev = e;
+    }
+    void join() {
+        if (ev) cudaStreamWaitEvent(s, ev, 0);
+        ev = nullptr;
+    }
+    ~StreamJoin() { join(); }
+};
+
+struct SideArgs {
+    const int32_t *rx, *ry;
+    int64_t nr;
+    const int32_t *sy, *sz;
+    int64_t ns;
+    int bx, by, bz;
+    int64_t theta_z;
+    const int32_t *y_tag, *z_tag;
+};
+
+// R_CSR and the S side; the (y, z) pairs are sorted on the context's second
+// stream while the R side is built on s.
+template <typename KR, typename KS>
+static void build_sides(const Ctx& ctx, Plan& p, const SideArgs& a, cudaStream_t s) {
+    PendingPairs<KS> spp;
+    StreamJoin sjoin;
+    cudaStream_t ss = s;
+    if (ctx.aux && ctx.ev_fork && ctx.ev_join) {
+        DIM3_CUDA(cudaEventRecord(ctx.ev_fork, s));
+        DIM3_CUDA(cudaStreamWaitEvent(ctx.aux, ctx.ev_fork, 0));
+        ss = ctx.aux;
+    }
+    sort_unique_pairs_enqueue<KS>(a.sy, a.sz, a.ns, a.bz, a.by + a.bz, spp, ss);
+    if (ss != s) {
+        DIM3_CUDA(cudaEventRecord(ctx.ev_join, ss));
+        sjoin.arm(s, ctx.ev_join);
+    }
+    build_r_side<KR>(p, a.rx, a.ry, a.nr, a.bx, a.by, s);
+    sjoin.join();
+    spp.adopt(s);
+    build_s_side<KS>(ctx, p, a.sy, a.sz, a.ns, a.by, a.bz, a.theta_z, a.y_tag, a.z_tag, s, &spp);
+}
+
 Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStream_t s, bool* prefer_classical) {
     PhaseScope phase(ctx.stats, PH_PARTITION, s);
     std::unique_ptr<Plan> p(new Plan());
@@ -581,11 +658,30 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
             p->x_tag.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
         }
         // The three maps leave their distinct counts on the device; they are
-        // read together (with f1's |OUT_J| when that is asked for).
+        // read together (with f1's |OUT_J| when that is asked for). The z map
+        // depends on neither of the others and runs on the context's second
+        // stream meanwhile; `zjoin` makes s wait for it before anything that
+        // reads its results, and on every way out of this block (buffers the
+        // z map writes are freed in s's order).
         ValueMap ymap, xmap, zmap;
+        p->dict_y.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+        p->dict_x.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
+        p->dict_z.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
+        StreamJoin zjoin;
+        cudaStream_t zs = s;
+        if (ctx.aux && ctx.ev_fork && ctx.ev_join) {
+            DIM3_CUDA(cudaEventRecord(ctx.ev_fork, s));
+            DIM3_CUDA(cudaStreamWaitEvent(ctx.aux, ctx.ev_fork, 0));
+            zs = ctx.aux;
+        }
+        build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(), p->dict_z.as<int32_t>(),
+                        z_tag.as<int32_t>(), zs, false);
+        if (zs != s) {
+            DIM3_CUDA(cudaEventRecord(ctx.ev_join, zs));
+            zjoin.arm(s, ctx.ev_join);
+        }
         {
             // y from S.y; R tuples whose y is absent from S.y get id -1 (dropped)
-            p->dict_y.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
             build_value_map(in.s_key, in.s_tag, p->n_inst, nullptr, ns, ymap, sy_id.as<int32_t>(),
                             p->dict_y.as<int32_t>(), y_tag.as<int32_t>(), s, false);
             probe_value_map(ymap, in.r_key, in.r_tag, nr, ry_id.as<int32_t>(), s);
@@ -612,12 +708,9 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
             *prefer_classical = f1_value(nr, ns, out_j, ctx.opt.f1c) > 0.0;
             if (*prefer_classical) return nullptr;
         }
-        p->dict_x.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
         build_value_map(in.r_val, in.r_tag, p->n_inst, ry_id.as<int32_t>(), nr, xmap, rx_id.as<int32_t>(),
                         p->dict_x.as<int32_t>(), p->x_tag.as<int32_t>(), s, false);
-        p->dict_z.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
-        build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(),
-                        p->dict_z.as<int32_t>(), z_tag.as<int32_t>(), s, false);
+        zjoin.join();
         ValueMap* maps[3] = {&ymap, &xmap, &zmap};
         resolve_counts(maps, 3, nullptr, nullptr, s);
         DIM3_REQUIRE(ymap.n_distinct >= 0 && ymap.n_distinct <= ns && xmap.n_distinct >= 0 &&
@@ -637,14 +730,14 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
     instance_ranges(p->x_tag.as<int32_t>(), p->info.n_x, p->n_inst, p->inst_x_lo, p->h_inst_x_lo, s);
     instance_ranges(z_tag.as<int32_t>(), p->info.n_z, p->n_inst, p->inst_z_lo, p->h_inst_z_lo, s);
     const int bx = bits_for(p->info.n_x), by = bits_for(p->info.n_y), bz = bits_for(p->info.n_z);
-    if (bx + by <= 32)
-        build_r_side<uint32_t>(*p, rx, ry, nr, bx, by, s);
-    else
-        build_r_side<uint64_t>(*p, rx, ry, nr, bx, by, s);
-    if (by + bz <= 32)
-        build_s_side<uint32_t>(ctx, *p, sy, sz, ns, by, bz, theta_z, y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
-    else
-        build_s_side<uint64_t>(ctx, *p, sy, sz, ns, by, bz, theta_z, y_tag.as<int32_t>(), z_tag.as<int32_t>(), s);
+    const SideArgs sa{rx, ry, nr, sy, sz, ns, bx, by, bz, theta_z, y_tag.as<int32_t>(), z_tag.as<int32_t>()};
+    if (bx + by <= 32) {
+        if (by + bz <= 32) build_sides<uint32_t, uint32_t>(ctx, *p, sa, s);
+        else build_sides<uint32_t, uint64_t>(ctx, *p, sa, s);
+    } else {
+        if (by + bz <= 32) build_sides<uint64_t, uint32_t>(ctx, *p, sa, s);
+        else build_sides<uint64_t, uint64_t>(ctx, *p, sa, s);
+    }
     if (in.cache) finish_cache_index(*p, s);
     if (batch) p->y_tag = std::move(y_tag);
     DIM3_CUDA(cudaStreamSynchronize(s));

@@ -428,18 +428,38 @@ __global__ void k_unique_scatter(const K* in, int64_t n, const int32_t* flags, c
 }
 
 template <typename K>
-static int64_t unique_impl(const K* in, K* out, int64_t n, cudaStream_t s, const int64_t* n_dev) {
-    if (n == 0) return 0;
-    DevBuf flags, pos;
-    flags.alloc((size_t)n * sizeof(int32_t), s);
+static const int64_t* unique_enqueue(const K* in, K* out, int64_t n, cudaStream_t s, const int64_t* n_dev,
+                                     DevBuf& pos) {
     pos.alloc(((size_t)n + 1) * sizeof(int64_t), s);
+    if (n == 0) {
+        fill_i64(pos.as<int64_t>(), 0, 1, s);
+        return pos.as<int64_t>();
+    }
+    DevBuf flags;
+    flags.alloc((size_t)n * sizeof(int32_t), s);
     unsigned g = (unsigned)std::min<int64_t>(ceil_div(n, kThreads), 8192);
     k_unique_flags<K><<<g, kThreads, 0, s>>>(in, n, n_dev, flags.as<int32_t>());
     DIM3_LAUNCHED();
     exclusive_scan_i32_to_i64(flags.as<int32_t>(), pos.as<int64_t>(), n, s);
     k_unique_scatter<K><<<g, kThreads, 0, s>>>(in, n, flags.as<int32_t>(), pos.as<int64_t>(), out);
     DIM3_LAUNCHED();
-    return read_i64(pos.as<int64_t>() + n, s);
+    return pos.as<int64_t>() + n;
+}
+
+template <typename K>
+static int64_t unique_impl(const K* in, K* out, int64_t n, cudaStream_t s, const int64_t* n_dev) {
+    if (n == 0) return 0;
+    DevBuf pos;
+    return read_i64(unique_enqueue<K>(in, out, n, s, n_dev, pos), s);
+}
+
+const int64_t* unique_sorted_u32_async(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s,
+                                       const int64_t* n_dev, DevBuf& pos) {
+    return unique_enqueue<uint32_t>(in, out, n, s, n_dev, pos);
+}
+const int64_t* unique_sorted_u64_async(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s,
+                                       const int64_t* n_dev, DevBuf& pos) {
+    return unique_enqueue<uint64_t>(in, out, n, s, n_dev, pos);
 }
 
 int64_t unique_sorted_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s, const int64_t* n_dev) {
