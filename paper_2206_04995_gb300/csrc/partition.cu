@@ -663,28 +663,38 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
         // stream meanwhile; `zjoin` makes s wait for it before anything that
         // reads its results, and on every way out of this block (buffers the
         // z map writes are freed in s's order).
+        //
+        // A self-join (R and S given by the same column pointers) maps once:
+        // every R.y occurs in S.y, so R's y ids are S's, no tuple is dropped,
+        // and the x map (over R.x) is the z map (over S.z).
+        const bool self_join = in.r_key == in.s_key && in.r_val == in.s_val && nr == ns && in.r_tag == in.s_tag;
         ValueMap ymap, xmap, zmap;
         p->dict_y.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
         p->dict_x.alloc((size_t)std::max<int64_t>(nr, 1) * 4, s);
         p->dict_z.alloc((size_t)std::max<int64_t>(ns, 1) * 4, s);
         StreamJoin zjoin;
-        cudaStream_t zs = s;
-        if (ctx.aux && ctx.ev_fork && ctx.ev_join) {
-            DIM3_CUDA(cudaEventRecord(ctx.ev_fork, s));
-            DIM3_CUDA(cudaStreamWaitEvent(ctx.aux, ctx.ev_fork, 0));
-            zs = ctx.aux;
-        }
-        build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(), p->dict_z.as<int32_t>(),
-                        z_tag.as<int32_t>(), zs, false);
-        if (zs != s) {
-            DIM3_CUDA(cudaEventRecord(ctx.ev_join, zs));
-            zjoin.arm(s, ctx.ev_join);
+        if (!self_join) {
+            cudaStream_t zs = s;
+            if (ctx.aux && ctx.ev_fork && ctx.ev_join) {
+                DIM3_CUDA(cudaEventRecord(ctx.ev_fork, s));
+                DIM3_CUDA(cudaStreamWaitEvent(ctx.aux, ctx.ev_fork, 0));
+                zs = ctx.aux;
+            }
+            build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(),
+                            p->dict_z.as<int32_t>(), z_tag.as<int32_t>(), zs, false);
+            if (zs != s) {
+                DIM3_CUDA(cudaEventRecord(ctx.ev_join, zs));
+                zjoin.arm(s, ctx.ev_join);
+            }
         }
         {
             // y from S.y; R tuples whose y is absent from S.y get id -1 (dropped)
             build_value_map(in.s_key, in.s_tag, p->n_inst, nullptr, ns, ymap, sy_id.as<int32_t>(),
                             p->dict_y.as<int32_t>(), y_tag.as<int32_t>(), s, false);
-            probe_value_map(ymap, in.r_key, in.r_tag, nr, ry_id.as<int32_t>(), s);
+            if (self_join)
+                DIM3_CUDA(cudaMemcpyAsync(ry_id.p, sy_id.p, (size_t)nr * 4, cudaMemcpyDeviceToDevice, s));
+            else
+                probe_value_map(ymap, in.r_key, in.r_tag, nr, ry_id.as<int32_t>(), s);
         }
         if (prefer_classical) {
             // f1 (Section 2.6) from the y ids just made: |OUT_J| of the bags
@@ -712,7 +722,15 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
                         p->dict_x.as<int32_t>(), p->x_tag.as<int32_t>(), s, false);
         zjoin.join();
         ValueMap* maps[3] = {&ymap, &xmap, &zmap};
-        resolve_counts(maps, 3, nullptr, nullptr, s);
+        resolve_counts(maps, self_join ? 2 : 3, nullptr, nullptr, s);
+        if (self_join) {
+            zmap.n_distinct = xmap.n_distinct;
+            const size_t b = (size_t)std::max<int64_t>(ns, 1) * 4;
+            DIM3_CUDA(cudaMemcpyAsync(sz_id.p, rx_id.p, b, cudaMemcpyDeviceToDevice, s));
+            DIM3_CUDA(cudaMemcpyAsync(p->dict_z.p, p->dict_x.p, (size_t)std::max<int64_t>(xmap.n_distinct, 1) * 4,
+                                      cudaMemcpyDeviceToDevice, s));
+            if (batch) DIM3_CUDA(cudaMemcpyAsync(z_tag.p, p->x_tag.p, b, cudaMemcpyDeviceToDevice, s));
+        }
         DIM3_REQUIRE(ymap.n_distinct >= 0 && ymap.n_distinct <= ns && xmap.n_distinct >= 0 &&
                          xmap.n_distinct <= nr && zmap.n_distinct >= 0 && zmap.n_distinct <= ns,
                      DIM3_ERR_CUDA, "value map: inconsistent distinct count");

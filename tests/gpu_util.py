@@ -13,8 +13,13 @@ def host(t: torch.Tensor) -> np.ndarray:
     return t.detach().cpu().numpy()
 
 
-def inst_dev(inst):
-    return dev(inst.r_key), dev(inst.r_val), dev(inst.s_key), dev(inst.s_val)
+def inst_dev(inst, share_self: bool = True):
+    """Device columns of an instance; a self-join's S columns are R's tensors
+    (the library then maps once) unless share_self is False."""
+    rk, rv = dev(inst.r_key), dev(inst.r_val)
+    if inst.self_join and share_self:
+        return rk, rv, rk, rv
+    return rk, rv, dev(inst.s_key), dev(inst.s_val)
 
 
 def rows_of(out_x: torch.Tensor, out_z: torch.Tensor, xs: np.ndarray, out_c: torch.Tensor | None = None):

@@ -163,6 +163,38 @@ def test_chung_lu_small(ctx):
     assert_count(ctx, inst)
 
 
+@pytest.mark.parametrize("which", ["cfg1", "chung_lu", "dups"])
+@pytest.mark.parametrize("theta", [-1, 4])
+def test_self_join_shared_pointers(ctx, which, theta):
+    """R and S given by the same tensors (the library maps once) and by
+    separate copies give the same plan sizes and results, equal to the oracle."""
+    if which == "cfg1":
+        inst = gen.config1_self()
+    elif which == "chung_lu":
+        inst = gen.chung_lu_self(np.random.default_rng(11), 5_000, 20_000, 2.1)
+    else:
+        inst = gen.small_two_table(21, 3000, 3000, 300, 300, 150, dup_frac=0.2, self_join=True)
+    assert inst.self_join
+    shared = inst_dev(inst)
+    assert shared[0].data_ptr() == shared[2].data_ptr()
+    separate = inst_dev(inst, share_self=False)
+    infos = []
+    for cols in (shared, separate):
+        plan = ctx.partition(*cols, theta_z=theta)
+        try:
+            infos.append({k: plan.info[k] for k in ("n_x", "n_y", "n_z", "out_j", "n_z_dense", "n_s_sparse")})
+        finally:
+            plan.close()
+    assert infos[0] == infos[1] and infos[0]["n_x"] == infos[0]["n_z"]
+    ox, oz, oc = oracle.join_count(inst.r_key, inst.r_val, inst.s_key, inst.s_val)[:3]
+    for cols in (shared, separate):
+        x, z, c = ctx.join_count(*cols)
+        assert np.array_equal(host(x), ox) and np.array_equal(host(z), oz)
+        assert np.array_equal(host(c), oc.astype(np.int32))
+        x, z = ctx.join_project(*cols)
+        assert np.array_equal(host(x), ox) and np.array_equal(host(z), oz)
+
+
 # ------------------------------------------- invariance to split and variants
 @pytest.mark.parametrize("variant", [dim3.DENSE_TC, dim3.DENSE_POPC, dim3.DENSE_PROBE])
 @pytest.mark.parametrize("theta", [0, 5, 40, 1 << 30])
