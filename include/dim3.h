@@ -26,7 +26,16 @@
  * - Sizes are int64. Null pointers with a nonzero size, or negative sizes,
  *   give DIM3_ERR_ARG. n = 0 is legal and yields an empty result.
  * - A context is bound to one device and may be used by one host thread at
- *   a time.
+ *   a time. It owns a second stream on which independent partition steps
+ *   (the z mapping, the (y, z) pair sort) run beside the caller's stream;
+ *   the caller's stream is made to wait for them before the call returns or
+ *   enqueues anything that reads their results.
+ * - Bounded device waits (decoupled look-back of sorts and of the one-pass
+ *   compaction, tensor-core pipeline barriers) give up after 2 s; the call
+ *   that observes it returns DIM3_ERR_TIMEOUT.
+ * - Self-joins: when R and S are passed as the same column pointers, the
+ *   values are mapped once (the x map serves as the z map). Results equal
+ *   those of separate copies of the same tables.
  */
 #ifndef DIM3_H
 #define DIM3_H
