@@ -166,6 +166,7 @@ static void collect_sort_rank(ValueMap& vm, int64_t cap, int64_t n, int tag_bits
 }
 
 int64_t resolve_counts(ValueMap* const* maps, int n_maps, const int64_t* extra, int64_t* extra_out, cudaStream_t s) {
+    DIM3_REQUIRE(n_maps >= 0 && n_maps <= 7, DIM3_ERR_ARG, "resolve_counts: at most 7 maps");
     const int64_t* src[8];
     int64_t got[8];
     int k = 0;
