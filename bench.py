@@ -62,6 +62,9 @@ def parse_args():
     ap.add_argument("--mjp", type=int, default=0,
                     help="k: time the k-hop line query Pi(E join ... join E) (Section 4.2) on the workload's "
                          "edges, with the DP's deduplication placement and the two baseline plans")
+    ap.add_argument("--f1-sweep", action="store_true",
+                    help="Section 2.6's f1 on 1M x 1M uniform tables over a range of N_Y: one JSON line per "
+                         "point with the forced hybrid and classical times and f1's choice")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -272,6 +275,9 @@ def main():
         return
     if args.mjp:
         run_mjp(args, rank, world, local_rank)
+        return
+    if args.f1_sweep:
+        run_f1_sweep(args, local_rank)
         return
 
     import torch
@@ -768,6 +774,57 @@ def dataclasses_replace(q):
     import dataclasses
 
     return dataclasses.replace(q)
+
+
+def run_f1_sweep(args, local_rank):
+    """f1 (Section 2.6) against measurement: |R| = |S| = 1e6 tuples, x and z
+    uniform over [-1e8, 1e8), y uniform over [0, N_Y); for each N_Y one
+    dim3_join_project into caller-sized buffers, best of `--steps` calls
+    after `--warmup`, with the path forced hybrid, forced classical, and left
+    to f1 (default constants). Prints one JSON line per N_Y."""
+    import torch
+
+    import paper_2206_04995_gb300 as dim3
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(local_rank)
+    n = 1_000_000
+    for ny in (3 * 10**3, 10**4, 3 * 10**4, 10**5, 3 * 10**5, 10**6, 10**7, 10**8):
+        rng = np.random.default_rng(0)
+        cols = [torch.from_numpy(a.astype(np.int32)).to(dev) for a in
+                (rng.integers(0, ny, n), rng.integers(-10**8, 10**8, n), rng.integers(0, ny, n),
+                 rng.integers(-10**8, 10**8, n))]
+        ctx = dim3.Context(local_rank)
+        plan = ctx.partition(*cols)
+        out_j = int(plan.info["out_j"])
+        out_p = int(plan.row_counts().sum().item())
+        plan.close()
+        ox = torch.empty(max(out_p, 1), dtype=torch.int32, device=dev)
+        oz = torch.empty_like(ox)
+        line = {"n_r": n, "n_s": n, "n_y": ny, "out_j": out_j, "out_p": out_p}
+        for path, name in ((dim3.PATH_HYBRID, "hybrid_ms"), (dim3.PATH_CLASSICAL, "classical_ms"),
+                           (dim3.PATH_AUTO, "f1_ms")):
+            ctx.set_option(dim3.OPT_PATH, path)
+            for _ in range(args.warmup):
+                ctx.join_project(*cols, out_x=ox, out_z=oz)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(max(args.steps, 1)):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                x, _ = ctx.join_project(*cols, out_x=ox, out_z=oz)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+                assert x.numel() == out_p
+            line[name] = round(best, 4)
+            if path == dim3.PATH_AUTO:
+                line["f1_chose"] = "hybrid" if ctx.last_path() == 1 else "classical"
+        print(json.dumps(line), flush=True)
+        ctx.close()
+        del ox, oz
+        torch.cuda.empty_cache()
 
 
 def device_columns(torch, host_cols, dev):
