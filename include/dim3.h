@@ -151,13 +151,16 @@ typedef enum {
     DIM3_PHASE_DENSE_TC = 5      /* the tcgen05 DenseEC kernel alone (inside DIM3_PHASE_DENSE_EC) */
 } dim3_phase;
 
-/* Library version as major*10000 + minor*100 + patch. */
+/* Library version as major*10000 + minor*100 + patch (library plumbing; no
+ * passage of the paper). */
 DIM3_API int dim3_version(void);
 
 /* Message of the last failed call on this host thread ("" if none). */
 DIM3_API const char *dim3_last_error(void);
 
-/* Create a context on CUDA device `device`. *out receives the handle. */
+/* Create a context on CUDA device `device`. *out receives the handle.
+ * Contexts, options, timing and errors are library plumbing: the paper's
+ * Algorithm 1 defines the steps they drive, not these calls. */
 DIM3_API int dim3_ctx_create(dim3_ctx **out, int device);
 
 /* Destroy a context. Plans made with it must be destroyed first. */
@@ -210,8 +213,9 @@ DIM3_API int dim3_map(dim3_ctx *ctx, const int32_t *d_vals, int64_t n, int32_t *
  * dim3_map_noalloc -- dim3_map for callers that may not allocate device
  * memory (a host engine that fixed its GPU memory budget at start-up and
  * forbids later allocations, code living under another framework's allocator,
- * or latency-critical code that must not enter the allocator). The paper has
- * no counterpart: it is an interface variant, not a step of the method.
+ * or latency-critical code that must not enter the allocator). It computes
+ * the mapping of Section 2.2 (rank ids, as dim3_map); the allocation-free
+ * form is an interface variant with no counterpart in the paper.
  *   d_vals, d_ids, d_dict, n_distinct: as for dim3_map; n <= 65536.
  * No context. Runs on the current device and stream. All scratch lives in one
  * fixed 2,883,840-byte device array inside the library (held by every GPU
@@ -284,7 +288,8 @@ DIM3_API int dim3_map_tuples(dim3_ctx *ctx, const int32_t *const *d_cols, int k,
 /*
  * dim3_gather_i32 -- d_dst[i] = d_src[d_idx[i]] for i < n (int32 device
  * arrays; d_src has n_src entries). Translates ids back to attribute values
- * through dim3_map_tuples' d_first. An index outside [0, n_src) gives
+ * through dim3_map_tuples' d_first (the inverse of the multi-attribute
+ * mapping of Section 2.2). An index outside [0, n_src) gives
  * DIM3_ERR_ARG, with d_dst[i] = -1 there. Synchronises the stream.
  */
 DIM3_API int dim3_gather_i32(dim3_ctx *ctx, const int32_t *d_src, int64_t n_src, const int32_t *d_idx, int64_t n,
@@ -329,8 +334,8 @@ DIM3_API int dim3_cache_build(dim3_ctx *ctx, const int32_t *d_r_key, const int32
                               dim3_cache_info *info, void *stream);
 
 /*
- * dim3_cache_export -- copy a cache's entries to device buffers sized from
- * its info: d_z [n_entries] int32 (ascending z values), d_size [n_entries]
+ * dim3_cache_export -- copy a cache's entries (Section 3: per cached z, its
+ * x list or the complement of it in X) to device buffers sized from its info: d_z [n_entries] int32 (ascending z values), d_size [n_entries]
  * int64 (k, or k - |X| for a complement entry), d_complement [n_entries]
  * uint8 (1 = complement; also marks k = |X|, whose size is 0), d_offsets
  * [n_entries + 1] int64, d_xs [n_list] int32 (entry e's x values, ascending,
@@ -339,11 +344,13 @@ DIM3_API int dim3_cache_build(dim3_ctx *ctx, const int32_t *d_r_key, const int32
 DIM3_API int dim3_cache_export(dim3_ctx *ctx, const dim3_cache *cache, int32_t *d_z, int64_t *d_size,
                                uint8_t *d_complement, int64_t *d_offsets, int32_t *d_xs, void *stream);
 
+/* Free a cache's device memory (Section 3's cache; stream-ordered). */
 DIM3_API int dim3_cache_destroy(dim3_cache *cache);
 
 /*
  * dim3_partition_cached -- dim3_partition with a cache built on the same
- * tables: the dictionaries are those of the full tables, the S tuples of
+ * tables (Section 3: cached z are left out of S_sparse and S_dense and their
+ * stored results are output in addition): the dictionaries are those of the full tables, the S tuples of
  * cached z are dropped after mapping, and the plan's Join-Project results
  * include the cached pairs (info.n_z_cached = entries). Join-Count on such a
  * plan gives DIM3_ERR_UNSUPPORTED (the cache holds pairs, not counts). A
@@ -420,13 +427,15 @@ DIM3_API int dim3_mjp_plan(int k, const double *r_size, const double *out_j, con
 DIM3_API int dim3_mjp_execute(dim3_ctx *ctx, int k, const dim3_edge_table *tables, const int *dedup,
                               int32_t *d_out_x, int32_t *d_out_z, int64_t capacity, int64_t *count, void *stream);
 
-/* Copy of the plan's sizes. */
+/* Copy of the plan's sizes: |X|, |Y|, |Z|, |Z_dense|, |OUT_J| and the other
+ * quantities of Algorithm 1's partition steps (Sections 2.2-2.4). */
 DIM3_API int dim3_plan_get_info(const dim3_plan *plan, dim3_plan_info *info);
 
 /*
  * dim3_plan_row_counts -- per-x output sizes for the x-id range
  * [x_begin, x_end): d_counts[i] = |{z : (x_begin + i, z) in result}|
- * (int64 device, x_end - x_begin entries). Useful to size x-range chunks.
+ * (int64 device, x_end - x_begin entries): the per-x popcounts of the union
+ * of Algorithm 1's sparse and dense results. Useful to size x-range chunks.
  */
 DIM3_API int dim3_plan_row_counts(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,
                          int64_t *d_counts, void *stream);
@@ -504,10 +513,13 @@ typedef enum {
     DIM3_TABLE_OUTJ_X = 11    /* int64 [n_x]   join tuples per x: sum over y in R[x] of deg_S(y) */
 } dim3_table;
 
-/* Copy table `which` into d_dst (device), which holds `bytes` bytes. */
+/* Copy table `which` (a structure of Algorithm 1: dictionaries, R_CSR,
+ * S_sparse, degrees, the dense split) into d_dst (device), which holds
+ * `bytes` bytes. */
 DIM3_API int dim3_plan_export(dim3_plan *plan, int which, void *d_dst, int64_t bytes, void *stream);
 
-/* Free a plan's device tables (stream-ordered on the plan's stream). */
+/* Free a plan's device tables (stream-ordered on the plan's stream; library
+ * plumbing). */
 DIM3_API int dim3_plan_destroy(dim3_plan *plan);
 
 /*
