@@ -166,6 +166,16 @@ DIM3_API int dim3_ctx_create(dim3_ctx **out, int device);
 /* Destroy a context. Plans made with it must be destroyed first. */
 DIM3_API int dim3_ctx_destroy(dim3_ctx *ctx);
 
+/*
+ * dim3_selftest_wait_timeout -- failure detection without a GPU fault: one
+ * warp runs the decoupled look-back of the one-pass compaction against a
+ * predecessor that never publishes, with a limit of `seconds` (0 < seconds
+ * <= 2). Returns DIM3_ERR_TIMEOUT when the wait gave up and reported it (the
+ * expected outcome; the context stays usable), DIM3_ERR_CUDA if it did not.
+ * Synchronises the stream. Library plumbing, not a step of the paper.
+ */
+DIM3_API int dim3_selftest_wait_timeout(dim3_ctx *ctx, double seconds, void *stream);
+
 /* Set a dim3_option. Returns DIM3_ERR_ARG for an unknown option. */
 DIM3_API int dim3_ctx_set_option(dim3_ctx *ctx, int option, int64_t value);
 

@@ -13,6 +13,14 @@ from .dim3 import (  # noqa: F401
     AGG_MAX,
     AGG_MIN,
     AGG_SUM,
+    DIM3_ERR_ARG,
+    DIM3_ERR_CAPACITY,
+    DIM3_ERR_CUDA,
+    DIM3_ERR_NOMEM,
+    DIM3_ERR_OVERFLOW,
+    DIM3_ERR_TIMEOUT,
+    DIM3_ERR_UNSUPPORTED,
+    DIM3_OK,
     DENSE_AUTO,
     DENSE_POPC,
     DENSE_PROBE,

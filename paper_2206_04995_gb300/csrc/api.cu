@@ -175,6 +175,16 @@ int dim3_ctx_create(dim3_ctx** out, int device) {
     });
 }
 
+int dim3_selftest_wait_timeout(dim3_ctx* ctx, double seconds, void* stream) {
+    return guarded([&] {
+        DIM3_REQUIRE(ctx, DIM3_ERR_ARG, "ctx is null");
+        DeviceGuard g(ctx->c.device);
+        const int gave_up = dimcube::wait_selftest(seconds, as_stream(stream));
+        DIM3_REQUIRE(gave_up, DIM3_ERR_CUDA, "self-test: the bounded wait did not report giving up");
+        throw dimcube::Error(DIM3_ERR_TIMEOUT, "self-test: the bounded wait gave up as intended");
+    });
+}
+
 int dim3_ctx_destroy(dim3_ctx* ctx) {
     return guarded([&] { delete ctx; });
 }

@@ -190,6 +190,10 @@ struct Ctx {
     Options opt;
 };
 
+// Bounded-wait self-test (selftest.cu): 1 if a look-back whose predecessor
+// never publishes gave up after `seconds` and reported it, else 0.
+int wait_selftest(double seconds, cudaStream_t s);
+
 // prefer_classical non-null (a single instance of value columns): after the
 // y mapping, evaluate f1 (Section 2.6); when it favours the classical
 // solution, set *prefer_classical and return nullptr without finishing.

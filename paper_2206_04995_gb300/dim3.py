@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True):
                                     ctypes.POINTER(PlanInfo), P], INT),
             "dim3_map_tuples": ([P, P, ctypes.c_int, ctypes.c_uint32, I64, P, P, ctypes.POINTER(I64), P], INT),
             "dim3_gather_i32": ([P, P, I64, P, I64, P, P], INT),
+            "dim3_selftest_wait_timeout": ([P, ctypes.c_double, P], INT),
             "dim3_ctx_set_f1_costs": ([P, ctypes.c_double, ctypes.c_double, ctypes.c_double], INT),
             "dim3_ctx_last_path": ([P], INT),
             "dim3_join_aggregate": ([P, P, P, P, I64, P, P, P, I64, ctypes.c_int, ctypes.c_int, P, P, P, I64,
@@ -240,6 +241,11 @@ class Context:
         _check(self._lib.dim3_map_tuples(self._h, ptrs, len(cols), int(unsigned_mask) & 0xFFFFFFFF, n, _ptr(ids),
                                          _ptr(first), ctypes.byref(nd), _stream(self.device, stream)))
         return ids, first[: nd.value]
+
+    def selftest_wait_timeout(self, seconds: float = 0.05, stream=None) -> int:
+        """Run ``dim3_selftest_wait_timeout``; returns its status (DIM3_ERR_TIMEOUT
+        when the bounded wait gave up as intended)."""
+        return self._lib.dim3_selftest_wait_timeout(self._h, float(seconds), _stream(self.device, stream))
 
     def gather(self, src, idx, stream=None):
         """src[idx] through ``dim3_gather_i32`` (int32)."""
