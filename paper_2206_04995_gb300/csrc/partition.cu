@@ -576,18 +576,26 @@ __global__ void k_sum_deg(const int32_t* __restrict__ ids, int64_t n, const unsi
     if (threadIdx.x == 0 && acc) atomicAdd(total, acc);
 }
 
-// Makes stream s wait on an event recorded on another stream: at join(), or
-// when it goes out of scope (also while an exception unwinds).
+// Armed when work is forked from stream s onto stream `from`: join() records
+// the event on `from` (after everything enqueued there so far) and makes s
+// wait for it. Joins when it goes out of scope too, so an exception thrown
+// half-way through the forked work still orders s after it (s frees buffers
+// that work reads).
 struct StreamJoin {
-    cudaStream_t s = nullptr;
+    cudaStream_t s = nullptr, from = nullptr;
     cudaEvent_t ev = nullptr;
-    void arm(cudaStream_t st, cudaEvent_t e) {
+    void arm(cudaStream_t st, cudaStream_t other, cudaEvent_t e) {
         s = st;
+        from = other;
         ev = e;
     }
-    void join() {
-        if (ev) cudaStreamWaitEvent(s, ev, 0);
+    cudaError_t join() {
+        if (!ev) return cudaSuccess;
+        cudaEvent_t e = ev;
         ev = nullptr;
+        cudaError_t r = cudaEventRecord(e, from);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(s, e, 0);
+        return r;
     }
     ~StreamJoin() { join(); }
 };
@@ -613,14 +621,11 @@ static void build_sides(const Ctx& ctx, Plan& p, const SideArgs& a, cudaStream_t
         DIM3_CUDA(cudaEventRecord(ctx.ev_fork, s));
         DIM3_CUDA(cudaStreamWaitEvent(ctx.aux, ctx.ev_fork, 0));
         ss = ctx.aux;
+        sjoin.arm(s, ss, ctx.ev_join);
     }
     sort_unique_pairs_enqueue<KS>(a.sy, a.sz, a.ns, a.bz, a.by + a.bz, spp, ss);
-    if (ss != s) {
-        DIM3_CUDA(cudaEventRecord(ctx.ev_join, ss));
-        sjoin.arm(s, ctx.ev_join);
-    }
     build_r_side<KR>(p, a.rx, a.ry, a.nr, a.bx, a.by, s);
-    sjoin.join();
+    DIM3_CUDA(sjoin.join());
     spp.adopt(s);
     build_s_side<KS>(ctx, p, a.sy, a.sz, a.ns, a.by, a.bz, a.theta_z, a.y_tag, a.z_tag, s, &spp);
 }
@@ -679,13 +684,10 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
                 DIM3_CUDA(cudaEventRecord(ctx.ev_fork, s));
                 DIM3_CUDA(cudaStreamWaitEvent(ctx.aux, ctx.ev_fork, 0));
                 zs = ctx.aux;
+                zjoin.arm(s, zs, ctx.ev_join);
             }
             build_value_map(in.s_val, in.s_tag, p->n_inst, nullptr, ns, zmap, sz_id.as<int32_t>(),
                             p->dict_z.as<int32_t>(), z_tag.as<int32_t>(), zs, false);
-            if (zs != s) {
-                DIM3_CUDA(cudaEventRecord(ctx.ev_join, zs));
-                zjoin.arm(s, ctx.ev_join);
-            }
         }
         {
             // y from S.y; R tuples whose y is absent from S.y get id -1 (dropped)
@@ -720,7 +722,7 @@ Plan* build_plan(const Ctx& ctx, const PlanInput& in, int64_t theta_z, cudaStrea
         }
         build_value_map(in.r_val, in.r_tag, p->n_inst, ry_id.as<int32_t>(), nr, xmap, rx_id.as<int32_t>(),
                         p->dict_x.as<int32_t>(), p->x_tag.as<int32_t>(), s, false);
-        zjoin.join();
+        DIM3_CUDA(zjoin.join());
         ValueMap* maps[3] = {&ymap, &xmap, &zmap};
         resolve_counts(maps, self_join ? 2 : 3, nullptr, nullptr, s);
         if (self_join) {
