@@ -201,26 +201,64 @@ def reduce_over_ranks(dist, busy_s: float, pairs: int, device):
     return float(mx[0]), float(t[1])
 
 
-def cpu_baseline(inst, target_s: float, rng_seed: int = 5):
+def rows_on_device(torch, out_x, out_z, xs: np.ndarray):
+    """The (x, z) rows of a canonical device result whose x is in xs, as host
+    arrays (searchsorted on the device, then one copy per row)."""
+    xs = np.unique(np.asarray(xs, np.int32))
+    q = torch.from_numpy(xs).to(out_x.device)
+    lo = torch.searchsorted(out_x, q, right=False).cpu().numpy()
+    hi = torch.searchsorted(out_x, q, right=True).cpu().numpy()
+    px = [out_x[a:b].cpu().numpy() for a, b in zip(lo, hi) if b > a]
+    pz = [out_z[a:b].cpu().numpy() for a, b in zip(lo, hi) if b > a]
+    cat = (lambda p: np.concatenate(p) if p else np.zeros(0, np.int32))  # noqa: E731
+    return cat(px), cat(pz)
+
+
+def boundary_x(torch, out_x, total: int) -> np.ndarray:
+    """x of the rows holding output positions 0, total - 1 and those next to
+    2^31 and 2^32 (where 32-bit offsets would wrap)."""
+    pos = sorted({p for p in [0, total - 1] + [b + d for b in (1 << 31, 1 << 32) for d in (-1, 0)]
+                  if 0 <= p < total})
+    if not pos:
+        return np.zeros(0, np.int32)
+    return np.unique(out_x[torch.tensor(pos, dtype=torch.int64, device=out_x.device)].cpu().numpy())
+
+
+def cpu_baseline(inst, target_s: float, rng_seed: int = 5, check=None):
     """The oracle as it stands, single-threaded, on the rows of a random x
-    sample sized to take about target_s seconds."""
+    sample sized to take about target_s seconds.
+
+    ``check`` = (extra_x, rows_fn): the sample also holds the x values
+    extra_x, and the oracle's rows are compared element by element with the
+    GPU rows rows_fn(xs) of the timed output. Returns (baseline, verified)."""
     import oracle
 
     oracle.build()
     xs = np.unique(inst.r_val)
+    extra = np.zeros(0, np.int32) if check is None else np.asarray(check[0], np.int32)
     rng = np.random.default_rng(rng_seed)
     k = 4
     while True:
-        pick = rng.choice(xs, size=min(k, xs.size), replace=False)
+        pick = np.unique(np.concatenate([rng.choice(xs, size=min(k, xs.size), replace=False), extra]))
         t0 = time.perf_counter()
-        x, _, _ = oracle.join_project(inst.r_key, inst.r_val, inst.s_key, inst.s_val, x_filter=pick)
+        x, z, _ = oracle.join_project(inst.r_key, inst.r_val, inst.s_key, inst.s_val, x_filter=pick)
         dt = time.perf_counter() - t0
-        if dt >= target_s * 0.5 or pick.size == xs.size:
+        if dt >= target_s * 0.5 or pick.size >= xs.size:
             break
         k = int(min(xs.size, max(k * 2, k * target_s / max(dt, 1e-3) * 0.9)))
-    return {"value": x.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"rows of {pick.size} random x of {xs.size} (R restricted to them, S whole); "
+    base = {"value": x.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"rows of {pick.size} x of {xs.size} (random, plus the first, the last and those holding "
+                      f"output positions next to 2^31 and 2^32; R restricted to them, S whole); "
                       f"{x.size} pairs in {dt:.2f} s"}
+    verified = None
+    if check is not None:
+        gx, gz = check[1](pick)
+        ok = bool(gx.size == x.size and np.array_equal(gx, x) and np.array_equal(gz, z))
+        verified = {"rows": int(pick.size), "pairs": int(x.size), "ok": ok,
+                    "boundary_x": [int(v) for v in extra],
+                    "how": "oracle rows (its x filter) vs the same rows of the last timed step's output, "
+                           "element by element"}
+    return base, verified
 
 
 def run_reference(args, rank: int, world: int):
@@ -418,9 +456,14 @@ def main():
     if not args.no_e2e and args.e2e_steps > 0:
         e2e = run_e2e(torch, host_cols, join_call, dev, out_p, args.e2e_steps)
 
-    cpu = None
+    cpu, verified = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(inst, args.cpu_seconds)
+        # the oracle's sample also checks the timed output: its rows are
+        # compared with the same rows of the last timed step
+        check = None
+        if cache is None and ranges is None:
+            check = (boundary_x(torch, out_x, out_p), lambda xs: rows_on_device(torch, out_x, out_z, xs))
+        cpu, verified = cpu_baseline(inst, args.cpu_seconds, check=check)
 
     if rank == 0:
         line = {
@@ -443,6 +486,7 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "verified": verified,
         }
         print(json.dumps(line), flush=True)
     if dist:

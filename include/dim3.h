@@ -223,17 +223,23 @@ DIM3_API int dim3_map(dim3_ctx *ctx, const int32_t *d_vals, int64_t n, int32_t *
  * dim3_map_noalloc -- dim3_map for callers that may not allocate device
  * memory (a host engine that fixed its GPU memory budget at start-up and
  * forbids later allocations, code living under another framework's allocator,
- * or latency-critical code that must not enter the allocator). It computes
- * the mapping of Section 2.2 (rank ids, as dim3_map); the allocation-free
- * form is an interface variant with no counterpart in the paper.
+ * or latency-critical code that must not enter the allocator). It returns the
+ * same rank ids and dictionary as dim3_map. This allocation-free entry point
+ * is an interface variant: the paper has no counterpart.
  *   d_vals, d_ids, d_dict, n_distinct: as for dim3_map; n <= 65536.
  * No context. Runs on the current device and stream. All scratch lives in one
  * fixed 2,883,840-byte device array inside the library (held by every GPU
- * that loads it until the process exits); nothing is allocated or freed.
- * The first call on a device looks up that array's device address, so make it
- * before any stream capture. Every call reuses the same array: calls that
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller. n > 65536 gives DIM3_ERR_OVERFLOW.
+ * that loads it until the process exits); the calls themselves allocate and
+ * free nothing. With lazy module loading (the CUDA default) the library's
+ * module, and with it that array, is placed on a device by the first call
+ * there, which can fail for lack of memory: an engine with a fixed budget
+ * should make one call per device at start-up. That first call also looks up
+ * the array's device address, so it should come before any stream capture.
+ * The address is kept per device index for the life of the process: after
+ * cudaDeviceReset the cached address is stale, so do not use this entry
+ * point on a device that was reset. Every call reuses the same array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller. n > 65536 gives DIM3_ERR_OVERFLOW.
  * Synchronises the stream.
  */
 DIM3_API int dim3_map_noalloc(const int32_t *d_vals, int64_t n, int32_t *d_ids, int32_t *d_dict,

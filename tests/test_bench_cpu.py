@@ -57,3 +57,25 @@ def test_default_arguments(monkeypatch):
     assert args.gpus == 1 and args.warmup >= 3 and args.steps >= 1
     assert args.workload == "two_table_1m_zipf1" and args.impl == "ours"
     assert not args.f1_sweep and not args.no_e2e
+
+
+def test_cpu_baseline_checks_sampled_rows():
+    """The oracle leg compares its rows with the same rows of a result (here a
+    host copy of the oracle's own full result in CPU tensors), and flags a
+    result with one wrong z; boundary rows of a short result are its first
+    and last x."""
+    import gen
+    import oracle
+
+    inst = gen.small_two_table(3, n_r=3000, n_s=2500, nx=300, ny=80, nz=250, zipf=1.0)
+    ox, oz, _ = oracle.join_project(inst.r_key, inst.r_val, inst.s_key, inst.s_val)
+    tx, tz = torch.from_numpy(ox.copy()), torch.from_numpy(oz.copy())
+    bx = bench.boundary_x(torch, tx, ox.size)
+    assert set(bx.tolist()) == {int(ox[0]), int(ox[-1])}
+    base, ver = bench.cpu_baseline(inst, 0.01, check=(bx, lambda xs: bench.rows_on_device(torch, tx, tz, xs)))
+    assert ver["ok"] and ver["rows"] >= 2 and base["kind"] == "oracle" and base["cores"] == 1
+    tz[ox.size // 2] += 1
+    mid = int(ox[ox.size // 2])
+    _, ver = bench.cpu_baseline(inst, 0.01, check=(np.array([mid], np.int32),
+                                                    lambda xs: bench.rows_on_device(torch, tx, tz, xs)))
+    assert not ver["ok"]

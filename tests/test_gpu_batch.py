@@ -10,7 +10,7 @@ import torch
 import gen
 import oracle
 import paper_2206_04995_gb300 as dim3
-from tests.gpu_util import dev, host, inst_dev
+from tests.gpu_util import dev, host, inst_dev, rows_of
 
 pytestmark = pytest.mark.gpu
 
@@ -120,20 +120,33 @@ def test_batch_config4_scaled_vs_oracle():
 
 def test_batch_config4_full_vs_single_path():
     """The 256-instance workload: every instance equals the one-at-a-time path;
-    a few small instances are also checked against the oracle."""
+    the 6 smallest instances are checked against the oracle whole, and the 8
+    largest (up to ~3e8 pairs each) on 48 sampled x rows each (the first, the
+    last and random ones) through the oracle's x filter."""
     insts = gen.config4_batch()
     c = ctx_with()
     cols = [inst_dev(i) for i in insts]
     x, z, per = c.batch_join_project(cols)
     off = np.concatenate([[0], np.cumsum(per)])
-    small = sorted(range(len(insts)), key=lambda t: insts[t].nr)[:6]
+    order = sorted(range(len(insts)), key=lambda t: insts[t].nr)
+    small, large = order[:6], order[-8:]
+    rng = np.random.default_rng(41)
     for t, col in enumerate(cols):
         sx, sz = c.join_project(*col)
         assert per[t] == sx.numel()
-        assert torch.equal(x[off[t]:off[t + 1]], sx) and torch.equal(z[off[t]:off[t + 1]], sz), f"instance {t}"
+        bx, bz = x[off[t]:off[t + 1]], z[off[t]:off[t + 1]]
+        assert torch.equal(bx, sx) and torch.equal(bz, sz), f"instance {t}"
+        i = insts[t]
         if t in small:
-            ox, oz, _ = oracle.join_project(insts[t].r_key, insts[t].r_val, insts[t].s_key, insts[t].s_val)
+            ox, oz, _ = oracle.join_project(i.r_key, i.r_val, i.s_key, i.s_val)
             assert np.array_equal(host(sx), ox) and np.array_equal(host(sz), oz)
+        if t in large:
+            xs = np.unique(i.r_val)
+            pick = np.unique(np.concatenate([xs[:1], xs[-1:], rng.choice(xs, size=46, replace=False)]))
+            gx, gz, _ = rows_of(bx, bz, pick)
+            ox, oz, _ = oracle.join_project(i.r_key, i.r_val, i.s_key, i.s_val, x_filter=pick)
+            assert gx.size == ox.size, f"instance {t}: sampled rows {gx.size} vs oracle {ox.size}"
+            assert np.array_equal(gx, ox) and np.array_equal(gz, oz), f"instance {t} sampled rows"
     c.close()
 
 

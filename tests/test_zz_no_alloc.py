@@ -1,5 +1,6 @@
 """dim3_map_noalloc, the mapping entry point for callers that may not allocate
-device memory, against dim3_map (exact equality), on two calls in a row.
+device memory, against dim3_map and against the oracle's rank map (exact
+equality), on calls in a row.
 
 The second call is smaller than the first and reuses the same fixed scratch
 array, so a result that leaned on leftovers of the first call would show
@@ -14,6 +15,7 @@ import pytest
 import torch
 
 import gen
+import oracle
 import paper_2206_04995_gb300 as dim3
 
 pytestmark = pytest.mark.gpu
@@ -41,13 +43,27 @@ def _map_noalloc(vals: torch.Tensor):
     return rc, ids[:n], dct[: max(nd.value, 0)], nd.value, lib
 
 
-def test_map_noalloc_matches_map_on_two_calls_in_a_row():
+def _columns():
+    """Value columns in call order: the largest column, a smaller one
+    after it, a table filled to its largest load (65,536 distinct values in
+    131,072 slots) and a short column of INT32 extremes, 0 and -1 with
+    repeats (the order of the signed sort key)."""
+    out = []
+    for n, pool, seed in [(MAX_N, 40_000, 1), (9_000, 1_500, 2)]:
+        rng = np.random.default_rng(seed)
+        out.append(gen.random_ids(rng, pool)[rng.integers(0, pool, size=n)])
+    out.append(gen.random_ids(np.random.default_rng(3), MAX_N))
+    ext = np.array([2**31 - 1, -2**31, 0, -1, 1, -2**31, 2**31 - 1, 0, -1, -2, 2**31 - 2, -2**31 + 1] * 5,
+                   dtype=np.int64).astype(np.int32)
+    out.append(np.random.default_rng(4).permutation(ext))
+    return out
+
+
+def test_map_noalloc_matches_map_and_oracle_on_calls_in_a_row():
     ctx = dim3.Context(0)
     try:
-        for n, pool, seed in [(MAX_N, 40_000, 1), (9_000, 1_500, 2)]:
-            rng = np.random.default_rng(seed)
-            vals = gen.random_ids(rng, pool)[rng.integers(0, pool, size=n)]
-            d_vals = torch.from_numpy(vals).cuda()
+        for vals in _columns():
+            d_vals = torch.from_numpy(np.ascontiguousarray(vals, np.int32)).cuda()
             ref_ids, ref_dict = ctx.map(d_vals)
             rc, ids, dct, nd, lib = _map_noalloc(d_vals)
             assert rc == 0, lib.dim3_last_error()
@@ -55,6 +71,9 @@ def test_map_noalloc_matches_map_on_two_calls_in_a_row():
             assert nd == ref_dict.numel()
             assert torch.equal(ids, ref_ids)
             assert torch.equal(dct, ref_dict)
+            o_ids, o_dict = oracle.rank_map(vals)
+            assert np.array_equal(ids.cpu().numpy(), o_ids)
+            assert np.array_equal(dct.cpu().numpy(), o_dict)
     finally:
         ctx.close()
 
