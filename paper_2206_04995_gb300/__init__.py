@@ -35,6 +35,7 @@ from .dim3 import (  # noqa: F401
     OPT_ID_CHUNK_MAX,
     OPT_LIGHT_ROW_MAX,
     OPT_PATH,
+    OPT_TILE_WORDS,
     PATH_AUTO,
     PATH_CLASSICAL,
     PATH_HYBRID,

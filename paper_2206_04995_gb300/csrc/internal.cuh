@@ -84,6 +84,7 @@ struct Options {
     int64_t two_pass = 0;   // nonzero: always a counting pass before the emitting pass
     int64_t id_chunk_max = -1;  // pairs per 4096-z chunk written through staged ids (<0: 512)
     int64_t path = 0;           // one-call joins: 0 f1 decides, 1 hybrid, 2 classical
+    int64_t tile_words = 0;     // z-tiled rows: bitmap words per tile (0: automatic)
     // f1 constants (Section 2.6), seconds: t_map per input row, t_randRW per
     // join tuple of the hybrid path, t_hash per join tuple of the classical path
     double f1c[3] = {kF1TMap, kF1TRand, kF1THash};
@@ -151,6 +152,11 @@ struct Plan {
     DevBuf cache_off;  // int64 [rows + 1]
     DevBuf cache_dbits; // dense bits of the cached range
     DevBuf cache_dcnt;  // dense counts of the cached range
+    // z-tiled single instance: the cached range's (row, tile) units
+    DevBuf cache_units;     // int32 [cache_n_list]: rows run per tile (null: every row)
+    DevBuf cache_tcnt;      // int32 [cache_n_list * cache_tiles]: pairs per unit
+    int64_t cache_n_list = 0, cache_tile_bits = 0;
+    int cache_tiles = 0;
 };
 
 // Per-phase CUDA-event timing (DIM3_OPT_TIMING). Events are recorded on the

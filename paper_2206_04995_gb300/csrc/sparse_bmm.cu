@@ -73,6 +73,12 @@ struct XRowArgs {
     int32_t* out_z;
     int32_t* out_c;
     int vec_ok;
+    // z-tiled single instance (k_tile_rows): units = (listed row, z tile)
+    const int32_t* unit_rows;  // row numbers (x - x_begin) of the rows to run, or null (rows 0 .. n_list-1)
+    int64_t n_list;            // rows in the list
+    int n_tiles;               // z tiles per row
+    int32_t* tcnt;             // counting pass out: pairs of every unit [n_list * n_tiles]
+    const int32_t* tcnt_in;    // emitting pass: the counting pass's unit pairs
 };
 
 // Fill out[o0, o1) with v using 16-byte stores where aligned.
@@ -207,6 +213,108 @@ __device__ __forceinline__ void flush_warp_ids(int32_t* dst, const int32_t* st, 
             }
         }
     }
+}
+
+// Compaction of one warp's run of 32-word groups [g0, g1) of a z-tile bitmap
+// (holding `mine` set bits) into out_z from position wpos, z ascending: the
+// per-warp stage st collects z values (dense groups) or z ids (sparse 4096-z
+// chunks) and is flushed with 16-byte stores. Called by a whole warp.
+__device__ __forceinline__ void compact_run(const XRowArgs& a, const uint32_t* bm, int tw, int g0, int g1, int mine,
+                                            int64_t zt0, int64_t wpos, int32_t* st) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    // Set bits are staged as z ids, group after group, and turned
+    // into z values only when the stage is flushed: a sparse row
+    // then costs one round of independent dictionary gathers per
+    // ~1000 pairs instead of one dependent round per group.
+    int sh = (int)(wpos & 3), sc = 0;  // stage holds pairs [wpos, wpos + sc) at st[sh ..]
+    // Chunks of 4 groups (128 words, 4096 z): lane l first reads words
+    // 4l .. 4l+3; a sparse chunk is extracted lane by lane in one step,
+    // a dense one group by group with the transposed dictionary reads.
+    // A dense run (an eighth of its bits set or more, large stage):
+    // every group straight through compact_group, no chunk scan.
+    const bool dense_run = a.stage_ints >= kWarpStage && (int64_t)mine * 8 >= (int64_t)(g1 - g0) * 1024;
+    for (int g = g0; dense_run && g < g1; ++g) {
+        const int w = (g << 5) + lane;
+        const uint32_t word = w < tw ? bm[w] : 0u;
+        const int c = __popc(word);
+        const int incl = warp_inclusive_scan(c);
+        const int total_g = __shfl_sync(kFull, incl, 31);
+        if (total_g == 0) continue;
+        sh = (int)(wpos & 3);
+        compact_group(st, sh, word, incl - c, total_g, a.dict_z + zt0 + ((int64_t)g << 10), lane, lt);
+        __syncwarp();
+        flush_warp(a.out_z + (wpos - sh), st, sh, total_g, a.vec_ok);
+        __syncwarp();
+        wpos += total_g;
+    }
+    for (int gc = g0; !dense_run && gc < g1; gc += 4) {
+        const int wl = (gc << 5) + (lane << 2);
+        const int wlim = min(tw, g1 << 5);
+        uint32_t wv[4];
+        int c4 = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wv[k] = wl + k < wlim ? bm[wl + k] : 0u;
+            c4 += __popc(wv[k]);
+        }
+        const int incl4 = warp_inclusive_scan(c4);
+        const int total_c = __shfl_sync(kFull, incl4, 31);
+        if (total_c == 0) continue;
+        if (total_c <= a.id_max) {
+            if (sh + sc + total_c > a.stage_ints) {
+                __syncwarp();
+                flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
+                __syncwarp();
+                wpos += sc;
+                sh = (int)(wpos & 3);
+                sc = 0;
+            }
+            int pos = sh + sc + incl4 - c4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t v = wv[k];
+                while (v) {
+                    const int b = __ffs(v) - 1;
+                    v &= v - 1;
+                    st[pos++] = (int32_t)(zt0 + ((int64_t)(wl + k) << 5) + b);
+                }
+            }
+            sc += total_c;
+            continue;
+        }
+        // dense chunk: write z values directly (coalesced dictionary
+        // reads, lane l reading entry 32 j + l), one half-group (16
+        // words, at most 512 pairs) per flush; pending ids go first
+        if (sc) {
+            __syncwarp();
+            flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
+            __syncwarp();
+            wpos += sc;
+            sc = 0;
+        }
+        const int per = a.stage_ints >= kWarpStage ? 1 : 2;  // whole groups fit a large stage
+        for (int h = gc * per; h < min(gc + 4, g1) * per; ++h) {
+            const int g = h / per;
+            const int w = (g << 5) + lane;
+            const bool mine_half = per == 1 || (lane >> 4) == (h & 1);
+            const uint32_t word = (mine_half && w < tw) ? bm[w] : 0u;
+            const int c = __popc(word);
+            const int incl = warp_inclusive_scan(c);
+            const int total_g = __shfl_sync(kFull, incl, 31);
+            if (total_g == 0) continue;
+            sh = (int)(wpos & 3);
+            compact_group(st, sh, word, incl - c, total_g, a.dict_z + zt0 + ((int64_t)g << 10), lane, lt);
+            __syncwarp();
+            flush_warp(a.out_z + (wpos - sh), st, sh, total_g, a.vec_ok);
+            __syncwarp();
+            wpos += total_g;
+        }
+        sh = (int)(wpos & 3);
+    }
+    __syncwarp();
+    if (sc) flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
+    __syncwarp();
 }
 
 // Register caps: 32 for the counting instance (eight CTAs per SM), 64 for the
@@ -412,100 +520,7 @@ __global__ void __launch_bounds__(kThreads, kEmit ? 4 : 8) k_xrow_bits(const XRo
                 if (w < warp) wpos += c;
                 tile_total += c;
             }
-            // Set bits are staged as z ids, group after group, and turned
-            // into z values only when the stage is flushed: a sparse row
-            // then costs one round of independent dictionary gathers per
-            // ~1000 pairs instead of one dependent round per group.
-            int32_t* st = stage + warp * a.stage_ints;
-            const unsigned lt = lanemask_lt();
-            int sh = (int)(wpos & 3), sc = 0;  // stage holds pairs [wpos, wpos + sc) at st[sh ..]
-            // Chunks of 4 groups (128 words, 4096 z): lane l first reads words
-            // 4l .. 4l+3; a sparse chunk is extracted lane by lane in one step,
-            // a dense one group by group with the transposed dictionary reads.
-            // A dense run (an eighth of its bits set or more, large stage):
-            // every group straight through compact_group, no chunk scan.
-            const bool dense_run = a.stage_ints >= kWarpStage && (int64_t)mine * 8 >= (int64_t)(g1 - g0) * 1024;
-            for (int g = g0; write && dense_run && g < g1; ++g) {
-                const int w = (g << 5) + lane;
-                const uint32_t word = w < tw ? bm[w] : 0u;
-                const int c = __popc(word);
-                const int incl = warp_inclusive_scan(c);
-                const int total_g = __shfl_sync(kFull, incl, 31);
-                if (total_g == 0) continue;
-                sh = (int)(wpos & 3);
-                compact_group(st, sh, word, incl - c, total_g, a.dict_z + zt0 + ((int64_t)g << 10), lane, lt);
-                __syncwarp();
-                flush_warp(a.out_z + (wpos - sh), st, sh, total_g, a.vec_ok);
-                __syncwarp();
-                wpos += total_g;
-            }
-            for (int gc = g0; write && !dense_run && gc < g1; gc += 4) {
-                const int wl = (gc << 5) + (lane << 2);
-                const int wlim = min(tw, g1 << 5);
-                uint32_t wv[4];
-                int c4 = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    wv[k] = wl + k < wlim ? bm[wl + k] : 0u;
-                    c4 += __popc(wv[k]);
-                }
-                const int incl4 = warp_inclusive_scan(c4);
-                const int total_c = __shfl_sync(kFull, incl4, 31);
-                if (total_c == 0) continue;
-                if (total_c <= a.id_max) {
-                    if (sh + sc + total_c > a.stage_ints) {
-                        __syncwarp();
-                        flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
-                        __syncwarp();
-                        wpos += sc;
-                        sh = (int)(wpos & 3);
-                        sc = 0;
-                    }
-                    int pos = sh + sc + incl4 - c4;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        uint32_t v = wv[k];
-                        while (v) {
-                            const int b = __ffs(v) - 1;
-                            v &= v - 1;
-                            st[pos++] = (int32_t)(zt0 + ((int64_t)(wl + k) << 5) + b);
-                        }
-                    }
-                    sc += total_c;
-                    continue;
-                }
-                // dense chunk: write z values directly (coalesced dictionary
-                // reads, lane l reading entry 32 j + l), one half-group (16
-                // words, at most 512 pairs) per flush; pending ids go first
-                if (sc) {
-                    __syncwarp();
-                    flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
-                    __syncwarp();
-                    wpos += sc;
-                    sc = 0;
-                }
-                const int per = a.stage_ints >= kWarpStage ? 1 : 2;  // whole groups fit a large stage
-                for (int h = gc * per; h < min(gc + 4, g1) * per; ++h) {
-                    const int g = h / per;
-                    const int w = (g << 5) + lane;
-                    const bool mine_half = per == 1 || (lane >> 4) == (h & 1);
-                    const uint32_t word = (mine_half && w < tw) ? bm[w] : 0u;
-                    const int c = __popc(word);
-                    const int incl = warp_inclusive_scan(c);
-                    const int total_g = __shfl_sync(kFull, incl, 31);
-                    if (total_g == 0) continue;
-                    sh = (int)(wpos & 3);
-                    compact_group(st, sh, word, incl - c, total_g, a.dict_z + zt0 + ((int64_t)g << 10), lane, lt);
-                    __syncwarp();
-                    flush_warp(a.out_z + (wpos - sh), st, sh, total_g, a.vec_ok);
-                    __syncwarp();
-                    wpos += total_g;
-                }
-                sh = (int)(wpos & 3);
-            }
-            __syncwarp();
-            if (write && sc) flush_warp_ids(a.out_z + (wpos - sh), st, sh, sc, a.dict_z, a.vec_ok);
-            __syncwarp();
+            if (write) compact_run(a, bm, tw, g0, g1, mine, zt0, wpos, stage + warp * a.stage_ints);
             out_pos += tile_total;
         }
         __syncthreads();
@@ -949,6 +964,165 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
     if (!kEmit && tid == 0) a.cnt[xr] = total;
 }
 
+// ------------------------------------------------------------- tiled rows
+// A single instance whose z range spans several shared-memory tiles: one CTA
+// per (x row, z tile) unit, so the tiles of a row run side by side and every
+// CTA holds one tile's SPA bitmap. The bitmap is built from the row's join
+// tuples that fall in the tile, taken as ONE flat list: the tile boundaries
+// of every S_sparse row are precomputed (tile_ptr), an exclusive scan over
+// the row's R entries gives each entry's first tuple, and thread i takes
+// tuples i, i + 256, ... (a binary search over the scan finds a tuple's
+// entry). Every lane sets a bit in every step whatever the lengths of the S
+// rows (which are mostly short in power-law graphs), and the loads of
+// different tuples are independent, so they overlap instead of forming one
+// dependent chain per R entry. The counting pass stores each unit's pairs;
+// the emitting pass writes unit (x, t) after the units (x, t' < t) of its row
+// and after all earlier rows.
+constexpr int kTileChunk = 2 * kThreads;  // R entries of a row per round (two per thread)
+
+template <bool kEmit>
+__global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);           // emit: kWarps x a.stage_ints
+    uint32_t* bm = smem + (kEmit ? kWarps * a.stage_ints : 0);  // tile words
+    __shared__ uint32_t s_s0[kTileChunk];    // first tuple of the entry's segment in ss_col
+    __shared__ int32_t s_seg[kTileChunk];    // exclusive scan of the segment lengths
+    __shared__ int32_t s_wide[kTileChunk];   // bitmap rows of the chunk's wide S rows
+    __shared__ int32_t s_sc[kWarps + 1];
+    __shared__ int32_t s_wc[kWarps];
+    __shared__ int64_t s_scan[kWarps + 1];
+    __shared__ int s_nwide[2];  // wide rows of the current chunk; the two alternate between chunks
+
+    const int64_t unit = blockIdx.x;
+    const int T = a.n_tiles;
+    const int64_t li = unit / T;
+    const int t = (int)(unit - li * T);
+    if (li >= a.n_list) return;
+    const int64_t xr = a.unit_rows ? (int64_t)a.unit_rows[li] : li;
+    const int64_t x = a.x_begin + xr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t zt0 = (int64_t)t * a.tile_bits, zt1 = min64(zt0 + a.tile_bits, a.n_z);
+    const int tw = (int)((zt1 - zt0 + 31) >> 5);
+    if (kEmit && a.tcnt_in[unit] == 0) return;  // nothing of this row in this tile
+    const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
+    clear_words(bm, tw);
+    if (tid == 0) s_nwide[0] = 0;
+    __syncthreads();
+    for (int64_t c0 = r0, ck = 0; c0 < r1; c0 += kTileChunk, ++ck) {
+        const int nc = (int)min64(kTileChunk, r1 - c0);
+        int* nwide = &s_nwide[ck & 1];
+        if (tid == 0) s_nwide[(ck + 1) & 1] = 0;  // the next chunk's counter (the previous chunk's is done)
+        int cnt[2];
+        uint32_t first[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = 2 * tid + k;
+            cnt[k] = 0;
+            first[k] = 0u;
+            if (i < nc) {
+                const int32_t y = a.r_col[c0 + i];
+                const int32_t b = a.bm_row_of_y[y];
+                if (b >= 0) {
+                    s_wide[atomicAdd(nwide, 1)] = b;
+                } else {
+                    const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + t;
+                    const int64_t s0 = tp[0];
+                    cnt[k] = (int)(tp[1] - s0);
+                    first[k] = (uint32_t)s0;
+                }
+            }
+        }
+        int n_tup;
+        const int ex = block_exclusive_scan<int, kThreads>(cnt[0] + cnt[1], &n_tup, s_sc);
+        s_seg[2 * tid] = ex;
+        s_seg[2 * tid + 1] = ex + cnt[0];
+        s_s0[2 * tid] = first[0];
+        s_s0[2 * tid + 1] = first[1];
+        __syncthreads();
+        // the chunk's tuples in the tile, four per thread per step
+        for (int j0 = 0; j0 < n_tup; j0 += 4 * kThreads) {
+            int32_t zz[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u * kThreads + tid;
+                zz[u] = -1;
+                if (j < n_tup) {
+                    int lo = 0, hi = nc;  // last entry whose first tuple is <= j
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_seg[mid] <= j) lo = mid; else hi = mid;
+                    }
+                    zz[u] = __ldg(a.ss_col + s_s0[lo] + (j - s_seg[lo]));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (zz[u] >= 0) {
+                    const int z = (int)(zz[u] - zt0);
+                    atomicOr(&bm[z >> 5], 1u << (z & 31));
+                }
+            }
+        }
+        // wide S rows of the chunk: OR their bitmap words over the tile
+        const int nw = *nwide;
+        if (nw > 0) {
+            const uint32_t* bits = a.ss_bits + (zt0 >> 5);
+            for (int w = tid; w < tw; w += kThreads) {
+                uint32_t acc = 0u;
+                for (int i = 0; i < nw; ++i) acc |= __ldg(bits + a.bm_off[s_wide[i]] + w);
+                if (acc) atomicOr(&bm[w], acc);
+            }
+        }
+        __syncthreads();
+    }
+    if (a.n_zd > 0) {
+        // DenseEC result of x over the dense index (see k_xrow_bits)
+        const uint32_t* drow = a.d_bits + xr * a.zdw;
+        for (int64_t d = tid; d < a.n_zd; d += kThreads) {
+            if ((drow[d >> 5] >> (d & 31)) & 1u) {
+                int32_t z = a.zd_list[d];
+                if (z >= zt0 && z < zt1) {
+                    z -= (int32_t)zt0;
+                    atomicOr(&bm[z >> 5], 1u << (z & 31));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!kEmit) {
+        const int64_t c = block_sum<int64_t, kThreads>(popc_words(bm, tw), s_scan);
+        if (tid == 0) a.tcnt[unit] = (int32_t)c;
+        return;
+    }
+    int64_t o = a.off[xr];
+    for (int u = 0; u < t; ++u) o += a.tcnt_in[li * T + u];
+    fill_range(a.out_x, o, o + a.tcnt_in[unit], a.dict_x[x], a.vec_ok);
+    const int groups = (tw + 31) >> 5;
+    const int gpw = (groups + kWarps - 1) / kWarps;
+    const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
+    int mine = 0;
+    for (int g = g0; g < g1; ++g) {
+        const int w = (g << 5) + lane;
+        mine += w < tw ? __popc(bm[w]) : 0;
+    }
+    mine = warp_sum(mine);
+    if (lane == 0) s_wc[warp] = mine;
+    __syncthreads();
+    int64_t wpos = o;
+    for (int w = 0; w < warp; ++w) wpos += s_wc[w];
+    compact_run(a, bm, tw, g0, g1, mine, zt0, wpos, stage + warp * a.stage_ints);
+}
+
+// cnt[row] = pairs of the row's units, for the listed rows
+__global__ void k_tile_sum(const int32_t* __restrict__ tcnt, const int32_t* __restrict__ rows, int64_t n_list, int T,
+                           int64_t* cnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_list; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        for (int t = 0; t < T; ++t) c += tcnt[i * T + t];
+        cnt[rows ? rows[i] : i] = c;
+    }
+}
+
 // ----------------------------------------------------------------- host side
 static size_t bits_smem(int64_t tile_bits, bool emit, int stage_ints) {
     return (emit ? (size_t)kWarps * stage_ints * 4 : 0) + (size_t)(tile_bits / 32) * 4;
@@ -966,7 +1140,25 @@ static void setup_attrs(const Ctx& ctx) {
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_tile_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_tile_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     done[d] = true;
+}
+
+// Project rows of a single instance whose z range needs several bitmap tiles
+// (of at most kMaxTileWords words, or of the option's size) run as (row,
+// tile) units (k_tile_rows).
+static bool use_tiles(const Ctx& ctx, const Plan& p, int kind) {
+    const int64_t lim = ctx.opt.tile_words > 0 ? std::min<int64_t>(ctx.opt.tile_words, kMaxTileWords) : kMaxTileWords;
+    return kind == 0 && p.n_inst == 1 && p.zw > lim;
+}
+
+// Bitmap words per tile of k_tile_rows: the option if set, else the fewest
+// tiles of at most kMaxTileWords words, of equal size (a multiple of 32 words).
+static int64_t tile_words_for(const Ctx& ctx, const Plan& p) {
+    if (ctx.opt.tile_words > 0) return std::min<int64_t>(ctx.opt.tile_words, kMaxTileWords);
+    const int64_t n_tiles = ceil_div(p.zw, kMaxTileWords);
+    return std::min<int64_t>(kMaxTileWords, ceil_div(ceil_div(p.zw, n_tiles), 32) * 32);
 }
 
 // tile_ptr[y * cols + t] = first entry of S_sparse row y with z >= start of
@@ -1122,12 +1314,37 @@ __global__ void __launch_bounds__(kThreads) k_light_rows(const LightArgs a) {
     const unsigned lt = lanemask_lt();
     for (int64_t i = blockIdx.x * (int64_t)kWarps + warp; i < a.n; i += (int64_t)gridDim.x * kWarps) {
         const int64_t xr = a.rows[i], x = a.x_begin + xr;
+        // gather the row's join tuples' z ids: 32 R entries at a time, lane l
+        // holding entry l's S row start and the exclusive scan of the row
+        // lengths; lane l then copies tuples l, l + 32, ... of the batch, its
+        // entry found by a binary search over the lanes (shuffles), so the
+        // loads of all entries are independent
         int n = 0;
-        for (int64_t q = a.r_rowptr[x]; q < a.r_rowptr[x + 1]; ++q) {
-            const int32_t y = a.r_col[q];
-            const int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
-            for (int64_t j = s0 + lane; j < s1; j += 32) buf[n + (int)(j - s0)] = a.ss_col[j];
-            n += (int)(s1 - s0);
+        const int64_t q1 = a.r_rowptr[x + 1];
+        for (int64_t qb = a.r_rowptr[x]; qb < q1; qb += 32) {
+            const int64_t q = qb + lane;
+            int64_t s0 = 0;
+            int len = 0;
+            if (q < q1) {
+                const int32_t y = a.r_col[q];
+                s0 = a.ss_rowptr[y];
+                len = (int)(a.ss_rowptr[y + 1] - s0);
+            }
+            const int incl = warp_inclusive_scan(len);
+            const int ex = incl - len, m = __shfl_sync(kFull, incl, 31);
+            for (int j0 = 0; j0 < m; j0 += 32) {
+                const int j = j0 + lane;
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int e = __shfl_sync(kFull, ex, lo + step);
+                    if (e <= j) lo += step;
+                }
+                const int64_t base = __shfl_sync(kFull, s0, lo);
+                const int e_lo = __shfl_sync(kFull, ex, lo);
+                if (j < m) buf[n + j] = __ldg(a.ss_col + base + (j - e_lo));
+            }
+            n += m;
         }
         int pw = 1;
         while (pw < n) pw <<= 1;
@@ -1170,9 +1387,10 @@ __global__ void k_light_flags(const int64_t* __restrict__ outj_x, int64_t n_x, i
         light[x] = outj_x[x] <= lim ? 1 : 0;
 }
 
-__global__ void k_light_range(const uint8_t* __restrict__ light, int64_t x_begin, int64_t rows, int32_t* flag) {
+__global__ void k_light_range(const uint8_t* __restrict__ light, int64_t x_begin, int64_t rows, int want,
+                              int32_t* flag) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
-        flag[r] = light[x_begin + r];
+        flag[r] = (light ? (int)light[x_begin + r] : 0) == want ? 1 : 0;
 }
 
 __global__ void k_light_list(const int32_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t rows,
@@ -1223,20 +1441,30 @@ static const uint8_t* ensure_light(const Ctx& ctx, Plan& p, cudaStream_t s) {
     return p.light_n > 0 ? p.light.as<uint8_t>() : nullptr;
 }
 
-// the light rows of [x_begin, x_begin + rows): counting (cnt) or emitting (off)
-static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* cnt, const int64_t* off,
-                         int32_t* out_x, int32_t* out_z, cudaStream_t s) {
-    DevBuf flag, pos, list;
+// Row numbers r of [x_begin, x_begin + rows) whose light flag equals `want`
+// (flags null: every row is heavy) into `list`; returns their number.
+static int64_t list_rows(const uint8_t* light, int64_t x_begin, int64_t rows, int want, DevBuf& list,
+                         cudaStream_t s) {
+    DevBuf flag, pos;
     flag.alloc((size_t)rows * 4, s);
     pos.alloc((size_t)(rows + 1) * 8, s);
-    k_light_range<<<blocks_for(rows), kThreads, 0, s>>>(p.light.as<uint8_t>(), x_begin, rows, flag.as<int32_t>());
+    k_light_range<<<blocks_for(rows), kThreads, 0, s>>>(light, x_begin, rows, want, flag.as<int32_t>());
     DIM3_LAUNCHED();
     exclusive_scan_i32_to_i64(flag.as<int32_t>(), pos.as<int64_t>(), rows, s);
     const int64_t n = read_i64(pos.as<int64_t>() + rows, s);
-    if (n == 0) return;
+    if (n == 0) return 0;
     list.alloc((size_t)n * 4, s);
     k_light_list<<<blocks_for(rows), kThreads, 0, s>>>(flag.as<int32_t>(), pos.as<int64_t>(), rows, list.as<int32_t>());
     DIM3_LAUNCHED();
+    return n;
+}
+
+// the light rows of [x_begin, x_begin + rows): counting (cnt) or emitting (off)
+static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* cnt, const int64_t* off,
+                         int32_t* out_x, int32_t* out_z, cudaStream_t s) {
+    DevBuf list;
+    const int64_t n = list_rows(p.light.as<uint8_t>(), x_begin, rows, 1, list, s);
+    if (n == 0) return;
     LightArgs la{};
     la.rows = list.as<int32_t>();
     la.n = n;
@@ -1294,6 +1522,30 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
     DIM3_LAUNCHED();
 }
 
+// One (row, tile) unit per CTA: counting (a.tcnt) or emitting (a.tcnt_in).
+static void launch_tiles(const Ctx& ctx, const XRowArgs& a, bool emit, cudaStream_t s) {
+    const int64_t units = a.n_list * a.n_tiles;
+    if (units <= 0) return;
+    DIM3_REQUIRE(units < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long for its z tiles");
+    setup_attrs(ctx);
+    PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
+    const size_t sm = bits_smem(a.tile_bits, emit, a.stage_ints);
+    if (emit) k_tile_rows<true><<<(unsigned)units, kThreads, sm, s>>>(a);
+    else k_tile_rows<false><<<(unsigned)units, kThreads, sm, s>>>(a);
+    DIM3_LAUNCHED();
+}
+
+// make_args with k_tile_rows's tile size and tile starts (built once per size).
+static XRowArgs tile_args(Plan& p, int64_t x_begin, int64_t rows, int64_t tile_bits, cudaStream_t s) {
+    XRowArgs a = make_args(p, x_begin, rows, 0);
+    a.tile_bits = tile_bits;
+    ensure_tile_ptr(p, 0, tile_bits, s);
+    a.tile_ptr = p.tile_ptr[0].as<int64_t>();
+    a.tile_cols = p.tile_cols[0];
+    a.n_tiles = (int)ceil_div(p.info.n_z, tile_bits);
+    return a;
+}
+
 // Dense results and per-row counts of a range, cached on the plan so that a
 // count query followed by the emitting call does the counting pass once.
 static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int kind, cudaStream_t s) {
@@ -1317,9 +1569,35 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
     DevBuf cnt;
     cnt.alloc((size_t)std::max<int64_t>(rows, 1) * 8, s);
     p.cache_off.alloc((size_t)(rows + 1) * 8, s);
+    p.cache_units.release();
+    p.cache_tcnt.release();
+    p.cache_n_list = 0;
+    p.cache_tiles = 0;
     if (rows > 0) {
         if (p.info.n_z <= 0 || p.info.n_r_kept == 0) {
             DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
+        } else if (use_tiles(ctx, p, kind)) {
+            XRowArgs a = tile_args(p, x_begin, rows, tile_words_for(ctx, p) * 32, s);
+            a.d_bits = p.cache_dbits.as<uint32_t>();
+            const uint8_t* light = ensure_light(ctx, p, s);
+            a.n_list = light ? list_rows(light, x_begin, rows, 0, p.cache_units, s) : rows;
+            a.unit_rows = p.cache_units.as<int32_t>();
+            p.cache_tcnt.alloc((size_t)std::max<int64_t>(a.n_list * a.n_tiles, 1) * 4, s);
+            a.tcnt = p.cache_tcnt.as<int32_t>();
+            DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
+            launch_tiles(ctx, a, false, s);
+            if (a.n_list > 0) {
+                k_tile_sum<<<blocks_for(a.n_list), kThreads, 0, s>>>(a.tcnt, a.unit_rows, a.n_list, a.n_tiles,
+                                                                    cnt.as<int64_t>());
+                DIM3_LAUNCHED();
+            }
+            if (light) {
+                PhaseScope phase(ctx.stats, PH_COUNT, s);
+                launch_light(p, x_begin, rows, cnt.as<int64_t>(), nullptr, nullptr, nullptr, s);
+            }
+            p.cache_n_list = a.n_list;
+            p.cache_tiles = a.n_tiles;
+            p.cache_tile_bits = a.tile_bits;
         } else {
             XRowArgs a = prep_args(p, x_begin, rows, kind, s);
             a.d_bits = p.cache_dbits.as<uint32_t>();
@@ -1432,7 +1710,8 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
     check_range(p, x_begin, x_end);
     const bool cached = p.cache_begin == x_begin && p.cache_end == x_end && p.cache_kind == kind;
     if (!cached && kind == 0 && capacity > 0 && out_x && out_z && x_end > x_begin && p.info.n_z > 0 &&
-        p.info.n_r_kept > 0 && p.zw <= kMaxTileWords && !ctx.opt.two_pass && !ensure_light(ctx, p, s))
+        p.info.n_r_kept > 0 && !use_tiles(ctx, p, 0) && p.zw <= kMaxTileWords && !ctx.opt.two_pass &&
+        !ensure_light(ctx, p, s))
         return plan_join_single_pass(ctx, p, x_begin, x_end, out_x, out_z, capacity, count, s);
     ensure_counts(ctx, p, x_begin, x_end, kind, s);
     const int64_t rows = x_end - x_begin;
@@ -1440,7 +1719,24 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
     if (count) *count = total;
     if (total > capacity) throw Error(DIM3_ERR_CAPACITY, "output capacity " + std::to_string(capacity) +
                                                              " < result size " + std::to_string(total));
-    if (total > 0) {
+    if (total > 0 && use_tiles(ctx, p, kind)) {
+        DIM3_REQUIRE(out_x && out_z, DIM3_ERR_ARG, "null output buffer");
+        XRowArgs a = tile_args(p, x_begin, rows, p.cache_tile_bits, s);
+        a.d_bits = p.cache_dbits.as<uint32_t>();
+        a.off = p.cache_off.as<int64_t>();
+        a.out_x = out_x;
+        a.out_z = out_z;
+        a.vec_ok = ((reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z)) & 15u) == 0;
+        set_stage(ctx, p, a, total);
+        a.unit_rows = p.cache_units.as<int32_t>();
+        a.n_list = p.cache_n_list;
+        a.tcnt_in = p.cache_tcnt.as<int32_t>();
+        launch_tiles(ctx, a, true, s);
+        if (p.light_n > 0) {
+            PhaseScope phase(ctx.stats, PH_EMIT, s);
+            launch_light(p, x_begin, rows, nullptr, a.off, out_x, out_z, s);
+        }
+    } else if (total > 0) {
         DIM3_REQUIRE(out_x && out_z && (kind == 0 || out_cnt), DIM3_ERR_ARG, "null output buffer");
         XRowArgs a = prep_args(p, x_begin, rows, kind, s);
         a.d_bits = p.cache_dbits.as<uint32_t>();
