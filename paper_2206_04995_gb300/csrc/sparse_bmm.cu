@@ -968,17 +968,19 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
 // A single instance whose z range spans several shared-memory tiles: one CTA
 // per (x row, z tile) unit, so the tiles of a row run side by side and every
 // CTA holds one tile's SPA bitmap. The bitmap is built from the row's join
-// tuples that fall in the tile, taken as ONE flat list: the tile boundaries
-// of every S_sparse row are precomputed (tile_ptr), an exclusive scan over
-// the row's R entries gives each entry's first tuple, and thread i takes
-// tuples i, i + 256, ... (a binary search over the scan finds a tuple's
-// entry). Every lane sets a bit in every step whatever the lengths of the S
-// rows (which are mostly short in power-law graphs), and the loads of
-// different tuples are independent, so they overlap instead of forming one
-// dependent chain per R entry. The counting pass stores each unit's pairs;
-// the emitting pass writes unit (x, t) after the units (x, t' < t) of its row
-// and after all earlier rows.
+// tuples that fall in the tile: the tile boundaries of every S_sparse row are
+// precomputed (tile_ptr), so each R entry y of the row names one segment of
+// S_sparse[y]. Segments of at least 32 tuples (in power-law graphs nearly all
+// join tuples lie in them: the neighbours of a vertex are biased towards
+// hubs) are cut into pieces of up to 256 tuples, and the warps take the pieces
+// in turn, each lane loading every 32nd tuple of a piece (coalesced, eight
+// independent loads in flight). Shorter segments are walked by the thread that
+// read their entry. The counting pass stores each unit's pairs; the emitting
+// pass writes unit (x, t) after the units (x, t' < t) of its row and after all
+// earlier rows.
 constexpr int kTileChunk = 2 * kThreads;  // R entries of a row per round (two per thread)
+constexpr int kPiece = 256;               // tuples per warp work item
+constexpr int kLongSeg = 32;              // segments from this length on go to the warps
 
 template <bool kEmit>
 __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
@@ -986,7 +988,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
     int32_t* stage = reinterpret_cast<int32_t*>(smem);           // emit: kWarps x a.stage_ints
     uint32_t* bm = smem + (kEmit ? kWarps * a.stage_ints : 0);  // tile words
     __shared__ uint32_t s_s0[kTileChunk];    // first tuple of the entry's segment in ss_col
-    __shared__ int32_t s_seg[kTileChunk];    // exclusive scan of the segment lengths
+    __shared__ int32_t s_len[kTileChunk];    // its length
+    __shared__ int32_t s_pc[kTileChunk];     // exclusive scan of the pieces of long segments
     __shared__ int32_t s_wide[kTileChunk];   // bitmap rows of the chunk's wide S rows
     __shared__ int32_t s_sc[kWarps + 1];
     __shared__ int32_t s_wc[kWarps];
@@ -1012,12 +1015,12 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
         const int nc = (int)min64(kTileChunk, r1 - c0);
         int* nwide = &s_nwide[ck & 1];
         if (tid == 0) s_nwide[(ck + 1) & 1] = 0;  // the next chunk's counter (the previous chunk's is done)
-        int cnt[2];
+        int len[2];
         uint32_t first[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int i = 2 * tid + k;
-            cnt[k] = 0;
+            len[k] = 0;
             first[k] = 0u;
             if (i < nc) {
                 const int32_t y = a.r_col[c0 + i];
@@ -1027,39 +1030,59 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
                 } else {
                     const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + t;
                     const int64_t s0 = tp[0];
-                    cnt[k] = (int)(tp[1] - s0);
+                    len[k] = (int)(tp[1] - s0);
                     first[k] = (uint32_t)s0;
                 }
             }
         }
-        int n_tup;
-        const int ex = block_exclusive_scan<int, kThreads>(cnt[0] + cnt[1], &n_tup, s_sc);
-        s_seg[2 * tid] = ex;
-        s_seg[2 * tid + 1] = ex + cnt[0];
+        const int pc0 = len[0] >= kLongSeg ? (len[0] + kPiece - 1) / kPiece : 0;
+        const int pc1 = len[1] >= kLongSeg ? (len[1] + kPiece - 1) / kPiece : 0;
+        int n_pieces;
+        const int ex = block_exclusive_scan<int, kThreads>(pc0 + pc1, &n_pieces, s_sc);
+        s_pc[2 * tid] = ex;
+        s_pc[2 * tid + 1] = ex + pc0;
         s_s0[2 * tid] = first[0];
         s_s0[2 * tid + 1] = first[1];
+        s_len[2 * tid] = len[0];
+        s_len[2 * tid + 1] = len[1];
         __syncthreads();
-        // the chunk's tuples in the tile, four per thread per step
-        for (int j0 = 0; j0 < n_tup; j0 += 4 * kThreads) {
-            int32_t zz[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = j0 + u * kThreads + tid;
-                zz[u] = -1;
-                if (j < n_tup) {
-                    int lo = 0, hi = nc;  // last entry whose first tuple is <= j
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (s_seg[mid] <= j) lo = mid; else hi = mid;
-                    }
-                    zz[u] = __ldg(a.ss_col + s_s0[lo] + (j - s_seg[lo]));
-                }
+        // long segments: piece p of the chunk goes to warp p mod 8
+        for (int p = warp; p < n_pieces; p += kWarps) {
+            int lo = 0, hi = nc;  // the entry whose pieces hold p (same search in every lane)
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_pc[mid] <= p) lo = mid; else hi = mid;
             }
+            const int off = (p - s_pc[lo]) * kPiece;
+            const int n = min(kPiece, s_len[lo] - off);
+            const int32_t* src = a.ss_col + s_s0[lo] + off;
+            int32_t zz[kPiece / 32];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kPiece / 32; ++u) zz[u] = u * 32 + lane < n ? __ldg(src + u * 32 + lane) : -1;
+#pragma unroll
+            for (int u = 0; u < kPiece / 32; ++u) {
                 if (zz[u] >= 0) {
                     const int z = (int)(zz[u] - zt0);
                     atomicOr(&bm[z >> 5], 1u << (z & 31));
+                }
+            }
+        }
+        // short segments: the thread that read the entry walks it
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (len[k] > 0 && len[k] < kLongSeg) {
+                const int32_t* src = a.ss_col + first[k];
+                for (int q0 = 0; q0 < len[k]; q0 += 4) {
+                    int32_t zz[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) zz[u] = q0 + u < len[k] ? __ldg(src + q0 + u) : -1;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (zz[u] >= 0) {
+                            const int z = (int)(zz[u] - zt0);
+                            atomicOr(&bm[z >> 5], 1u << (z & 31));
+                        }
+                    }
                 }
             }
         }
