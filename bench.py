@@ -50,8 +50,9 @@ def parse_args():
     ap.add_argument("--dense-variant", type=int, default=None, help="0 auto, 1 tensor core, 2 popc, 3 probe")
     ap.add_argument("--opt", action="append", default=[],
                     help="library option KEY=VALUE (dim3_option number), e.g. 6=1 for one x row per emitting CTA")
-    ap.add_argument("--serve-queries", type=int, default=200)
-    ap.add_argument("--serve-max-tuples", type=int, default=200_000)
+    ap.add_argument("--serve-queries", type=int, default=2000)
+    ap.add_argument("--serve-max-tuples", type=int, default=2_000_000)
+    ap.add_argument("--serve-workers", type=int, default=2)
     ap.add_argument("--premapped", action="store_true",
                     help="columns given as ids (mapping skipped, dim3_partition_ids); ids made on the host before timing")
     ap.add_argument("--cache-budget", type=int, default=None,
@@ -65,6 +66,8 @@ def parse_args():
     ap.add_argument("--f1-sweep", action="store_true",
                     help="Section 2.6's f1 on 1M x 1M uniform tables over a range of N_Y: one JSON line per "
                          "point with the forced hybrid and classical times and f1's choice")
+    ap.add_argument("--count", action="store_true",
+                    help="time dim3_join_count (Join-Aggregate COUNT per pair) instead of dim3_join_project")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -363,6 +366,8 @@ def main():
         dim3_partition_ids, for a cache dim3_partition_cached, each followed
         by dim3_plan_join_project + dim3_plan_destroy."""
         if ranges is None and cache is None:
+            if args.count:
+                return ctx.join_count(*c, out_x=ox, out_z=oz, out_c=out_c)[:2]
             return ctx.join_project(*c, out_x=ox, out_z=oz)
         pl = ctx.partition_cached(*c, cache) if cache is not None else ctx.partition_ids(*c, *ranges)
         try:
@@ -380,6 +385,7 @@ def main():
     plan.close()
     out_x = torch.empty(out_p, dtype=torch.int32, device=dev)
     out_z = torch.empty(out_p, dtype=torch.int32, device=dev)
+    out_c = torch.empty(out_p if args.count else 0, dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > 129 MB L2
 
     def step():
@@ -443,9 +449,9 @@ def main():
     else:
         emit_ms, emit_n = tm["sparse_emit"]
         emit_s = emit_ms / 1e3 / args.steps  # the whole emitting pass of one step
-        alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
+        alg_bytes = (12 if args.count else 8) * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
         achieved = alg_bytes / emit_s / 1e9
-        traffic, tinfo = traffic_for(args.workload)
+        traffic, tinfo = traffic_for(args.workload) if not args.count else (None, {"kernel": "k_xrow_counts<emit>"})
         kname = (tinfo or {}).get("kernel", "k_xrow_emit_g / k_xrow_bits<emit>")
         roofline = {"bound": "hbm", "kernel": f"{kname} (SparseBMM+union+compaction)",
                     "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s", "frac": achieved / peaks["hbm"],
@@ -453,7 +459,7 @@ def main():
                     "launch_ms": emit_s * 1e3}
 
     e2e = None
-    if not args.no_e2e and args.e2e_steps > 0:
+    if not args.no_e2e and args.e2e_steps > 0 and not args.count:
         e2e = run_e2e(torch, host_cols, join_call, dev, out_p, args.e2e_steps)
 
     cpu, verified = None, None
@@ -461,7 +467,7 @@ def main():
         # the oracle's sample also checks the timed output: its rows are
         # compared with the same rows of the last timed step
         check = None
-        if cache is None and ranges is None:
+        if cache is None and ranges is None and not args.count:
             check = (boundary_x(torch, out_x, out_p), lambda xs: rows_on_device(torch, out_x, out_z, xs))
         cpu, verified = cpu_baseline(inst, args.cpu_seconds, check=check)
 
@@ -470,7 +476,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * busy_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": inst.name, "n_r": inst.nr, "n_s": inst.ns, "n_x": info["n_x"],
+            "config": {"workload": inst.name + (" (Join-Count)" if args.count else ""), "n_r": inst.nr, "n_s": inst.ns, "n_x": info["n_x"],
                        "n_y": info["n_y"], "n_z": info["n_z"], "n_z_dense": info["n_z_dense"],
                        "out_p": out_p, "out_j": info["out_j"], "theta_z": info["theta_z"],
                        "l2": "flushed between steps (256 MiB write outside the step events)",
@@ -627,60 +633,97 @@ def run_batch(args, rank, world, local_rank):
     ctx.close()
 
 
-def run_serve(args, rank, world, local_rank):
-    """A bounded sample of the Poisson query stream (the first --serve-queries
-    queries, tuple counts capped at --serve-max-tuples): served by the
-    continuous-batching loop and by the plain loop (one query at a time, one
-    stream), first all queued at once (capacity, pairs/s), then arriving at
-    their Poisson times (latency p50/p99)."""
-    import torch
-
+def serve_queries(torch, n_queries: int, hi: int, rank: int, dev):
+    """The Poisson stream of Join-Project / Join-Count queries (arrivals,
+    kinds, sizes and seeds from gen.config5_stream), each query's tables drawn
+    on the device from its seed (gen.device) and kept in page-locked host
+    memory, from where the server copies them in."""
     import gen
-    from paper_2206_04995_gb300.serve import Limits, Query, Server, summarize
+    from gen import device as gdev
+    from paper_2206_04995_gb300.serve import Query
 
-    torch.cuda.set_device(local_rank)
-    stream = gen.config5_stream(seed=4 + 1000 * rank, n_queries=args.serve_queries, hi=args.serve_max_tuples)
+    stream = gen.config5_stream(seed=4 + 1000 * rank, n_queries=n_queries, hi=hi)
     qs = []
     for i, q in enumerate(stream):
-        inst = q.instance()
-        qs.append(Query(i, q.kind, inst.r_key, inst.r_val, inst.s_key, inst.s_val, q.arrival_s))
+        cols = [c.cpu().pin_memory() for c in gdev.query_tables(q, dev)]
+        qs.append(Query(i, q.kind, *cols, q.arrival_s))
+    torch.cuda.synchronize()
+    return qs
 
-    def run(workers, limits, realtime):
-        srv = Server(local_rank, workers=workers, limits=limits)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = srv.run([dataclasses_replace(q) for q in qs], realtime=realtime)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        srv.close()
-        s = summarize(res, wall)
-        del res
-        torch.cuda.empty_cache()
-        return s
+
+def serve_runs(torch, qs, local_rank, workers: int, modes=("queued", "poisson")):
+    """Served (continuous batching, `workers` streams) and plain (one query at
+    a time on one stream, every query alone) runs of the stream: all queued at
+    once (capacity) and arriving at their Poisson times (latency). Results are
+    handed over in chunks and released at once (the consumer only counts)."""
+    import dataclasses
+
+    from paper_2206_04995_gb300.serve import Limits, Server, summarize
 
     served_lim = Limits(max_batch=64, max_tuples=16_000_000, reserve_bytes=8 << 30)
-    plain_lim = Limits(max_batch=1, reserve_bytes=8 << 30)
-    run(2, served_lim, False)  # warm-up: context creation, module load, memory pool growth
-    cap_served = run(2, served_lim, False)
-    cap_plain = run(1, plain_lim, False)
-    lat_served = run(2, served_lim, True)
-    lat_plain = run(1, plain_lim, True)
+    plain_lim = Limits(max_batch=1, reserve_bytes=8 << 30, big_tuples=0)
+    out = {}
+    for mode in modes:
+        for name, w, lim in (("served", workers, served_lim), ("plain", 1, plain_lim)):
+            srv = Server(local_rank, workers=w, limits=lim, keep=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = srv.run([dataclasses.replace(q) for q in qs], realtime=(mode == "poisson"))
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            srv.close()
+            sm = summarize(res, wall)
+            span = max(q.arrival for q in qs) if mode == "poisson" else 0.0
+            sm["offered_pairs_per_s"] = sm["pairs"] / span if span > 0 else None
+            out[f"{name}_{mode}"] = sm
+            torch.cuda.empty_cache()
+    for mode in modes:
+        out[f"served_over_plain_{mode}"] = out[f"served_{mode}"]["pairs_per_s"] / out[f"plain_{mode}"]["pairs_per_s"]
+    return out
+
+
+def run_serve(args, rank, world, local_rank):
+    """The Poisson query stream (2,000 queries at 200 q/s, tuples log-uniform
+    in [1e4, 2e6] per table, half Join-Project and half Join-Count): served
+    by the continuous-batching loop and by the plain loop, all queued at once
+    and arriving at their Poisson times."""
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    t0 = time.perf_counter()
+    qs = serve_queries(torch, args.serve_queries, args.serve_max_tuples, rank, dev)
+    gen_s = time.perf_counter() - t0
+    # warm-up: contexts, module loading, memory pools
+    serve_runs(torch, qs[: min(len(qs), 40)], local_rank, args.serve_workers, modes=("queued",))
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = dim3_launch_count()
+    r = serve_runs(torch, qs, local_rank, args.serve_workers)
+    launches = dim3_launch_count() - l0
+    clocks = sampler.stop()
+    cap = r["served_queued"]
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": cap_served["pairs_per_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
-            "warmup": 1, "ms_per_step": 1e3 * cap_served["wall_s"], "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": cap["pairs_per_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
+            "warmup": 1, "ms_per_step": 1e3 * cap["wall_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "serve2000", "queries": len(qs), "max_tuples": args.serve_max_tuples,
-                       "rate_qps": 200.0, "sample": f"first {len(qs)} queries of the 2,000-query Poisson stream, "
-                       f"tuples log-uniform in [1e4, {args.serve_max_tuples:.0e}]",
-                       "served_capacity": cap_served, "plain_capacity": cap_plain,
-                       "served_over_plain": cap_served["pairs_per_s"] / cap_plain["pairs_per_s"],
-                       "served_poisson": lat_served, "plain_poisson": lat_plain,
-                       "p50_ms": lat_served["p50_ms"], "p99_ms": lat_served["p99_ms"]},
-            "e2e": {"value": cap_served["pairs_per_s"], "unit": UNIT,
+                       "rate_qps": 200.0, "workers": args.serve_workers, "inputs_s": gen_s,
+                       "tuples": int(sum(q.tuples for q in qs)), **r,
+                       "p50_ms": r["served_poisson"]["p50_ms"], "p99_ms": r["served_poisson"]["p99_ms"]},
+            "gpu_launches": launches, "clocks": clocks,
+            "e2e": {"value": cap["pairs_per_s"], "unit": UNIT,
                     "h2d_bytes_per_step": int(sum(q.tuples for q in qs) * 8), "d2h_bytes_per_step": 0,
-                    "note": "host inputs copied in per query; results stay on the device"},
+                    "note": "inputs copied in from page-locked host memory per query; results stay on the "
+                            "device, handed to the consumer chunk by chunk and released"},
         }), flush=True)
+
+
+def dim3_launch_count():
+    import paper_2206_04995_gb300 as dim3
+
+    return dim3.launch_count()
 
 
 def run_aggregate(args, rank, world, local_rank):
@@ -812,12 +855,6 @@ def run_mjp(args, rank, world, local_rank):
             "gpu_launches": launches, "clocks": clocks,
         }), flush=True)
     ctx.close()
-
-
-def dataclasses_replace(q):
-    import dataclasses
-
-    return dataclasses.replace(q)
 
 
 def run_f1_sweep(args, local_rank):

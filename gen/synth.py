@@ -46,13 +46,24 @@ class Instance:
         return int(self.s_key.size)
 
 
+def _sorted_unique(a: np.ndarray) -> np.ndarray:
+    """The distinct values of a, ascending (np.unique's result, by one sort)."""
+    a = np.sort(a, kind="stable")
+    if a.size == 0:
+        return a
+    keep = np.empty(a.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
 def random_ids(rng: np.random.Generator, k: int) -> np.ndarray:
     """k distinct uniformly random 32-bit values, in random order, as int32."""
     out = np.empty(0, dtype=np.uint32)
     while out.size < k:
         draw = rng.integers(0, 2**32, size=int((k - out.size) * 1.05) + 16,
                             dtype=np.uint64).astype(np.uint32)
-        out = np.unique(np.concatenate([out, draw]))
+        out = _sorted_unique(np.concatenate([out, draw]))
     return rng.permutation(out)[:k].view(np.int32)
 
 
@@ -87,7 +98,7 @@ def distinct_pairs(rng: np.random.Generator, n: int, draw, max_rounds: int = 200
             break
         need = n - keys.size
         a, b = draw(rng, int(need * 1.25) + 64)
-        keys = np.unique(np.concatenate([keys, _pack(a, b)]))
+        keys = _sorted_unique(np.concatenate([keys, _pack(a, b)]))
     else:
         raise RuntimeError(f"could not draw {n} distinct tuples")
     keys = rng.permutation(keys)[:n]

@@ -66,3 +66,41 @@ def test_served_small_against_oracle():
         else:
             ox, oz, _ = oracle.join_project(q.r_key, q.r_val, q.s_key, q.s_val)
         assert np.array_equal(host(r.out_x), ox) and np.array_equal(host(r.out_z), oz)
+
+
+@pytest.mark.parametrize("workers", [1, 3])
+def test_chunked_output_and_big_queries(workers):
+    """Results cut into many x-range chunks (a small chunk bound), big queries
+    alone and small ones batched, equal the query's result alone; without
+    keep, the parts handed to the consumer concatenate to the same result."""
+    qs = stream(24, 5, 1.0)
+    lim = Limits(max_batch=6, reserve_bytes=1 << 30, big_tuples=12_000, chunk_pairs=20_000)
+    srv = Server(0, workers=workers, limits=lim)
+    res = srv.run(qs, realtime=False)
+    srv.close()
+    assert max(r.chunks for r in res) > 3 and max(r.batch_size for r in res) > 1
+    assert all(r.batch_size == 1 for q, r in zip(qs, res) if q.tuples > 12_000)
+    got = {}
+
+    def on_part(q, x, z, c):
+        got.setdefault(q.qid, []).append((x.clone(), z.clone(), None if c is None else c.clone()))
+
+    srv = Server(0, workers=workers, limits=lim, keep=False, on_part=on_part)
+    res2 = srv.run(qs, realtime=False)
+    srv.close()
+    ctx = dim3.Context(0)
+    for q, r, r2 in zip(qs, res, res2):
+        ref = alone(ctx, q)
+        assert torch.equal(r.out_x, ref[0]) and torch.equal(r.out_z, ref[1]), f"query {q.qid}"
+        if q.kind == "count":
+            assert torch.equal(r.out_c, ref[2])
+        assert r2.pairs == ref[0].numel() and not r2.parts
+        parts = got.get(q.qid, [])
+        if parts:
+            assert torch.equal(torch.cat([p[0] for p in parts]), ref[0])
+            assert torch.equal(torch.cat([p[1] for p in parts]), ref[1])
+            if q.kind == "count":
+                assert torch.equal(torch.cat([p[2] for p in parts]), ref[2])
+        else:
+            assert ref[0].numel() == 0
+    ctx.close()
