@@ -157,6 +157,7 @@ struct Plan {
     DevBuf cache_tcnt;      // int32 [cache_n_list * cache_tiles]: pairs per unit
     int64_t cache_n_list = 0, cache_tile_bits = 0;
     int cache_tiles = 0;
+    int64_t max_mx = -1;  // largest |R[x]| (the bound of a pair's count), -1 until computed
 };
 
 // Per-phase CUDA-event timing (DIM3_OPT_TIMING). Events are recorded on the

@@ -982,16 +982,105 @@ constexpr int kTileChunk = 2 * kThreads;  // R entries of a row per round (two p
 constexpr int kPiece = 256;               // tuples per warp work item
 constexpr int kLongSeg = 32;              // segments from this length on go to the warps
 
+// Shared memory of visit_chunk.
+struct ChunkSmem {
+    uint32_t s0[kTileChunk];   // first tuple of the entry's segment in ss_col
+    int32_t len[kTileChunk];   // its length
+    int32_t pc[kTileChunk];    // exclusive scan of the pieces of long segments
+    int32_t sc[kWarps + 1];
+};
+
+// Calls visit(z) for every join tuple (y in R entries [c0, c0 + nc), z in
+// S_sparse[y]) -- only the z of tile t when tile_ptr is set. Entries whose y
+// is held as a bitmap row are skipped when `wide` is set and their bitmap
+// rows appended to wide[*nwide++] instead. Long segments are cut into pieces
+// of kPiece tuples taken by the warps in turn (coalesced, kPiece / 32
+// independent loads per lane); short ones are walked by the thread that read
+// the entry. Contains __syncthreads: call from every thread; the caller
+// synchronises before sm is reused.
+template <class Visit>
+__device__ __forceinline__ void visit_chunk(const XRowArgs& a, int64_t c0, int nc, int t, ChunkSmem& sm,
+                                            int32_t* wide, int* nwide, Visit visit) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int len[2];
+    uint32_t first[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int i = 2 * tid + k;
+        len[k] = 0;
+        first[k] = 0u;
+        if (i < nc) {
+            const int32_t y = a.r_col[c0 + i];
+            const int32_t b = wide ? a.bm_row_of_y[y] : -1;
+            if (b >= 0) {
+                wide[atomicAdd(nwide, 1)] = b;
+            } else {
+                int64_t s0, s1;
+                if (a.tile_ptr) {
+                    const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + t;
+                    s0 = tp[0];
+                    s1 = tp[1];
+                } else {
+                    s0 = a.ss_rowptr[y];
+                    s1 = a.ss_rowptr[y + 1];
+                }
+                len[k] = (int)(s1 - s0);
+                first[k] = (uint32_t)s0;
+            }
+        }
+    }
+    const int pc0 = len[0] >= kLongSeg ? (len[0] + kPiece - 1) / kPiece : 0;
+    const int pc1 = len[1] >= kLongSeg ? (len[1] + kPiece - 1) / kPiece : 0;
+    int n_pieces;
+    const int ex = block_exclusive_scan<int, kThreads>(pc0 + pc1, &n_pieces, sm.sc);
+    sm.pc[2 * tid] = ex;
+    sm.pc[2 * tid + 1] = ex + pc0;
+    sm.s0[2 * tid] = first[0];
+    sm.s0[2 * tid + 1] = first[1];
+    sm.len[2 * tid] = len[0];
+    sm.len[2 * tid + 1] = len[1];
+    __syncthreads();
+    // long segments: piece p of the chunk goes to warp p mod kWarps
+    for (int p = warp; p < n_pieces; p += kWarps) {
+        int lo = 0, hi = nc;  // the entry whose pieces hold p (the same search in every lane)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.pc[mid] <= p) lo = mid; else hi = mid;
+        }
+        const int off = (p - sm.pc[lo]) * kPiece;
+        const int n = min(kPiece, sm.len[lo] - off);
+        const int32_t* src = a.ss_col + sm.s0[lo] + off;
+        int32_t zz[kPiece / 32];
+#pragma unroll
+        for (int u = 0; u < kPiece / 32; ++u) zz[u] = u * 32 + lane < n ? __ldg(src + u * 32 + lane) : -1;
+#pragma unroll
+        for (int u = 0; u < kPiece / 32; ++u)
+            if (zz[u] >= 0) visit(zz[u]);
+    }
+    // short segments: the thread that read the entry walks it
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (len[k] > 0 && len[k] < kLongSeg) {
+            const int32_t* src = a.ss_col + first[k];
+            for (int q0 = 0; q0 < len[k]; q0 += 4) {
+                int32_t zz[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) zz[u] = q0 + u < len[k] ? __ldg(src + q0 + u) : -1;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (zz[u] >= 0) visit(zz[u]);
+            }
+        }
+    }
+}
+
 template <bool kEmit>
 __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     int32_t* stage = reinterpret_cast<int32_t*>(smem);           // emit: kWarps x a.stage_ints
     uint32_t* bm = smem + (kEmit ? kWarps * a.stage_ints : 0);  // tile words
-    __shared__ uint32_t s_s0[kTileChunk];    // first tuple of the entry's segment in ss_col
-    __shared__ int32_t s_len[kTileChunk];    // its length
-    __shared__ int32_t s_pc[kTileChunk];     // exclusive scan of the pieces of long segments
+    __shared__ ChunkSmem cs;
     __shared__ int32_t s_wide[kTileChunk];   // bitmap rows of the chunk's wide S rows
-    __shared__ int32_t s_sc[kWarps + 1];
     __shared__ int32_t s_wc[kWarps];
     __shared__ int64_t s_scan[kWarps + 1];
     __shared__ int s_nwide[2];  // wide rows of the current chunk; the two alternate between chunks
@@ -1015,77 +1104,10 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
         const int nc = (int)min64(kTileChunk, r1 - c0);
         int* nwide = &s_nwide[ck & 1];
         if (tid == 0) s_nwide[(ck + 1) & 1] = 0;  // the next chunk's counter (the previous chunk's is done)
-        int len[2];
-        uint32_t first[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int i = 2 * tid + k;
-            len[k] = 0;
-            first[k] = 0u;
-            if (i < nc) {
-                const int32_t y = a.r_col[c0 + i];
-                const int32_t b = a.bm_row_of_y[y];
-                if (b >= 0) {
-                    s_wide[atomicAdd(nwide, 1)] = b;
-                } else {
-                    const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + t;
-                    const int64_t s0 = tp[0];
-                    len[k] = (int)(tp[1] - s0);
-                    first[k] = (uint32_t)s0;
-                }
-            }
-        }
-        const int pc0 = len[0] >= kLongSeg ? (len[0] + kPiece - 1) / kPiece : 0;
-        const int pc1 = len[1] >= kLongSeg ? (len[1] + kPiece - 1) / kPiece : 0;
-        int n_pieces;
-        const int ex = block_exclusive_scan<int, kThreads>(pc0 + pc1, &n_pieces, s_sc);
-        s_pc[2 * tid] = ex;
-        s_pc[2 * tid + 1] = ex + pc0;
-        s_s0[2 * tid] = first[0];
-        s_s0[2 * tid + 1] = first[1];
-        s_len[2 * tid] = len[0];
-        s_len[2 * tid + 1] = len[1];
-        __syncthreads();
-        // long segments: piece p of the chunk goes to warp p mod 8
-        for (int p = warp; p < n_pieces; p += kWarps) {
-            int lo = 0, hi = nc;  // the entry whose pieces hold p (same search in every lane)
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (s_pc[mid] <= p) lo = mid; else hi = mid;
-            }
-            const int off = (p - s_pc[lo]) * kPiece;
-            const int n = min(kPiece, s_len[lo] - off);
-            const int32_t* src = a.ss_col + s_s0[lo] + off;
-            int32_t zz[kPiece / 32];
-#pragma unroll
-            for (int u = 0; u < kPiece / 32; ++u) zz[u] = u * 32 + lane < n ? __ldg(src + u * 32 + lane) : -1;
-#pragma unroll
-            for (int u = 0; u < kPiece / 32; ++u) {
-                if (zz[u] >= 0) {
-                    const int z = (int)(zz[u] - zt0);
-                    atomicOr(&bm[z >> 5], 1u << (z & 31));
-                }
-            }
-        }
-        // short segments: the thread that read the entry walks it
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (len[k] > 0 && len[k] < kLongSeg) {
-                const int32_t* src = a.ss_col + first[k];
-                for (int q0 = 0; q0 < len[k]; q0 += 4) {
-                    int32_t zz[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) zz[u] = q0 + u < len[k] ? __ldg(src + q0 + u) : -1;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (zz[u] >= 0) {
-                            const int z = (int)(zz[u] - zt0);
-                            atomicOr(&bm[z >> 5], 1u << (z & 31));
-                        }
-                    }
-                }
-            }
-        }
+        visit_chunk(a, c0, nc, t, cs, s_wide, nwide, [&](int32_t zid) {
+            const int z = (int)(zid - zt0);
+            atomicOr(&bm[z >> 5], 1u << (z & 31));
+        });
         // wide S rows of the chunk: OR their bitmap words over the tile
         const int nw = *nwide;
         if (nw > 0) {
@@ -1134,6 +1156,150 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
     int64_t wpos = o;
     for (int w = 0; w < warp; ++w) wpos += s_wc[w];
     compact_run(a, bm, tw, g0, g1, mine, zt0, wpos, stage + warp * a.stage_ints);
+}
+
+// ------------------------------------------------- Join-Count, packed
+// Join-Count rows of a single instance. The SPA holds one counter per z of a
+// z tile, packed CB bits wide (8 when no x has more than 255 R entries, 16
+// up to 65,535, else 32; a pair's count is at most |R[x]|, so it cannot carry
+// into the next counter), which puts 4x (2x) as many z in a tile of shared
+// memory. Join tuples come from visit_chunk (warp pieces of long S rows,
+// threads on short ones) and add 1 << (CB * slot) with one shared atomic;
+// DenseEC's counts are added the same way. Every warp then owns a run of the
+// tile's counter words: it counts their nonzero counters and, in the
+// emitting pass, writes (z, count) of each in z order through a per-warp
+// stage -- no block barrier between a warp's groups.
+constexpr int kCntStageP = 264;             // staged (z id, count) per warp: 2 x 128 + the alignment shift
+constexpr int64_t kMaxPackedWords = 7168;   // counter words per tile (28 KiB)
+
+template <int CB>
+__device__ __forceinline__ uint32_t nonzero_slots(uint32_t w) {
+    if (CB == 32) return w != 0u ? 1u : 0u;
+    if (CB == 16) return ((w & 0xFFFFu) != 0u ? 1u : 0u) | ((w >> 16) != 0u ? 2u : 0u);
+    const uint32_t m = __vcmpne4(w, 0u);  // 0xFF in every nonzero byte
+    return ((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u);
+}
+
+template <int CB, bool kEmit>
+__global__ void __launch_bounds__(kThreads) k_cnt_rows(const XRowArgs a) {
+    constexpr int CPW = 32 / CB;
+    constexpr int LCPW = CB == 8 ? 2 : CB == 16 ? 1 : 0;
+    constexpr uint32_t CMASK = CB == 32 ? 0xFFFFFFFFu : ((1u << CB) - 1u);
+    extern __shared__ __align__(16) uint32_t smem[];
+    int32_t* st_z = reinterpret_cast<int32_t*>(smem);            // emit: kWarps x kCntStageP z ids
+    int32_t* st_c = st_z + (kEmit ? kWarps * kCntStageP : 0);     // emit: kWarps x kCntStageP counts
+    uint32_t* ctr = reinterpret_cast<uint32_t*>(st_c + (kEmit ? kWarps * kCntStageP : 0));
+    __shared__ ChunkSmem cs;
+    __shared__ int32_t s_wc[kWarps];
+    __shared__ int64_t s_scan[kWarps + 1];
+
+    const int64_t xr = blockIdx.x;
+    if (xr >= a.n_rows) return;
+    const int64_t x = a.x_begin + xr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
+    int64_t out_pos = 0, total = 0;
+    if (kEmit) {
+        out_pos = a.off[xr];
+        if (a.off[xr + 1] == out_pos) return;
+        fill_range(a.out_x, out_pos, a.off[xr + 1], a.dict_x[x], a.vec_ok);
+    }
+    for (int t = 0; t < a.n_tiles; ++t) {
+        const int64_t zt0 = (int64_t)t * a.tile_bits, zt1 = min64(zt0 + a.tile_bits, a.n_z);
+        const int tw = (int)((zt1 - zt0 + CPW - 1) / CPW);
+        clear_words(ctr, tw);
+        __syncthreads();
+        for (int64_t c0 = r0; c0 < r1; c0 += kTileChunk) {
+            visit_chunk(a, c0, (int)min64(kTileChunk, r1 - c0), t, cs, nullptr, nullptr, [&](int32_t zid) {
+                const int z = (int)(zid - zt0);
+                atomicAdd(&ctr[z >> LCPW], 1u << (CB * (z & (CPW - 1))));
+            });
+            __syncthreads();
+        }
+        if (a.n_zd > 0) {
+            const int32_t* crow = a.d_cnt + xr * a.n_zd;
+            for (int64_t d = tid; d < a.n_zd; d += kThreads) {
+                const int32_t c = crow[d];
+                const int32_t z = a.zd_list[d];
+                if (c > 0 && z >= zt0 && z < zt1) {
+                    const int zz = (int)(z - zt0);
+                    atomicAdd(&ctr[zz >> LCPW], (uint32_t)c << (CB * (zz & (CPW - 1))));
+                }
+            }
+        }
+        __syncthreads();
+        // warp w owns counter words [w0, w1) (whole 32-word groups but the last)
+        const int wpw = ((tw + kWarps * 32 - 1) / (kWarps * 32)) * 32;
+        const int w0 = min(tw, warp * wpw), w1 = min(tw, w0 + wpw);
+        int mine = 0;
+        for (int w = w0 + lane; w < w1; w += 32) mine += __popc(nonzero_slots<CB>(ctr[w]));
+        mine = warp_sum(mine);
+        if (!kEmit) {
+            total += block_sum<int64_t, kThreads>(lane == 0 ? mine : 0, s_scan);
+            continue;  // block_sum ends with a barrier: the tile can be cleared
+        }
+        if (lane == 0) s_wc[warp] = mine;
+        __syncthreads();
+        int64_t wpos = out_pos, tile_total = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            if (w < warp) wpos += s_wc[w];
+            tile_total += s_wc[w];
+        }
+        int32_t* sz = st_z + warp * kCntStageP;
+        int32_t* sc_ = st_c + warp * kCntStageP;
+        int sh = (int)(wpos & 3), sc = 0;
+        for (int wb = w0; wb < w1; wb += 32) {
+            const int w = wb + lane;
+            const uint32_t word = w < w1 ? ctr[w] : 0u;
+            uint32_t m = nonzero_slots<CB>(word);
+            const int c = __popc(m);
+            const int incl = warp_inclusive_scan(c);
+            const int tot = __shfl_sync(kFull, incl, 31);
+            if (tot == 0) continue;
+            if (sh + sc + tot > kCntStageP) {
+                __syncwarp();
+                flush_warp_ids(a.out_z + (wpos - sh), sz, sh, sc, a.dict_z, a.vec_ok);
+                flush_warp(a.out_c + (wpos - sh), sc_, sh, sc, a.vec_ok);
+                __syncwarp();
+                wpos += sc;
+                sh = (int)(wpos & 3);
+                sc = 0;
+            }
+            int pos = sh + sc + incl - c;
+            while (m) {
+                const int slot = __ffs(m) - 1;
+                m &= m - 1;
+                sz[pos] = (int32_t)(zt0 + (int64_t)w * CPW + slot);
+                sc_[pos] = (int32_t)((word >> (CB * slot)) & CMASK);
+                ++pos;
+            }
+            sc += tot;
+        }
+        __syncwarp();
+        if (sc) {
+            flush_warp_ids(a.out_z + (wpos - sh), sz, sh, sc, a.dict_z, a.vec_ok);
+            flush_warp(a.out_c + (wpos - sh), sc_, sh, sc, a.vec_ok);
+        }
+        __syncwarp();
+        out_pos += tile_total;
+        __syncthreads();
+    }
+    if (!kEmit && tid == 0) a.cnt[xr] = total;
+}
+
+__global__ void k_max_row(const int64_t* __restrict__ rowptr, int64_t n, unsigned long long* out) {
+    __shared__ unsigned long long s_w[kThreads / 32 + 1];
+    unsigned long long m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)(rowptr[i + 1] - rowptr[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kThreads / 32; ++w) m = max(m, s_w[w]);
+        atomicMax(out, m);
+    }
 }
 
 // cnt[row] = pairs of the row's units, for the listed rows
@@ -1545,6 +1711,62 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
     DIM3_LAUNCHED();
 }
 
+// Join-Count rows of a single instance go through k_cnt_rows.
+static bool use_packed_counts(const Plan& p, int kind) { return kind == 1 && p.n_inst == 1; }
+
+// Counter width of k_cnt_rows: the largest |R[x]| bounds every count.
+static int counter_bits(Plan& p, cudaStream_t s) {
+    if (p.max_mx < 0) {
+        DevBuf m;
+        m.alloc(8, s);
+        DIM3_CUDA(cudaMemsetAsync(m.p, 0, 8, s));
+        if (p.info.n_x > 0) {
+            k_max_row<<<blocks_for(p.info.n_x), kThreads, 0, s>>>(p.r_rowptr.as<int64_t>(), p.info.n_x,
+                                                                 m.as<unsigned long long>());
+            DIM3_LAUNCHED();
+        }
+        p.max_mx = read_i64(m.as<int64_t>(), s);
+    }
+    return p.max_mx <= 255 ? 8 : p.max_mx <= 65535 ? 16 : 32;
+}
+
+// Arguments of k_cnt_rows: z per tile = counter words (at most kMaxPackedWords,
+// equal tiles) x counters per word; tile starts when there are several tiles.
+static XRowArgs cnt_args(Plan& p, int64_t x_begin, int64_t rows, int cb, cudaStream_t s) {
+    XRowArgs a = make_args(p, x_begin, rows, 1);
+    const int64_t cpw = 32 / cb;
+    const int64_t words = std::max<int64_t>(1, ceil_div(p.info.n_z, cpw));
+    const int64_t n_tiles = ceil_div(words, kMaxPackedWords);
+    a.tile_bits = ceil_div(words, n_tiles) * cpw;
+    a.n_tiles = (int)ceil_div(std::max<int64_t>(p.info.n_z, 1), a.tile_bits);
+    a.tile_ptr = nullptr;
+    if (a.n_tiles > 1) {
+        ensure_tile_ptr(p, 1, a.tile_bits, s);
+        a.tile_ptr = p.tile_ptr[1].as<int64_t>();
+        a.tile_cols = p.tile_cols[1];
+    }
+    return a;
+}
+
+static void launch_cnt(const Ctx& ctx, const XRowArgs& a, int cb, bool emit, cudaStream_t s) {
+    if (a.n_rows <= 0 || a.n_z <= 0) return;
+    DIM3_REQUIRE(a.n_rows < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long");
+    PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
+    const size_t words = (size_t)ceil_div(a.tile_bits, 32 / cb);
+    const size_t sm = (emit ? (size_t)2 * kWarps * kCntStageP * 4 : 0) + words * 4;
+    const unsigned g = (unsigned)a.n_rows;
+#define DIM3_CNT_LAUNCH(CB)                                                 \
+    do {                                                                    \
+        if (emit) k_cnt_rows<CB, true><<<g, kThreads, sm, s>>>(a);          \
+        else k_cnt_rows<CB, false><<<g, kThreads, sm, s>>>(a);              \
+    } while (0)
+    if (cb == 8) DIM3_CNT_LAUNCH(8);
+    else if (cb == 16) DIM3_CNT_LAUNCH(16);
+    else DIM3_CNT_LAUNCH(32);
+#undef DIM3_CNT_LAUNCH
+    DIM3_LAUNCHED();
+}
+
 // One (row, tile) unit per CTA: counting (a.tcnt) or emitting (a.tcnt_in).
 static void launch_tiles(const Ctx& ctx, const XRowArgs& a, bool emit, cudaStream_t s) {
     const int64_t units = a.n_list * a.n_tiles;
@@ -1599,6 +1821,11 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
     if (rows > 0) {
         if (p.info.n_z <= 0 || p.info.n_r_kept == 0) {
             DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
+        } else if (use_packed_counts(p, kind)) {
+            XRowArgs a = cnt_args(p, x_begin, rows, counter_bits(p, s), s);
+            a.d_cnt = p.cache_dcnt.as<int32_t>();
+            a.cnt = cnt.as<int64_t>();
+            launch_cnt(ctx, a, counter_bits(p, s), false, s);
         } else if (use_tiles(ctx, p, kind)) {
             XRowArgs a = tile_args(p, x_begin, rows, tile_words_for(ctx, p) * 32, s);
             a.d_bits = p.cache_dbits.as<uint32_t>();
@@ -1742,7 +1969,19 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
     if (count) *count = total;
     if (total > capacity) throw Error(DIM3_ERR_CAPACITY, "output capacity " + std::to_string(capacity) +
                                                              " < result size " + std::to_string(total));
-    if (total > 0 && use_tiles(ctx, p, kind)) {
+    if (total > 0 && use_packed_counts(p, kind)) {
+        DIM3_REQUIRE(out_x && out_z && out_cnt, DIM3_ERR_ARG, "null output buffer");
+        const int cb = counter_bits(p, s);
+        XRowArgs a = cnt_args(p, x_begin, rows, cb, s);
+        a.d_cnt = p.cache_dcnt.as<int32_t>();
+        a.off = p.cache_off.as<int64_t>();
+        a.out_x = out_x;
+        a.out_z = out_z;
+        a.out_c = out_cnt;
+        a.vec_ok = ((reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z) |
+                     reinterpret_cast<uintptr_t>(out_cnt)) & 15u) == 0;
+        launch_cnt(ctx, a, cb, true, s);
+    } else if (total > 0 && use_tiles(ctx, p, kind)) {
         DIM3_REQUIRE(out_x && out_z, DIM3_ERR_ARG, "null output buffer");
         XRowArgs a = tile_args(p, x_begin, rows, p.cache_tile_bits, s);
         a.d_bits = p.cache_dbits.as<uint32_t>();
