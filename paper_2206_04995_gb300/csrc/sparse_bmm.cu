@@ -1750,6 +1750,17 @@ static XRowArgs cnt_args(Plan& p, int64_t x_begin, int64_t rows, int cb, cudaStr
 
 static void launch_cnt(const Ctx& ctx, const XRowArgs& a, int cb, bool emit, cudaStream_t s) {
     if (a.n_rows <= 0 || a.n_z <= 0) return;
+    static bool done[64] = {false};
+    if (!done[ctx.device & 63]) {
+        const int mx = (int)((size_t)2 * kWarps * kCntStageP * 4 + (size_t)kMaxPackedWords * 4);
+        DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        done[ctx.device & 63] = true;
+    }
     DIM3_REQUIRE(a.n_rows < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long");
     PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
     const size_t words = (size_t)ceil_div(a.tile_bits, 32 / cb);

@@ -30,6 +30,8 @@ def _wide_hub(seed, n_hub_y):
 
 CASES = {
     "cb8_multi_tile": lambda: gen.small_two_table(31, n_r=60_000, n_s=60_000, nx=6000, ny=2000, nz=200_000),
+    # 28,000 z: one tile of ~7,000 counter words, the largest shared-memory footprint
+    "cb8_largest_tile": lambda: gen.small_two_table(37, n_r=3000, n_s=200_000, nx=500, ny=2000, nz=28_000),
     "cb8_one_tile": lambda: gen.small_two_table(32, n_r=40_000, n_s=40_000, nx=4000, ny=1000, nz=3000, zipf=0.8),
     "cb16_multi_tile": lambda: gen.small_two_table(33, n_r=40_000, n_s=40_000, nx=50, ny=5000, nz=60_000, zipf=1.0),
     "cb16_power_law": lambda: gen.chung_lu_self(np.random.default_rng(34), 60_000, 80_000, 2.1),
