@@ -68,6 +68,10 @@ def parse_args():
                          "point with the forced hybrid and classical times and f1's choice")
     ap.add_argument("--count", action="store_true",
                     help="time dim3_join_count (Join-Aggregate COUNT per pair) instead of dim3_join_project")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (theta_z, DenseEC variant, emit rows) before timing")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload only: skip the batch256, serve2000 and chung_lu_1m_4m sub-records")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -351,6 +355,13 @@ def main():
         k, v = kv.split("=")
         ctx.set_option(int(k), int(v))
 
+    tuned = None
+    if (not args.no_tune and theta is None and variant is None and not args.opt and ranges is None
+            and args.cache_budget is None and not args.count):
+        from paper_2206_04995_gb300 import tune
+
+        tuned = tune.summary(tune.tune(ctx, cols, use_cache=False))
+
     cache = None
     cache_cfg = None
     if args.cache_budget is not None:
@@ -471,6 +482,18 @@ def main():
             check = (boundary_x(torch, out_x, out_p), lambda xs: rows_on_device(torch, out_x, out_z, xs))
         cpu, verified = cpu_baseline(inst, args.cpu_seconds, check=check)
 
+    sub = None
+    if (rank == 0 and world == 1 and not args.no_sub and args.workload == "two_table_1m_zipf1" and args.scale == 1.0
+            and ranges is None and cache is None and not args.count):
+        # the other configured workloads, each with its own timing: the
+        # headline's buffers are released first
+        ctx.close()
+        del out_x, out_z, out_c, flush
+        torch.cuda.empty_cache()
+        sub = {"batch256": run_batch(args, rank, world, local_rank, sub=True),
+               "chung_lu_1m_4m": onecall_record("chung_lu_1m_4m", local_rank),
+               "serve2000": serve_record(args, local_rank)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -483,7 +506,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "mapping": ("skipped: pre-mapped id columns (dim3_partition_ids); output pairs are ids"
                                    if ranges else "order-preserving hash + radix rank (dim3_join_project)"),
-                       "partial_result_cache": cache_cfg,
+                       "partial_result_cache": cache_cfg, "tuner": tuned,
                        "join_tuples_per_s": info["out_j"] * args.steps * (pairs_all / total_pairs) / busy_max},
             "roofline": roofline,
             "phase_ms": phases,
@@ -493,6 +516,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "verified": verified,
+            "sub": sub,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -500,10 +524,88 @@ def main():
     ctx.close()
 
 
-def run_batch(args, rank, world, local_rank):
+def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, tune_it: bool = True):
+    """A compact record of one workload through the one-call path
+    (dim3_join_project into caller buffers), tuned first: pairs/s, phases and
+    the emitting pass's HBM roofline."""
+    import torch
+
+    import paper_2206_04995_gb300 as dim3
+
+    dev = torch.device("cuda", local_rank)
+    inst = make_workload(name, 0)
+    cols = device_columns(torch, [inst.r_key, inst.r_val, inst.s_key, inst.s_val], dev)
+    ctx = dim3.Context(local_rank)
+    tuned = None
+    if tune_it:
+        from paper_2206_04995_gb300 import tune
+
+        tuned = tune.summary(tune.tune(ctx, cols, use_cache=False))
+    plan = ctx.partition(*cols)
+    info = plan.info
+    out_p = int(plan.row_counts().sum().item())
+    plan.close()
+    out_x = torch.empty(out_p, dtype=torch.int32, device=dev)
+    out_z = torch.empty(out_p, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    for _ in range(warmup):
+        ctx.join_project(*cols, out_x=out_x, out_z=out_z)
+    torch.cuda.synchronize()
+    ctx.set_option(dim3.OPT_TIMING, 1)
+    ctx.timing(reset=True)
+    ms = []
+    for k in range(steps):
+        flush.fill_(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, _ = ctx.join_project(*cols, out_x=out_x, out_z=out_z)
+        e1.record()
+        torch.cuda.synchronize()
+        assert x.numel() == out_p
+        ms.append(e0.elapsed_time(e1))
+    tm = ctx.timing()
+    ctx.close()
+    peaks = measured_peaks()
+    emit_s = tm["sparse_emit"][0] / 1e3 / steps
+    alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
+    achieved = alg_bytes / emit_s / 1e9 if emit_s > 0 else None
+    del out_x, out_z, flush
+    torch.cuda.empty_cache()
+    return {"pairs_per_s": out_p * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps, "steps": steps,
+            "out_p": out_p, "out_j": info["out_j"], "n_x": info["n_x"], "n_z": info["n_z"],
+            "n_z_dense": info["n_z_dense"], "phase_ms": {k: round(v[0] / steps, 4) for k, v in tm.items() if v[1]},
+            "roofline": {"bound": "hbm", "kernel": "emitting pass (k_tile_rows<emit> + k_light_rows<emit>, or "
+                         "k_xrow_emit_g)", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm"] if achieved else None, "peak_source": peaks["source"],
+                         "alg_bytes_per_launch": alg_bytes, "launch_ms": emit_s * 1e3},
+            "tuner": tuned, "l2": "flushed between steps"}
+
+
+def serve_record(args, local_rank: int):
+    """A compact record of the full query stream, served and plain, queued
+    and Poisson (see run_serve)."""
+    import torch
+
+    dev = torch.device("cuda", local_rank)
+    t0 = time.perf_counter()
+    qs = serve_queries(torch, args.serve_queries, args.serve_max_tuples, 0, dev)
+    gen_s = time.perf_counter() - t0
+    serve_runs(torch, qs[: min(len(qs), 40)], local_rank, args.serve_workers, modes=("queued",))
+    r = serve_runs(torch, qs, local_rank, args.serve_workers)
+    keep = ("pairs_per_s", "wall_s", "p50_ms", "p99_ms", "mean_batch", "offered_pairs_per_s")
+    out = {k: ({kk: v[kk] for kk in keep} if isinstance(v, dict) else v) for k, v in r.items()}
+    out.update(queries=len(qs), pairs=r["served_queued"]["pairs"], tuples=int(sum(q.tuples for q in qs)),
+               inputs_s=gen_s, workers=args.serve_workers)
+    del qs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args, rank, world, local_rank, sub=False):
     """256 independent two-table instances (log-uniform sizes): one step is
     ONE dim3_batch_join_project call over all of them; the same instances run
-    one call each (the plain path) beside it for the ratio."""
+    one call each (the plain path) beside it for the ratio. With sub, returns
+    a compact record (no end-to-end or oracle legs) instead of printing."""
     import torch
 
     import gen
@@ -518,6 +620,12 @@ def run_batch(args, rank, world, local_rank):
     for kv in args.opt:
         k, v = kv.split("=")
         ctx.set_option(int(k), int(v))
+    tuned = None
+    if not args.no_tune and not args.opt:
+        from paper_2206_04995_gb300 import tune
+
+        tuned = tune.summary(tune.tune(ctx, cols, batch=True, use_cache=False))
+    steps, warmup = (10, 3) if sub else (args.steps, args.warmup)
     plan = ctx.batch_partition(cols)
     info = plan.info
     out_p = int(plan.row_counts().sum().item())
@@ -558,11 +666,11 @@ def run_batch(args, rank, world, local_rank):
             ms.append(e0.elapsed_time(e1))
         return ms
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched()
         plain()
     torch.cuda.synchronize()
-    plain_ms = timed(plain, max(1, min(args.steps, 3)))
+    plain_ms = timed(plain, max(1, min(steps, 3)))
     ctx.set_option(dim3.OPT_TIMING, 1)
     ctx.timing(reset=True)
     sampler = ClockSampler(local_rank)
@@ -570,20 +678,31 @@ def run_batch(args, rank, world, local_rank):
     l0 = dim3.launch_count()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
-    batch_ms = timed(batched, args.steps)
+    batch_ms = timed(batched, steps)
     t_wall = time.perf_counter() - t_wall
     launches = dim3.launch_count() - l0
     clocks = sampler.stop()
     tm = ctx.timing()
     ctx.set_option(dim3.OPT_TIMING, 0)
     busy = sum(batch_ms) / 1e3
-    value = out_p * args.steps / busy
+    value = out_p * steps / busy
     plain_value = out_p * len(plain_ms) / (sum(plain_ms) / 1e3)
     peaks = measured_peaks()
     emit_ms, emit_n = tm["sparse_emit"]
     emit_s = emit_ms / 1e3 / max(emit_n, 1)
     alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
     achieved = alg_bytes / emit_s / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_xrow_bits<emit> over all instances", "achieved": achieved,
+                "peak": peaks["hbm"], "unit": "GB/s", "frac": achieved / peaks["hbm"],
+                "peak_source": peaks["source"], "traffic": None, "alg_bytes_per_launch": alg_bytes,
+                "launch_ms": emit_s * 1e3}
+    phase_ms = {k: round(v[0] / max(v[1], 1), 4) for k, v in tm.items() if v[1]}
+    if sub:
+        ctx.close()
+        return {"pairs_per_s": value, "ms_per_step": sum(batch_ms) / len(batch_ms), "steps": steps,
+                "plain_pairs_per_s": plain_value, "plain_ms_per_step": sum(plain_ms) / len(plain_ms),
+                "batched_over_plain": value / plain_value, "out_p": out_p, "n_inst": len(insts),
+                "roofline": roofline, "phase_ms": phase_ms, "gpu_launches": launches, "tuner": tuned}
     e2e = None
     if not args.no_e2e:
         h_in = [[c.cpu().pin_memory() for c in cc] for cc in cols]
@@ -616,18 +735,15 @@ def run_batch(args, rank, world, local_rank):
                "sample": f"{len(small)} of the 256 instances (every 16th by size), whole; {n} pairs in {dt:.2f} s"}
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sum(batch_ms) / len(batch_ms), "higher_is_better": True,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": sum(batch_ms) / len(batch_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "batch256", "n_inst": len(insts), "tuples": int(sum(i.nr + i.ns for i in insts)),
                        "out_p": out_p, "out_j": info["out_j"], "plain_pairs_per_s": plain_value,
                        "plain_ms_per_step": sum(plain_ms) / len(plain_ms), "batched_over_plain": value / plain_value,
-                       "l2": "flushed between steps (256 MiB write outside the step events)"},
-            "roofline": {"bound": "hbm", "kernel": "k_xrow_bits<emit> over all instances", "achieved": achieved,
-                         "peak": peaks["hbm"], "unit": "GB/s", "frac": achieved / peaks["hbm"],
-                         "peak_source": peaks["source"], "traffic": None, "alg_bytes_per_launch": alg_bytes,
-                         "launch_ms": emit_s * 1e3},
-            "phase_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in tm.items() if v[1]},
+                       "tuner": tuned, "l2": "flushed between steps (256 MiB write outside the step events)"},
+            "roofline": roofline,
+            "phase_ms": phase_ms,
             "wall_s": t_wall, "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }), flush=True)
     ctx.close()

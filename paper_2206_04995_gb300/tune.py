@@ -73,15 +73,21 @@ def dense_estimate(m_z: np.ndarray, theta: int, n_x: int, n_y: int):
     return n_zd, flops, bytes_
 
 
-def _time_join(ctx, cols, out_x, out_z, repeats: int) -> float:
-    ctx.join_project(*cols, out_x=out_x, out_z=out_z)  # warm
+def _time_join(ctx, cols, out_x, out_z, repeats: int, batch: bool = False) -> float:
+    def call():
+        if batch:
+            ctx.batch_join_project(cols, out_x=out_x, out_z=out_z)
+        else:
+            ctx.join_project(*cols, out_x=out_x, out_z=out_z)
+
+    call()  # warm
     torch.cuda.synchronize()
     best = float("inf")
     for _ in range(repeats):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        ctx.join_project(*cols, out_x=out_x, out_z=out_z)
+        call()
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
@@ -89,16 +95,17 @@ def _time_join(ctx, cols, out_x, out_z, repeats: int) -> float:
 
 
 def tune(ctx: dim3.Context, cols, repeats: int = 2, cache_path: str | None = None, use_cache: bool = True,
-         apply: bool = True) -> dict:
+         apply: bool = True, batch: bool = False) -> dict:
     """Choose theta_z, the DenseEC variant and the emit rows per CTA for the
-    input `cols` = (r_key, r_val, s_key, s_val) on device; set them on `ctx`
-    (apply) and return the decision with the timings it rests on."""
-    plan = ctx.partition(*cols, theta_z=INF)
+    input `cols` = (r_key, r_val, s_key, s_val) on device -- or, with batch,
+    a list of such instances timed through one batched call; set them on
+    `ctx` (apply) and return the decision with the timings it rests on."""
+    plan = ctx.batch_partition(cols, theta_z=INF) if batch else ctx.partition(*cols, theta_z=INF)
     info = plan.info
     m_z = plan.export("m_z").cpu().numpy().astype(np.int64)
     out_p = int(plan.row_counts().sum().item())
     plan.close()
-    key = shape_key(info, int(m_z.max()) if m_z.size else 0)
+    key = shape_key(info, int(m_z.max()) if m_z.size else 0) + ("|batch" if batch else "")
     path = cache_path or default_cache_path()
     if use_cache:
         with _lock:
@@ -127,11 +134,11 @@ def tune(ctx: dim3.Context, cols, repeats: int = 2, cache_path: str | None = Non
                                "n_zd": n_zd, "flops": flops})
                 continue
         for v in variants:
-            for rows in (2, 1):
+            for rows in ((1,) if batch else (2, 1)):
                 cfg = {"theta": int(theta), "variant": int(v), "emit_rows": rows}
                 _apply(ctx, cfg)
                 try:
-                    ms = _time_join(ctx, cols, out_x, out_z, repeats)
+                    ms = _time_join(ctx, cols, out_x, out_z, repeats, batch)
                 except dim3.Dim3Error as e:
                     trials.append(dict(cfg, error=str(e)))
                     continue
@@ -165,3 +172,13 @@ def _apply(ctx, cfg: dict):
     ctx.set_option(dim3.OPT_THETA_Z, int(cfg["theta"]))
     ctx.set_option(dim3.OPT_DENSE_VARIANT, int(cfg["variant"]))
     ctx.set_option(dim3.OPT_EMIT_ROWS, int(cfg.get("emit_rows", 0)))
+
+
+def summary(decision: dict) -> dict:
+    """The decision without its trial list, plus the number of candidates
+    timed and skipped (for a bench line's config)."""
+    trials = decision.get("trials", [])
+    out = {k: v for k, v in decision.items() if k != "trials"}
+    out["timed"] = sum(1 for t in trials if "ms" in t)
+    out["skipped"] = sum(1 for t in trials if "skipped" in t)
+    return out

@@ -48,3 +48,29 @@ def test_tuner_decision_is_exact_and_cached(tmp_path):
         assert again["cached"] and again["theta"] == d["theta"] and again["variant"] == d["variant"]
         ctx.close()
         torch.cuda.synchronize()
+
+
+def test_summary_counts_trials():
+    d = {"theta": 5, "variant": 1, "emit_rows": 1, "ms": 1.0, "trials": [{"ms": 1.0}, {"skipped": "x"}, {"ms": 2.0}]}
+    s = tune.summary(d)
+    assert "trials" not in s and s["timed"] == 2 and s["skipped"] == 1 and s["theta"] == 5
+
+
+@pytest.mark.gpu
+def test_tuner_on_a_batch_is_exact(tmp_path):
+    """Tuning over a batch (timed through the batched call) leaves every
+    instance's result equal to the oracle's."""
+    import paper_2206_04995_gb300 as dim3
+    from tests.gpu_util import host, inst_dev
+
+    insts = gen.config4_batch(n_inst=12, lo=1000, hi=30_000)
+    ctx = dim3.Context(0)
+    cols = [inst_dev(i) for i in insts]
+    d = tune.tune(ctx, cols, batch=True, cache_path=str(tmp_path / "t.json"))
+    assert not d["cached"] and d["key"].endswith("|batch")
+    x, z, per = ctx.batch_join_project(cols)
+    off = np.concatenate([[0], np.cumsum(per)])
+    for t, i in enumerate(insts):
+        ox, oz, _ = oracle.join_project(i.r_key, i.r_val, i.s_key, i.s_val)
+        assert np.array_equal(host(x[off[t]:off[t + 1]]), ox) and np.array_equal(host(z[off[t]:off[t + 1]]), oz)
+    ctx.close()
