@@ -30,7 +30,8 @@ if ROOT not in sys.path:
 
 METRIC = "dedup (x,z) pairs/s on 1 GB300 vs plain path; served p50/p99 latency"
 UNIT = "pairs/s"
-WORKLOADS = ("two_table_1m_zipf1", "self_20k", "chung_lu_1m_4m", "dense_16k", "batch256", "serve2000")
+WORKLOADS = ("two_table_1m_zipf1", "self_20k", "chung_lu_1m_4m", "chung_lu_uncapped_x0.25", "dense_16k", "batch256",
+             "serve2000")
 # fp8 (f8f6f4) dense tensor rate = 2 x bf16 (nominal 4.5 vs 2.25 PFLOP/s)
 FP8_PER_BF16 = 2.0
 
@@ -91,6 +92,8 @@ def make_workload(name: str, rank: int = 0, scale: float = 1.0):
         n = max(64, int(16384 * scale))
         return gen.two_table(np.random.default_rng(7 + 1000 * rank), 16 * n * n // 1024, 16 * n * n // 1024,
                              n, n, n, 0.0, name=f"dense_{n}")
+    if name == "chung_lu_uncapped_x0.25":
+        return gen.chung_lu_uncapped(seed=2 + 1000 * rank, scale=0.25 * scale)
     return gen.config3_chung_lu(seed=2 + 1000 * rank, scale=scale)
 
 
@@ -492,6 +495,7 @@ def main():
         torch.cuda.empty_cache()
         sub = {"batch256": run_batch(args, rank, world, local_rank, sub=True),
                "chung_lu_1m_4m": onecall_record("chung_lu_1m_4m", local_rank),
+               "chung_lu_uncapped_x0.25": onecall_record("chung_lu_uncapped_x0.25", local_rank),
                "serve2000": serve_record(args, local_rank)}
 
     if rank == 0:
@@ -566,6 +570,14 @@ def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, 
     tm = ctx.timing()
     ctx.close()
     peaks = measured_peaks()
+    dense = None
+    if tm["dense_tc"][1]:
+        tc_s = tm["dense_tc"][0] / 1e3 / tm["dense_tc"][1]
+        flops = 2.0 * info["n_x"] * info["n_y_dense"] * info["n_z_dense"]
+        peak = peaks["bf16"] * FP8_PER_BF16
+        dense = {"bound": "tensor", "kernel": "k_dense_tc", "achieved": flops / tc_s / 1e12, "peak": peak,
+                 "unit": "TFLOP/s", "frac": flops / tc_s / 1e12 / peak, "launch_ms": tc_s * 1e3,
+                 "peak_source": f"{peaks['source']} bf16 burst x {FP8_PER_BF16} (fp8/bf16 nominal ratio)"}
     emit_s = tm["sparse_emit"][0] / 1e3 / steps
     alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
     achieved = alg_bytes / emit_s / 1e9 if emit_s > 0 else None
@@ -578,7 +590,7 @@ def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, 
                          "k_xrow_emit_g)", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm"] if achieved else None, "peak_source": peaks["source"],
                          "alg_bytes_per_launch": alg_bytes, "launch_ms": emit_s * 1e3},
-            "tuner": tuned, "l2": "flushed between steps"}
+            "dense_roofline": dense, "tuner": tuned, "l2": "flushed between steps"}
 
 
 def serve_record(args, local_rank: int):

@@ -9,6 +9,7 @@ from .synth import (  # noqa: F401
     CONFIGS,
     Instance,
     chung_lu_self,
+    chung_lu_uncapped,
     config1_self,
     config2_two_table,
     config3_chung_lu,

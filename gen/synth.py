@@ -154,19 +154,21 @@ def config2_two_table(seed: int = 1, scale: float = 1.0) -> Instance:
 
 
 def chung_lu_self(rng: np.random.Generator, n_vertices: int, n_edges: int,
-                  beta: float, name: str = "chung_lu") -> Instance:
+                  beta: float, name: str = "chung_lu", cap: bool = True) -> Instance:
     """Self Join-Project over an undirected Chung-Lu power-law graph.
 
     Expected-degree weights w_i proportional to i^(-1/(beta-1)), scaled to sum
-    2 * n_edges and capped at sqrt(2 * n_edges) (the usual Chung-Lu
-    constraint); both endpoints of an edge are drawn proportionally to w.
-    Self-loops and multi-edges are dropped and the draw is topped up to
-    exactly n_edges edges. R = S holds both directions of every edge.
+    2 * n_edges and, with cap, capped at sqrt(2 * n_edges) (the usual Chung-Lu
+    constraint; without it the hubs keep their power-law weight); both
+    endpoints of an edge are drawn proportionally to w. Self-loops and
+    multi-edges are dropped and the draw is topped up to exactly n_edges
+    edges. R = S holds both directions of every edge.
     """
     i = np.arange(1, n_vertices + 1, dtype=np.float64)
     w = i ** (-1.0 / (beta - 1.0))
     w *= 2.0 * n_edges / w.sum()
-    w = np.minimum(w, math.sqrt(2.0 * n_edges))
+    if cap:
+        w = np.minimum(w, math.sqrt(2.0 * n_edges))
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
 
@@ -195,6 +197,20 @@ def config3_chung_lu(seed: int = 2, scale: float = 1.0) -> Instance:
     ne = max(16, int(4_000_000 * scale))
     inst = chung_lu_self(rng, nv, ne, 2.1,
                          name="chung_lu_1m_4m" if scale == 1.0 else f"chung_lu_x{scale:g}")
+    inst.meta["seed"] = seed
+    return inst
+
+
+def chung_lu_uncapped(seed: int = 2, scale: float = 1.0) -> Instance:
+    """The Chung-Lu graph of config3_chung_lu without the weight cap (degree
+    exponent 2.1, hubs with degrees near 10^5 at full size): a two-hop
+    Join-Project whose hub z are dense enough for DenseEC. ``scale`` shrinks
+    the vertex and edge counts proportionally."""
+    rng = np.random.default_rng(seed)
+    nv = max(16, int(1_000_000 * scale))
+    ne = max(16, int(4_000_000 * scale))
+    inst = chung_lu_self(rng, nv, ne, 2.1, cap=False,
+                         name="chung_lu_uncapped_1m_4m" if scale == 1.0 else f"chung_lu_uncapped_x{scale:g}")
     inst.meta["seed"] = seed
     return inst
 

@@ -139,8 +139,9 @@ typedef enum {
                                    0: always group by group; <0: default (512); at most 1024 */
     DIM3_OPT_PATH = 9,          /* dim3_join_project / dim3_join_count: 0 (default) f1 of Section 2.6
                                    chooses, 1 the hybrid DIM^3 path, 2 the classical solution */
-    DIM3_OPT_TILE_WORDS = 10    /* z ranges wider than one shared-memory bitmap (393,216 z): 32-bit words
+    DIM3_OPT_TILE_WORDS = 10,   /* z ranges wider than one shared-memory bitmap (393,216 z): 32-bit words
                                    per z tile, 1024..12288; 0 (default): the fewest tiles, equal sizes */
+    DIM3_OPT_DENSE_TILE_N = 11  /* tensor-core DenseEC: dense z per CTA tile, 128 or 256; 0 (default): 256 */
 } dim3_option;
 
 /* Phases timed under DIM3_OPT_TIMING. */

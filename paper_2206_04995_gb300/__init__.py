@@ -36,6 +36,7 @@ from .dim3 import (  # noqa: F401
     OPT_LIGHT_ROW_MAX,
     OPT_PATH,
     OPT_TILE_WORDS,
+    OPT_DENSE_TILE_N,
     PATH_AUTO,
     PATH_CLASSICAL,
     PATH_HYBRID,

@@ -55,7 +55,7 @@ void dense_build_operands(const Ctx& ctx, Plan& p, const uint64_t* keys64, const
     p.zdw = p.zdw_op;  // widened by a partial result cache after the split
     p.kw = ceil_div(K, 32);
     p.k_pad = ceil_div(K, kTcBlockK) * kTcBlockK;
-    p.n_zd_pad = ceil_div(n_zd, kTcTileN) * kTcTileN;
+    p.n_zd_pad = ceil_div(n_zd, kTcPadN) * kTcPadN;
     if (variant == DIM3_DENSE_POPC) {
         p.b_bits.alloc((size_t)(n_zd * p.kw) * 4, s);
         DIM3_CUDA(cudaMemsetAsync(p.b_bits.p, 0, p.b_bits.bytes, s));
@@ -329,7 +329,7 @@ static void dense_product(const Ctx& ctx, const Plan& p, int64_t x_begin, int64_
         DevBuf tl;
         int64_t nt = 0;
         if (batch) {
-            nt = upload_block_tiles(p, x_begin, rows, kTcTileM, kTcTileN, tl, s);
+            nt = upload_block_tiles(p, x_begin, rows, kTcTileM, tc_tile_n(ctx), tl, s);
             if (nt == 0) return;
         }
         tc_dense_product(ctx, a.as<uint8_t>(), rows, rows_pad, p.b_tc.as<uint8_t>(), n_zd, p.n_zd_pad, p.k_pad, kind,

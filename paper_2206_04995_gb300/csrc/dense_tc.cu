@@ -10,10 +10,12 @@
 // Join-Count. The paper's early stop has no tensor-core analog; the tile
 // runs over all of K.
 //
-// One CTA computes a 128 x 256 tile of C (128 TMEM lanes x 256 FP32 columns):
-//   warp 0, one lane : TMA producer, 4-stage ring of (A 16 KB, B 32 KB) tiles
-//                      with 128-byte swizzle, one mbarrier pair per stage;
-//   warp 1, one lane : MMA issuer, 4 x (M128 N256 K32) per stage, commits to
+// One CTA computes a 128 x N tile of C (128 TMEM lanes x N FP32 columns, N =
+// 256 or 128, the DIM3_OPT_DENSE_TILE_N option):
+//   warp 0, one lane : TMA producer, a ring of (A 16 KB, B N x 128 B) tiles
+//                      (4 stages for N = 256, 6 for N = 128) with 128-byte
+//                      swizzle, one mbarrier pair per stage;
+//   warp 1, one lane : MMA issuer, 4 x (M128 N K32) per stage, commits to
 //                      the stage's "empty" barrier and finally to "done";
 //   warps 0-3        : epilogue, each warp reads its 32 TMEM lanes with
 //                      tcgen05.ld and writes result bits (or counts).
@@ -29,21 +31,27 @@
 
 namespace dimcube {
 
-constexpr int kStages = 4;
 constexpr int kTcThreads = 128;
 constexpr uint32_t kStageBytesA = kTcTileM * kTcBlockK;  // 16 KiB
-constexpr uint32_t kStageBytesB = kTcTileN * kTcBlockK;  // 32 KiB
-constexpr uint32_t kStageBytes = kStageBytesA + kStageBytesB;
-constexpr uint32_t kTmemCols = kTcTileN;  // one FP32 column per output column
-constexpr uint32_t kTcSmem = kStages * kStageBytes + 1024 + 256;
 constexpr uint32_t kWaitLimit = 1u << 26;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr int kGroupM = 16;  // row tiles per raster group (see k_dense_tc)
 
-// Instruction descriptor of tcgen05.mma.kind::f8f6f4: D = F32 (bits 4-5 = 1),
-// A = B = E4M3 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(kTcTileN >> 3) << 17) |
-                            ((uint32_t)(kTcTileM >> 4) << 24);
+// Pipeline shape of a CTA computing a 128 x N tile (N = 256 or 128): the B
+// tile of a stage is N rows of 128 K bytes; narrower tiles afford more stages.
+template <int N>
+struct TcShape {
+    static constexpr int kStages = N == 256 ? 4 : 6;
+    static constexpr uint32_t kStageBytesB = (uint32_t)N * kTcBlockK;
+    static constexpr uint32_t kStageBytes = kStageBytesA + kStageBytesB;
+    static constexpr uint32_t kTmemCols = N;  // one FP32 column per output column
+    static constexpr uint32_t kSmem = kStages * kStageBytes + 1024 + 256;
+    // Instruction descriptor of tcgen05.mma.kind::f8f6f4: D = F32 (bits 4-5 =
+    // 1), A = B = E4M3 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0),
+    // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+    static constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) |
+                                       ((uint32_t)(kTcTileM >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -144,25 +152,43 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
     return d;
 }
 
-template <int kKind>
+// Tile order: without a tile list the CTAs run down groups of kGroupM row
+// tiles, the row tile changing fastest (b = group * kGroupM * n_n + n * gm +
+// m_in_group), so CTAs that run together share their B tiles (each read by
+// up to kGroupM CTAs in a row) and a group's A tiles stay in L2 while it
+// sweeps every column tile.
+template <int kKind, int N>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_dense_tc(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b, int64_t rows,
                int64_t n_zd, int num_kb, uint32_t* __restrict__ d_bits, int64_t zdw, int32_t* __restrict__ d_cnt,
-               int* err, const int2* __restrict__ tiles) {
+               int* err, const int2* __restrict__ tiles, int n_m, int n_n) {
+    using Sh = TcShape<N>;
+    constexpr int kStages = Sh::kStages;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = base;
     uint8_t* sB = base + kStages * kStageBytesA;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kStageBytesB);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * Sh::kStageBytesB);
     uint64_t* empty = full + kStages;
     uint64_t* done = empty + kStages;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // batches compute only the tiles of the block-diagonal (tile list)
-    const int64_t m0 = (int64_t)(tiles ? tiles[blockIdx.x].x : (int)blockIdx.y) * kTcTileM;
-    const int64_t n0 = (int64_t)(tiles ? tiles[blockIdx.x].y : (int)blockIdx.x) * kTcTileN;
+    int tm, tn;
+    if (tiles) {
+        // batches compute only the tiles of the block-diagonal (tile list)
+        tm = tiles[blockIdx.x].x;
+        tn = tiles[blockIdx.x].y;
+    } else {
+        const int b = (int)blockIdx.x, per_group = kGroupM * n_n;
+        const int g = b / per_group, r = b - g * per_group;
+        const int first = g * kGroupM, gm = min(kGroupM, n_m - first);
+        tm = first + r % gm;
+        tn = r / gm;
+    }
+    const int64_t m0 = (int64_t)tm * kTcTileM;
+    const int64_t n0 = (int64_t)tn * N;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -176,7 +202,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap_b)) : "memory");
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_alloc(tmem_slot, Sh::kTmemCols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -194,9 +220,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             if (s_abort) break;
-            mbar_expect_tx(&full[s], kStageBytes);
+            mbar_expect_tx(&full[s], Sh::kStageBytes);
             tma_load_2d(sA + s * kStageBytesA, &tmap_a, &full[s], kb * kTcBlockK, (int32_t)m0);
-            tma_load_2d(sB + s * kStageBytesB, &tmap_b, &full[s], kb * kTcBlockK, (int32_t)n0);
+            tma_load_2d(sB + s * Sh::kStageBytesB, &tmap_b, &full[s], kb * kTcBlockK, (int32_t)n0);
         }
     } else if (warp == 1 && lane == 0) {
         for (int kb = 0; kb < num_kb; ++kb) {
@@ -209,10 +235,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             tc_fence_after();
             const uint32_t a_addr = smem_u32(sA + s * kStageBytesA);
-            const uint32_t b_addr = smem_u32(sB + s * kStageBytesB);
+            const uint32_t b_addr = smem_u32(sB + s * Sh::kStageBytesB);
 #pragma unroll
             for (int k = 0; k < kTcBlockK / 32; ++k)
-                tc_mma(tmem, smem_desc_sw128(a_addr + 32u * k), smem_desc_sw128(b_addr + 32u * k), kIdesc,
+                tc_mma(tmem, smem_desc_sw128(a_addr + 32u * k), smem_desc_sw128(b_addr + 32u * k), Sh::kIdesc,
                        (kb | k) != 0 ? 1u : 0u);
             tc_commit(&empty[s]);
         }
@@ -228,7 +254,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int64_t row = m0 + warp * 32 + lane;
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 #pragma unroll 1
-        for (int c0 = 0; c0 < kTcTileN; c0 += 32) {
+        for (int c0 = 0; c0 < N; c0 += 32) {
             uint32_t v[32];
             tmem_ld32(tmem + lane_base + (uint32_t)c0, v);
             if (kKind == 0) {
@@ -254,7 +280,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, kTmemCols);
+        tmem_dealloc(tmem, Sh::kTmemCols);
     }
 }
 
@@ -289,35 +315,51 @@ static CUtensorMap make_map(const uint8_t* ptr, int64_t inner, int64_t outer, ui
 
 bool tc_supported(const Ctx& ctx) { return ctx.cc_major == 10 && ctx.cc_minor == 3; }
 
+int tc_tile_n(const Ctx& ctx) { return ctx.opt.dense_tile_n == 128 ? 128 : 256; }
+
+template <int N>
+static void launch_tc(const Ctx& ctx, const uint8_t* A, int64_t rows, int64_t rows_pad, const uint8_t* B,
+                      int64_t n_zd, int64_t n_pad, int64_t k_pad, int kind, uint32_t* d_bits, int64_t zdw,
+                      int32_t* d_cnt, const int2* tiles, int64_t n_tiles, int* err, cudaStream_t s) {
+    using Sh = TcShape<N>;
+    static bool attr_done[64] = {false};
+    if (!attr_done[ctx.device & 63]) {
+        DIM3_CUDA(cudaFuncSetAttribute(k_dense_tc<0, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::kSmem));
+        DIM3_CUDA(cudaFuncSetAttribute(k_dense_tc<1, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::kSmem));
+        attr_done[ctx.device & 63] = true;
+    }
+    DIM3_REQUIRE(n_pad % N == 0, DIM3_ERR_ARG, "dense operand not padded to the tile width");
+    const CUtensorMap ma = make_map(A, k_pad, rows_pad, kTcTileM);
+    const CUtensorMap mb = make_map(B, k_pad, n_pad, N);
+    const int n_m = (int)(rows_pad / kTcTileM), n_n = (int)(n_pad / N);
+    const int64_t blocks = tiles ? n_tiles : (int64_t)n_m * n_n;
+    DIM3_REQUIRE(blocks < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "too many DenseEC tiles");
+    const int num_kb = (int)(k_pad / kTcBlockK);
+    PhaseScope phase(ctx.stats, PH_DENSE_TC, s);
+    if (kind == 0)
+        k_dense_tc<0, N><<<(unsigned)blocks, kTcThreads, Sh::kSmem, s>>>(ma, mb, rows, n_zd, num_kb, d_bits, zdw,
+                                                                         nullptr, err, tiles, n_m, n_n);
+    else
+        k_dense_tc<1, N><<<(unsigned)blocks, kTcThreads, Sh::kSmem, s>>>(ma, mb, rows, n_zd, num_kb, nullptr, zdw,
+                                                                         d_cnt, err, tiles, n_m, n_n);
+    DIM3_LAUNCHED();
+}
+
 void tc_dense_product(const Ctx& ctx, const uint8_t* A, int64_t rows, int64_t rows_pad, const uint8_t* B, int64_t n_zd,
                       int64_t n_pad, int64_t k_pad, int kind, uint32_t* d_bits, int64_t zdw, int32_t* d_cnt,
                       const int2* tiles, int64_t n_tiles, cudaStream_t s) {
     if (rows <= 0 || n_zd <= 0 || (tiles && n_tiles <= 0)) return;
-    DIM3_REQUIRE(!tiles || n_tiles < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "too many DenseEC tiles");
     DIM3_REQUIRE(tc_supported(ctx), DIM3_ERR_UNSUPPORTED, "tensor-core DenseEC needs an sm_103 device");
     DIM3_REQUIRE(k_pad > 0 && k_pad < kTcMaxK, DIM3_ERR_OVERFLOW, "DenseEC K exceeds the exact FP32 range");
-    DIM3_REQUIRE(rows_pad / kTcTileM < 65536, DIM3_ERR_OVERFLOW, "x range too long for one DenseEC launch");
-    static bool attr_done[64] = {false};
-    if (!attr_done[ctx.device & 63]) {
-        DIM3_CUDA(cudaFuncSetAttribute(k_dense_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-        DIM3_CUDA(cudaFuncSetAttribute(k_dense_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-        attr_done[ctx.device & 63] = true;
-    }
-    const CUtensorMap ma = make_map(A, k_pad, rows_pad, kTcTileM);
-    const CUtensorMap mb = make_map(B, k_pad, n_pad, kTcTileN);
     DevBuf err;
     err.alloc(sizeof(int), s);
     DIM3_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    const dim3 grid = tiles ? dim3((unsigned)n_tiles) : dim3((unsigned)(n_pad / kTcTileN), (unsigned)(rows_pad / kTcTileM));
-    const int num_kb = (int)(k_pad / kTcBlockK);
-    PhaseScope phase(ctx.stats, PH_DENSE_TC, s);
-    if (kind == 0)
-        k_dense_tc<0><<<grid, kTcThreads, kTcSmem, s>>>(ma, mb, rows, n_zd, num_kb, d_bits, zdw, nullptr,
-                                                         err.as<int>(), tiles);
+    if (tc_tile_n(ctx) == 128)
+        launch_tc<128>(ctx, A, rows, rows_pad, B, n_zd, n_pad, k_pad, kind, d_bits, zdw, d_cnt, tiles, n_tiles,
+                       err.as<int>(), s);
     else
-        k_dense_tc<1><<<grid, kTcThreads, kTcSmem, s>>>(ma, mb, rows, n_zd, num_kb, nullptr, zdw, d_cnt,
-                                                         err.as<int>(), tiles);
-    DIM3_LAUNCHED();
+        launch_tc<256>(ctx, A, rows, rows_pad, B, n_zd, n_pad, k_pad, kind, d_bits, zdw, d_cnt, tiles, n_tiles,
+                       err.as<int>(), s);
     int h = 0;
     DIM3_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     DIM3_CUDA(cudaStreamSynchronize(s));

@@ -12,8 +12,9 @@ measurement on the input itself:
   hopeless: the tensor-core product 2 |X| K |Z_d| (K bounded by the dense
   tuples) would take longer than twice the best time so far at the measured
   fp8 rate, or its dense operands would not fit a memory budget;
-* every surviving (theta_z, DenseEC variant, emit rows per CTA) is timed on
-  the device (CUDA events around the one-call path) and the fastest wins.
+* every surviving (theta_z, DenseEC variant -- for the tensor-core variant
+  also the tile width, 128 x 256 or 128 x 128 --, emit rows per CTA) is timed
+  on the device (CUDA events around the one-call path) and the fastest wins.
 
 Results are cached per GPU and input shape bucket (log2 of |R|, |S|, |X|,
 |Y|, |Z| and of the largest m_z) in a JSON file, so a workload of the same
@@ -133,9 +134,10 @@ def tune(ctx: dim3.Context, cols, repeats: int = 2, cache_path: str | None = Non
                 trials.append({"theta": theta, "skipped": "tensor-core work above twice the best time",
                                "n_zd": n_zd, "flops": flops})
                 continue
-        for v in variants:
+        shapes = [(v, tn) for v in variants for tn in ((256, 128) if v == dim3.DENSE_TC else (0,))]
+        for v, tile_n in shapes:
             for rows in ((1,) if batch else (2, 1)):
-                cfg = {"theta": int(theta), "variant": int(v), "emit_rows": rows}
+                cfg = {"theta": int(theta), "variant": int(v), "emit_rows": rows, "tile_n": tile_n}
                 _apply(ctx, cfg)
                 try:
                     ms = _time_join(ctx, cols, out_x, out_z, repeats, batch)
@@ -159,7 +161,7 @@ def tune(ctx: dim3.Context, cols, repeats: int = 2, cache_path: str | None = Non
                     data = json.load(open(path))
                 except Exception:  # noqa: BLE001
                     data = {}
-                data[key] = {k: decision[k] for k in ("theta", "variant", "emit_rows", "ms", "n_zd")}
+                data[key] = {k: decision.get(k, 0) for k in ("theta", "variant", "emit_rows", "tile_n", "ms", "n_zd")}
                 tmp = path + f".tmp{os.getpid()}"
                 json.dump(data, open(tmp, "w"), indent=1)
                 os.replace(tmp, path)
@@ -172,13 +174,30 @@ def _apply(ctx, cfg: dict):
     ctx.set_option(dim3.OPT_THETA_Z, int(cfg["theta"]))
     ctx.set_option(dim3.OPT_DENSE_VARIANT, int(cfg["variant"]))
     ctx.set_option(dim3.OPT_EMIT_ROWS, int(cfg.get("emit_rows", 0)))
+    ctx.set_option(dim3.OPT_DENSE_TILE_N, int(cfg.get("tile_n", 0)))
+
+
+VARIANT_NAMES = {dim3.DENSE_AUTO: "sparse", dim3.DENSE_TC: "tc", dim3.DENSE_POPC: "popc", dim3.DENSE_PROBE: "probe"}
 
 
 def summary(decision: dict) -> dict:
     """The decision without its trial list, plus the number of candidates
-    timed and skipped (for a bench line's config)."""
+    timed and skipped and the best time of every DenseEC choice
+    ("sparse" = no dense z; "tc256" / "tc128" = the tensor-core product with
+    128 x 256 / 128 x 128 tiles; "popc"; "probe") with its threshold, for a
+    bench line's config."""
     trials = decision.get("trials", [])
     out = {k: v for k, v in decision.items() if k != "trials"}
     out["timed"] = sum(1 for t in trials if "ms" in t)
     out["skipped"] = sum(1 for t in trials if "skipped" in t)
+    best = {}
+    for t in trials:
+        if "ms" not in t:
+            continue
+        name = VARIANT_NAMES.get(t["variant"], str(t["variant"])) if t.get("n_zd", 0) else "sparse"
+        if name == "tc":
+            name += str(t.get("tile_n", 256))
+        if name not in best or t["ms"] < best[name]["ms"]:
+            best[name] = {"ms": t["ms"], "theta": t["theta"], "n_zd": t.get("n_zd", 0)}
+    out["best_by_choice"] = best
     return out

@@ -51,9 +51,17 @@ def test_tuner_decision_is_exact_and_cached(tmp_path):
 
 
 def test_summary_counts_trials():
-    d = {"theta": 5, "variant": 1, "emit_rows": 1, "ms": 1.0, "trials": [{"ms": 1.0}, {"skipped": "x"}, {"ms": 2.0}]}
+    tr = [{"theta": tune.INF, "variant": 0, "ms": 3.0, "n_zd": 0},
+          {"theta": 9, "variant": 1, "tile_n": 256, "ms": 1.0, "n_zd": 40},
+          {"theta": 9, "variant": 1, "tile_n": 128, "ms": 1.5, "n_zd": 40},
+          {"theta": 4, "variant": 1, "tile_n": 256, "ms": 0.8, "n_zd": 90},
+          {"theta": 9, "variant": 2, "ms": 2.0, "n_zd": 40}, {"theta": 1, "skipped": "x", "n_zd": 500}]
+    d = {"theta": 4, "variant": 1, "emit_rows": 1, "ms": 0.8, "trials": tr}
     s = tune.summary(d)
-    assert "trials" not in s and s["timed"] == 2 and s["skipped"] == 1 and s["theta"] == 5
+    assert "trials" not in s and s["timed"] == 5 and s["skipped"] == 1 and s["theta"] == 4
+    b = s["best_by_choice"]
+    assert b["sparse"]["ms"] == 3.0 and b["tc256"] == {"ms": 0.8, "theta": 4, "n_zd": 90}
+    assert b["tc128"]["ms"] == 1.5 and b["popc"]["ms"] == 2.0 and "probe" not in b
 
 
 @pytest.mark.gpu
