@@ -8,10 +8,11 @@ measurement on the input itself:
 * candidates for theta_z (z is dense iff m_z >= theta_z) are infinity (all
   sparse) and the degrees at which the densest 0.1%, 1%, 5%, 20% and 100% of
   the z columns become dense;
-* a candidate is skipped without running when its DenseEC work is clearly
-  hopeless: the tensor-core product 2 |X| K |Z_d| (K bounded by the dense
-  tuples) would take longer than twice the best time so far at the measured
-  fp8 rate, or its dense operands would not fit a memory budget;
+* a (threshold, DenseEC variant) is skipped without running when it is
+  clearly hopeless: a lower bound of its DenseEC time (the tensor-core
+  product 2 |X| K |Z_d| at the measured fp8 rate, AND + popc word pairs, or
+  the probe's words; K bounded by the dense tuples) is above twice the best
+  time so far, or its operands would not fit a memory budget;
 * every surviving (theta_z, DenseEC variant -- for the tensor-core variant
   also the tile width, 128 x 256 or 128 x 128 --, emit rows per CTA) is timed
   on the device (CUDA events around the one-call path) and the fastest wins.
@@ -74,6 +75,28 @@ def dense_estimate(m_z: np.ndarray, theta: int, n_x: int, n_y: int):
     return n_zd, flops, bytes_
 
 
+POPC_WORDS = 1.3e13   # 32-bit AND + popc word operations per second (CUDA cores)
+PROBE_WORDS = 1.0e13  # dense-index words OR-ed per second by the probe (L2 loads)
+
+
+def variant_estimates(m_z: np.ndarray, theta: int, n_x: int, n_y: int, n_r: int) -> dict:
+    """Per DenseEC variant, (lower-bound seconds, operand bytes) for a
+    threshold: the tensor-core product (2 |X| K |Z_d| FLOP, 0/1 bytes of R
+    and S over K), AND + popc (|X| |Z_d| ceil(K / 32) word pairs, bitmaps of
+    R and S over K) and the probe (each R entry ORs one row of ceil(|Z_d| /
+    32) words, S's rows over the dense index). Every variant also holds the
+    dense result bits, |X| ceil(|Z_d| / 32) words."""
+    n_zd, flops, tc_bytes = dense_estimate(m_z, theta, n_x, n_y)
+    if n_zd == 0:
+        return {}
+    k = min(int(n_y), int(m_z[m_z >= theta].sum()))
+    kw, zdw = -(-k // 32), -(-n_zd // 32)
+    res = n_x * zdw * 4
+    return {dim3.DENSE_TC: (flops / TC_FLOPS, tc_bytes + res),
+            dim3.DENSE_POPC: (n_x * n_zd * kw / POPC_WORDS, (n_x + n_zd) * kw * 4 + res),
+            dim3.DENSE_PROBE: (n_r * zdw / PROBE_WORDS, k * zdw * 4 + res)}
+
+
 def _time_join(ctx, cols, out_x, out_z, repeats: int, batch: bool = False) -> float:
     def call():
         if batch:
@@ -124,16 +147,18 @@ def tune(ctx: dim3.Context, cols, repeats: int = 2, cache_path: str | None = Non
     trials = []
     best = None
     for theta in theta_candidates(m_z):
-        n_zd, flops, dbytes = dense_estimate(m_z, theta, info["n_x"], info["n_y"])
-        variants = [dim3.DENSE_AUTO] if n_zd == 0 else [dim3.DENSE_TC, dim3.DENSE_POPC, dim3.DENSE_PROBE]
-        if n_zd:
-            if dbytes > DENSE_BYTES_BUDGET:
-                trials.append({"theta": theta, "skipped": "dense operands over budget", "n_zd": n_zd})
-                continue
-            if best is not None and flops / TC_FLOPS * 1e3 > 2 * best["ms"]:
-                trials.append({"theta": theta, "skipped": "tensor-core work above twice the best time",
-                               "n_zd": n_zd, "flops": flops})
-                continue
+        est = variant_estimates(m_z, theta, info["n_x"], info["n_y"], info["n_r_kept"])
+        n_zd = int((m_z >= theta).sum())
+        variants = [dim3.DENSE_AUTO] if n_zd == 0 else []
+        for v, (sec, nbytes) in est.items():
+            if nbytes > DENSE_BYTES_BUDGET:
+                trials.append({"theta": theta, "variant": int(v), "skipped": "dense operands over budget",
+                               "n_zd": n_zd, "bytes": nbytes})
+            elif best is not None and sec * 1e3 > 2 * best["ms"]:
+                trials.append({"theta": theta, "variant": int(v), "skipped": "DenseEC work above twice the best time",
+                               "n_zd": n_zd, "est_ms": sec * 1e3})
+            else:
+                variants.append(v)
         shapes = [(v, tn) for v in variants for tn in ((256, 128) if v == dim3.DENSE_TC else (0,))]
         for v, tile_n in shapes:
             for rows in ((1,) if batch else (2, 1)):

@@ -82,3 +82,16 @@ def test_tuner_on_a_batch_is_exact(tmp_path):
         ox, oz, _ = oracle.join_project(i.r_key, i.r_val, i.s_key, i.s_val)
         assert np.array_equal(host(x[off[t]:off[t + 1]]), ox) and np.array_equal(host(z[off[t]:off[t + 1]]), oz)
     ctx.close()
+
+
+def test_variant_estimates_scale_with_their_own_work():
+    """The probe's bound grows with |R| and the dense index, not with |X| K:
+    on a sparse-R power-law shape it stays small where the tensor-core
+    operands would not fit the budget."""
+    m_z = np.array([40_000] * 200 + [10] * 200_000)
+    est = tune.variant_estimates(m_z, 1000, n_x=220_000, n_y=220_000, n_r=2_000_000)
+    tc_s, tc_b = est[tune.dim3.DENSE_TC]
+    pr_s, pr_b = est[tune.dim3.DENSE_PROBE]
+    po_s, po_b = est[tune.dim3.DENSE_POPC]
+    assert tc_b > tune.DENSE_BYTES_BUDGET > pr_b and pr_s < tc_s and pr_s < po_s
+    assert tune.variant_estimates(m_z, 10**9, 1, 1, 1) == {}
