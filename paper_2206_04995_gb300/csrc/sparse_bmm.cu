@@ -79,6 +79,10 @@ struct XRowArgs {
     int n_tiles;               // z tiles per row
     int32_t* tcnt;             // counting pass out: pairs of every unit [n_list * n_tiles]
     const int32_t* tcnt_in;    // emitting pass: the counting pass's unit pairs
+    // k_xrow_emit_g over a batch: groups of up to G rows of one instance,
+    // (first row, rows) each; null = consecutive groups of G rows
+    const int2* groups;
+    int64_t n_groups;
 };
 
 // Fill out[o0, o1) with v using 16-byte stores where aligned.
@@ -557,14 +561,28 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
         __syncthreads();
         blk = s_blk;
     }
-    const int64_t xr0 = blk * G;
-    if (xr0 >= a.n_rows) return;
-    const int ng = (int)min64(G, a.n_rows - xr0);
+    int64_t xr0;
+    int ng;
+    if (a.groups) {
+        if (blk >= a.n_groups) return;
+        const int2 g = a.groups[blk];
+        xr0 = g.x;
+        ng = g.y;
+    } else {
+        xr0 = blk * G;
+        if (xr0 >= a.n_rows) return;
+        ng = (int)min64(G, a.n_rows - xr0);
+    }
     const int64_t x0 = a.x_begin + xr0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = lanemask_lt();
     const int64_t tile_words = a.tile_bits >> 5;
-    const bool tiled = a.tile_bits < a.n_z;
+    // z window of the group's instance (all of Z for a single instance; the
+    // rows of a group share their instance), from a 32-aligned start so that
+    // bitmap words line up with the wide rows' words
+    const int tg = a.x_tag ? a.x_tag[x0] : 0;
+    const int64_t zb = a.z_lo[tg] & ~int64_t(31), ze = a.z_lo[tg + 1];
+    const bool tiled = a.tile_bits < ze - zb;
     // R_CSR rows of the group are adjacent: [rb[0], r_end); rb is indexed
     // only with unrolled constants so that it stays in registers
     int64_t rb[G + 1];
@@ -621,8 +639,8 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
         }
     }
 
-    for (int64_t zt0 = 0; zt0 < a.n_z; zt0 += a.tile_bits) {
-        const int64_t zt1 = min64(zt0 + a.tile_bits, a.n_z);
+    for (int64_t zt0 = zb; zt0 < ze; zt0 += a.tile_bits) {
+        const int64_t zt1 = min64(zt0 + a.tile_bits, ze);
         const int tw = (int)((zt1 - zt0 + 31) >> 5);
         clear_words(bm_all, (int)(ng * tile_words));
         __syncthreads();
@@ -651,7 +669,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
                 }
             }
             if (wmask) {
-                const uint32_t* bits = a.ss_bits + (zt0 >> 5);
+                const uint32_t* bits = a.ss_bits + ((zt0 - zb) >> 5);
                 for (int w = tid; w < tw; w += kThreads) {
                     uint32_t acc[G];
 #pragma unroll
@@ -711,7 +729,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
                 __syncthreads();
                 const int nl = s_wc[kWarps];
                 if (nl > 0) {
-                    const uint32_t* bits = a.ss_bits + (zt0 >> 5);
+                    const uint32_t* bits = a.ss_bits + ((zt0 - zb) >> 5);
                     for (int w = tid; w < tw; w += kThreads) {
                         uint32_t acc[G];
 #pragma unroll
@@ -731,11 +749,12 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
             }
         }
         if (a.n_zd > 0) {
-            // DenseEC results, one thread per dense index (see k_xrow_bits)
+            // DenseEC results, one thread per dense index of the instance (see k_xrow_bits)
+            const int64_t d0 = a.x_tag ? a.zd_lo[tg] : 0, d1 = a.x_tag ? a.zd_lo[tg + 1] : a.n_zd;
             for (int k = 0; k < ng; ++k) {
                 const uint32_t* drow = a.d_bits + (xr0 + k) * a.zdw;
                 uint32_t* bm = bm_all + k * tile_words;
-                for (int64_t d = tid; d < a.n_zd; d += kThreads) {
+                for (int64_t d = d0 + tid; d < d1; d += kThreads) {
                     if ((drow[d >> 5] >> (d & 31)) & 1u) {
                         int32_t z = a.zd_list[d];
                         if (z >= zt0 && z < zt1) {
@@ -786,6 +805,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
                 for (int w = 0; w < kWarps; ++w) ck += k < ng ? s_seg[k][w] : 0;
                 out_pos[k] = run;
                 if (write && k < ng) fill_range(a.out_x, run, run + ck, a.dict_x[x0 + k], a.vec_ok);
+                if (a.cnt && tid == 0 && k < ng) a.cnt[xr0 + k] = ck;  // the row counts, for later queries
                 run += ck;
             }
         }
@@ -1434,6 +1454,24 @@ static int emit_rows_per_cta(const Ctx& ctx, int64_t tile_bits) {
     return 1;
 }
 
+// Groups of up to G consecutive rows of [x_begin, x_begin + rows) that stay
+// inside one instance of a batch plan, as (first row - x_begin, rows), on the
+// device in `out`; returns their number.
+static int64_t group_list(const Plan& p, int64_t x_begin, int64_t rows, int G, DevBuf& out, cudaStream_t s) {
+    std::vector<int2> g;
+    g.reserve((size_t)(rows / G + p.n_inst + 1));
+    const int64_t x_end = x_begin + rows;
+    for (int t = 0; t < p.n_inst; ++t) {
+        const int64_t lo = std::max(x_begin, p.h_inst_x_lo[t]), hi = std::min(x_end, p.h_inst_x_lo[t + 1]);
+        for (int64_t r = lo; r < hi; r += G) g.push_back(make_int2((int)(r - x_begin), (int)std::min<int64_t>(G, hi - r)));
+    }
+    if (g.empty()) return 0;
+    out.alloc(g.size() * sizeof(int2), s);
+    DIM3_CUDA(cudaMemcpyAsync(out.p, g.data(), g.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    DIM3_CUDA(cudaStreamSynchronize(s));  // the host vector goes out of scope
+    return (int64_t)g.size();
+}
+
 // Staged entries per warp for the one-row emitting kernel: the large stage
 // (whole 1024-z groups per flush) when the range's output fills more than 2 %
 // of its rows' z-window bits, else the small one (more CTAs per SM). `pairs`
@@ -1682,11 +1720,12 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
     PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
     if (kind == 0) {
         const size_t sm = bits_smem(a.tile_bits, emit, a.stage_ints);
-        // several rows per CTA share one z window, so batches use one row per CTA
-        const int grp = (emit && a.x_tag == nullptr && !a.light) ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
+        // several rows per CTA share one z window: batches need a list of
+        // groups that stay inside one instance (a.groups)
+        const int grp = (emit && !a.light && (a.x_tag == nullptr || a.groups)) ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
         if (emit && grp > 1) {
             const size_t smg = (size_t)kWarps * kWarpStageIds * 4 + (size_t)grp * (size_t)(a.tile_bits / 32) * 4;
-            const unsigned gg = (unsigned)ceil_div(a.n_rows, grp);
+            const unsigned gg = (unsigned)(a.groups ? a.n_groups : ceil_div(a.n_rows, grp));
             static int cur2[64] = {0}, cur4[64] = {0};
             int* cur = (grp == 2 ? cur2 : cur4) + (ctx.device & 63);
             if ((int)smg > *cur) {
@@ -1922,8 +1961,18 @@ static int64_t plan_join_single_pass(const Ctx& ctx, Plan& p, int64_t x_begin, i
     a.out_x = out_x;
     a.out_z = out_z;
     a.vec_ok = ((reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z)) & 15u) == 0;
-    const int grp = a.x_tag == nullptr ? emit_rows_per_cta(ctx, a.tile_bits) : 1;
-    const int64_t nb = ceil_div(rows, grp);
+    const int grp = emit_rows_per_cta(ctx, a.tile_bits);
+    DevBuf groups, cnt;
+    if (grp > 1 && a.x_tag) {
+        a.n_groups = group_list(p, x_begin, rows, grp, groups, s);
+        a.groups = groups.as<int2>();
+    }
+    if (grp > 1) {
+        // several rows per block: each block also records its rows' counts
+        cnt.alloc((size_t)rows * 8, s);
+        a.cnt = cnt.as<int64_t>();
+    }
+    const int64_t nb = a.groups ? a.n_groups : ceil_div(rows, grp);
     DevBuf status, ticket, err;
     status.alloc((size_t)nb * 8, s);
     ticket.alloc(8, s);
@@ -1945,13 +1994,19 @@ static int64_t plan_join_single_pass(const Ctx& ctx, Plan& p, int64_t x_begin, i
     DIM3_REQUIRE(h_err == 0 && (last >> 62) == 2ull, DIM3_ERR_TIMEOUT,
                  "single-pass compaction: a block's offset was not published in time");
     const int64_t total = (int64_t)(last & kLbVal);
-    if (grp == 1) {
-        // one row per block: the inclusive prefixes are the row offsets; keep
-        // them (and the dense result) as the plan's counting-pass cache
+    {
+        // the row offsets (the inclusive prefixes with one row per block, else
+        // a scan of the recorded row counts) and the dense result become the
+        // plan's counting-pass cache
         p.cache_off.alloc((size_t)(rows + 1) * 8, s);
-        const unsigned g = (unsigned)std::min<int64_t>(ceil_div(rows + 1, kThreads), 4096);
-        k_status_to_offsets<<<g, kThreads, 0, s>>>(status.as<unsigned long long>(), rows, p.cache_off.as<int64_t>());
-        DIM3_LAUNCHED();
+        if (grp == 1) {
+            const unsigned g = (unsigned)std::min<int64_t>(ceil_div(rows + 1, kThreads), 4096);
+            k_status_to_offsets<<<g, kThreads, 0, s>>>(status.as<unsigned long long>(), rows,
+                                                       p.cache_off.as<int64_t>());
+            DIM3_LAUNCHED();
+        } else {
+            exclusive_scan_i64(cnt.as<int64_t>(), p.cache_off.as<int64_t>(), rows, s);
+        }
         p.cache_dbits = std::move(dbits);
         p.cache_dcnt.release();
         p.cache_begin = x_begin;
@@ -2023,6 +2078,14 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
         a.vec_ok = (al & 15u) == 0;
         set_stage(ctx, p, a, total);
         a.light = kind == 0 ? ensure_light(ctx, p, s) : nullptr;
+        DevBuf groups;
+        if (kind == 0 && a.x_tag && !a.light) {
+            const int G = emit_rows_per_cta(ctx, a.tile_bits);
+            if (G > 1) {
+                a.n_groups = group_list(p, x_begin, rows, G, groups, s);
+                a.groups = groups.as<int2>();
+            }
+        }
         launch_rows(ctx, a, kind, true, s);
         if (a.light) {
             PhaseScope phase(ctx.stats, PH_EMIT, s);

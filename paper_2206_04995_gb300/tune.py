@@ -161,7 +161,7 @@ def tune(ctx: dim3.Context, cols, repeats: int = 2, cache_path: str | None = Non
                 variants.append(v)
         shapes = [(v, tn) for v in variants for tn in ((256, 128) if v == dim3.DENSE_TC else (0,))]
         for v, tile_n in shapes:
-            for rows in ((1,) if batch else (2, 1)):
+            for rows in ((4, 2, 1) if batch else (2, 1)):
                 cfg = {"theta": int(theta), "variant": int(v), "emit_rows": rows, "tile_n": tile_n}
                 _apply(ctx, cfg)
                 try:

@@ -168,3 +168,26 @@ def test_batch_plan_ranges_and_preallocated_call():
     with pytest.raises(dim3.Dim3Error):
         c.batch_join_project(cols, out_x=bx[: n - 1], out_z=bz[: n - 1])
     c.close()
+
+
+@pytest.mark.parametrize("rows", [1, 2, 4])
+@pytest.mark.parametrize("two_pass", [0, 1])
+def test_batch_rows_per_cta(rows, two_pass):
+    """Batches emitted with 1, 2 or 4 x rows per CTA (groups that never cross
+    an instance, ragged at every instance end), one pass and two, with wide
+    S rows held as bitmaps over each instance's window and DenseEC results
+    over each instance's dense index."""
+    for opts in ({}, {dim3.OPT_BITMAP_ROW_MIN: 1}, {dim3.OPT_THETA_Z: 6, dim3.OPT_DENSE_VARIANT: dim3.DENSE_POPC}):
+        c = ctx_with({dim3.OPT_EMIT_ROWS: rows, dim3.OPT_TWO_PASS: two_pass, **opts})
+        insts = mixed_batch(31 + rows, k=11) + gen.config4_batch(n_inst=5, lo=1000, hi=15_000)
+        cols = [inst_dev(i) for i in insts]
+        n = sum(oracle.join_project(i.r_key, i.r_val, i.s_key, i.s_val)[0].size for i in insts)
+        bx = torch.empty(n + 3, dtype=torch.int32, device="cuda")
+        bz = torch.empty(n + 3, dtype=torch.int32, device="cuda")
+        x, z, per = c.batch_join_project(cols, out_x=bx[1:], out_z=bz[2:])
+        off = np.concatenate([[0], np.cumsum(per)])
+        for t, i in enumerate(insts):
+            ox, oz, _ = oracle.join_project(i.r_key, i.r_val, i.s_key, i.s_val)
+            assert np.array_equal(host(x[off[t]:off[t + 1]]), ox), (rows, two_pass, opts, t)
+            assert np.array_equal(host(z[off[t]:off[t + 1]]), oz), (rows, two_pass, opts, t)
+        c.close()
