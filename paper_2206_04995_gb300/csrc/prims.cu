@@ -64,10 +64,46 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const Tin* in, int64_t* 
     }
 }
 
+// One CTA for short inputs: tiles of kScanTile in order with a running carry
+// (one launch instead of three; the tiles are few).
+constexpr int64_t kScanOneBlockMax = 16 * kScanTile;
+
+template <typename Tin>
+__global__ void __launch_bounds__(kThreads) k_scan_one_block(const Tin* in, int64_t* out, int64_t n) {
+    __shared__ int64_t s_warp[kThreads / 32 + 1];
+    int64_t carry = 0;
+    for (int64_t t0 = 0; t0 < n; t0 += kScanTile) {
+        const int64_t base = t0 + (int64_t)threadIdx.x * kScanItems;
+        int64_t v[kScanItems];
+        int64_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const int64_t idx = base + j;
+            v[j] = idx < n ? (int64_t)in[idx] : 0;
+            sum += v[j];
+        }
+        int64_t tot;
+        int64_t run = block_exclusive_scan<int64_t, kThreads>(sum, &tot, s_warp) + carry;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const int64_t idx = base + j;
+            if (idx < n) out[idx] = run;
+            run += v[j];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
 template <typename Tin>
 static void exclusive_scan_impl(const Tin* in, int64_t* out, int64_t n, cudaStream_t s) {
     if (n == 0) {
         fill_i64(out, 0, 1, s);
+        return;
+    }
+    if (n <= kScanOneBlockMax) {
+        k_scan_one_block<Tin><<<1, kThreads, 0, s>>>(in, out, n);
+        DIM3_LAUNCHED();
         return;
     }
     const int64_t nb = ceil_div(n, kScanTile);
@@ -427,9 +463,34 @@ __global__ void k_unique_scatter(const K* in, int64_t n, const int32_t* flags, c
         if (flags[i]) out[pos[i]] = in[i];
 }
 
+// Short inputs: flags, scan and scatter in one CTA (one launch instead of
+// five); *count gets the number of distinct keys.
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_unique_one_block(const K* in, int64_t n, const int64_t* m_dev, K* out,
+                                                               int64_t* count) {
+    __shared__ int64_t s_warp[kThreads / 32 + 1];
+    const int64_t m = m_dev ? min64(n, *m_dev) : n;
+    int64_t carry = 0;
+    for (int64_t t0 = 0; t0 < m; t0 += kThreads) {
+        const int64_t i = t0 + threadIdx.x;
+        const bool keep = i < m && (i == 0 || in[i] != in[i - 1]);
+        int64_t tot;
+        const int64_t pos = block_exclusive_scan<int64_t, kThreads>(keep ? 1 : 0, &tot, s_warp) + carry;
+        if (keep) out[pos] = in[i];
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *count = carry;
+}
+
 template <typename K>
 static const int64_t* unique_enqueue(const K* in, K* out, int64_t n, cudaStream_t s, const int64_t* n_dev,
                                      DevBuf& pos) {
+    if (n > 0 && n <= kScanOneBlockMax) {
+        pos.alloc(sizeof(int64_t), s);
+        k_unique_one_block<K><<<1, kThreads, 0, s>>>(in, n, n_dev, out, pos.as<int64_t>());
+        DIM3_LAUNCHED();
+        return pos.as<int64_t>();
+    }
     pos.alloc(((size_t)n + 1) * sizeof(int64_t), s);
     if (n == 0) {
         fill_i64(pos.as<int64_t>(), 0, 1, s);
