@@ -162,6 +162,44 @@ __device__ __forceinline__ int64_t lookback_prefix(unsigned long long* status, i
     return prefix;
 }
 
+// Split form of lookback_prefix for blocks that publish their aggregate and
+// resolve their prefix later (with other work in between): lookback_publish
+// stores block b's aggregate (block 0: its inclusive prefix); lookback_resolve
+// (one whole warp) then waits for the predecessors as lookback_prefix does
+// and stores b's inclusive prefix. Same return and failure behaviour.
+__device__ __forceinline__ void lookback_publish(unsigned long long* status, int64_t b, int64_t aggregate) {
+    atomicExch(&status[b], (b == 0 ? kLbInc : kLbAgg) | (unsigned long long)aggregate);
+}
+
+__device__ __forceinline__ int64_t lookback_resolve(unsigned long long* status, int64_t b, int64_t aggregate, int* err,
+                                                    uint64_t wait_ns) {
+    const int lane = lane_id();
+    if (b == 0) return 0;
+    int64_t prefix = 0, j = b - 1;
+    const uint64_t t0 = global_ns();
+    uint32_t polls = 0;
+    while (true) {
+        const int64_t idx = j - lane;
+        const unsigned long long v = idx >= 0 ? ld_relaxed_u64(&status[idx]) : kLbInc;
+        if (!__all_sync(kFull, (v >> 62) != 0ull)) {
+            const bool late = ((++polls & 63u) == 0u) && (global_ns() - t0 > wait_ns);
+            if (__any_sync(kFull, late)) {
+                if (lane == 0) atomicExch(err, 1);
+                prefix = -1;
+                break;
+            }
+            continue;
+        }
+        const unsigned inc = __ballot_sync(kFull, (v >> 62) == 2ull);
+        const int stop = inc ? __ffs(inc) - 1 : 31;
+        prefix += warp_sum(lane <= stop ? (int64_t)(v & kLbVal) : (int64_t)0);
+        if (inc) break;
+        j -= 32;
+    }
+    if (lane == 0) atomicExch(&status[b], kLbInc | (unsigned long long)((prefix < 0 ? 0 : prefix) + aggregate));
+    return prefix;
+}
+
 // 32-bit finaliser of MurmurHash3 (Appleby): spreads keys over table slots.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;

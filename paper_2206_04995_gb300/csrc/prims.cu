@@ -13,86 +13,51 @@ namespace dimcube {
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kThreads * kScanItems;
 
-template <typename Tin>
-__global__ void __launch_bounds__(kThreads) k_scan_reduce(const Tin* in, int64_t n, int64_t* partial) {
-    __shared__ int64_t s_warp[kThreads / 32 + 1];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int64_t acc = 0;
-    for (int i = threadIdx.x; i < kScanTile; i += kThreads) {
-        int64_t idx = base + i;
-        if (idx < n) acc += (int64_t)in[idx];
-    }
-    acc = block_sum<int64_t, kThreads>(acc, s_warp);
-    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
-}
-
-// single block: exclusive scan of partial[0..nb) in place; total -> *total_out
-__global__ void __launch_bounds__(kThreads) k_scan_partials(int64_t* partial, int64_t nb, int64_t* total_out) {
-    __shared__ int64_t s_warp[kThreads / 32 + 1];
-    int64_t carry = 0;
-    for (int64_t base = 0; base < nb; base += kThreads) {
-        int64_t i = base + threadIdx.x;
-        int64_t v = i < nb ? partial[i] : 0;
-        int64_t tot;
-        int64_t ex = block_exclusive_scan<int64_t, kThreads>(v, &tot, s_warp);
-        if (i < nb) partial[i] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) *total_out = carry;
-}
+// Single-pass exclusive scan: one launch whatever n. Every CTA scans one
+// tile of kScanTile items and finds the tile's offset by decoupled look-back
+// over the tiles before it (logical tile numbers from a ticket, so a CTA only
+// waits on tiles already running; a wait that runs past 2 s gives up, stores 1
+// to the process-wide wait-fault flag, which fails the call with
+// DIM3_ERR_TIMEOUT after its next synchronisation). The last tile writes the
+// total to out[n].
+constexpr uint64_t kScanWaitNs = 2000000000ull;
 
 template <typename Tin>
-__global__ void __launch_bounds__(kThreads) k_scan_down(const Tin* in, int64_t* out, int64_t n,
-                                                        const int64_t* partial) {
+__global__ void __launch_bounds__(kThreads) k_scan_lb(const Tin* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                                                      int64_t n_tiles, unsigned long long* status,
+                                                      unsigned long long* ticket, int* err, int* fault) {
     __shared__ int64_t s_warp[kThreads / 32 + 1];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    __shared__ int64_t s_blk, s_pre;
+    if (threadIdx.x == 0) s_blk = (int64_t)atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const int64_t b = s_blk;
+    const int64_t base = b * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t v[kScanItems];
     int64_t sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        int64_t idx = base + j;
+        const int64_t idx = base + j;
         v[j] = idx < n ? (int64_t)in[idx] : 0;
         sum += v[j];
     }
     int64_t tot;
-    int64_t run = block_exclusive_scan<int64_t, kThreads>(sum, &tot, s_warp) + partial[blockIdx.x];
+    const int64_t ex = block_exclusive_scan<int64_t, kThreads>(sum, &tot, s_warp);
+    if ((threadIdx.x >> 5) == 0) {
+        const int64_t pre = lookback_prefix(status, b, tot, err, kScanWaitNs);
+        if ((threadIdx.x & 31) == 0) {
+            s_pre = pre < 0 ? 0 : pre;
+            if (pre < 0) *static_cast<volatile int*>(fault) = 1;
+        }
+    }
+    __syncthreads();
+    int64_t run = s_pre + ex;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        int64_t idx = base + j;
+        const int64_t idx = base + j;
         if (idx < n) out[idx] = run;
         run += v[j];
     }
-}
-
-// One CTA for short inputs: tiles of kScanTile in order with a running carry
-// (one launch instead of three; the tiles are few).
-constexpr int64_t kScanOneBlockMax = 16 * kScanTile;
-
-template <typename Tin>
-__global__ void __launch_bounds__(kThreads) k_scan_one_block(const Tin* in, int64_t* out, int64_t n) {
-    __shared__ int64_t s_warp[kThreads / 32 + 1];
-    int64_t carry = 0;
-    for (int64_t t0 = 0; t0 < n; t0 += kScanTile) {
-        const int64_t base = t0 + (int64_t)threadIdx.x * kScanItems;
-        int64_t v[kScanItems];
-        int64_t sum = 0;
-#pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            const int64_t idx = base + j;
-            v[j] = idx < n ? (int64_t)in[idx] : 0;
-            sum += v[j];
-        }
-        int64_t tot;
-        int64_t run = block_exclusive_scan<int64_t, kThreads>(sum, &tot, s_warp) + carry;
-#pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            const int64_t idx = base + j;
-            if (idx < n) out[idx] = run;
-            run += v[j];
-        }
-        carry += tot;
-    }
-    if (threadIdx.x == 0) out[n] = carry;
+    if (b == n_tiles - 1 && threadIdx.x == 0) out[n] = s_pre + tot;
 }
 
 template <typename Tin>
@@ -101,19 +66,14 @@ static void exclusive_scan_impl(const Tin* in, int64_t* out, int64_t n, cudaStre
         fill_i64(out, 0, 1, s);
         return;
     }
-    if (n <= kScanOneBlockMax) {
-        k_scan_one_block<Tin><<<1, kThreads, 0, s>>>(in, out, n);
-        DIM3_LAUNCHED();
-        return;
-    }
     const int64_t nb = ceil_div(n, kScanTile);
-    DevBuf partial;
-    partial.alloc((size_t)nb * sizeof(int64_t), s);
-    k_scan_reduce<Tin><<<(unsigned)nb, kThreads, 0, s>>>(in, n, partial.as<int64_t>());
-    DIM3_LAUNCHED();
-    k_scan_partials<<<1, kThreads, 0, s>>>(partial.as<int64_t>(), nb, out + n);
-    DIM3_LAUNCHED();
-    k_scan_down<Tin><<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, partial.as<int64_t>());
+    DIM3_REQUIRE(nb < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "scan too long");
+    DevBuf st;  // ticket, error word, then one status word per tile
+    st.alloc((size_t)(nb + 2) * sizeof(unsigned long long), s);
+    DIM3_CUDA(cudaMemsetAsync(st.p, 0, st.bytes, s));
+    unsigned long long* w = st.as<unsigned long long>();
+    k_scan_lb<Tin><<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, nb, w + 2, w, reinterpret_cast<int*>(w + 1),
+                                                     wait_fault_flag());
     DIM3_LAUNCHED();
 }
 
@@ -448,63 +408,68 @@ void radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t
 }
 
 // ------------------------------------------------------------------ unique
+// Drop adjacent duplicates in one launch: every CTA flags the first key of
+// each run in its tile of kScanTile keys, finds the tile's output offset by
+// decoupled look-back (as k_scan_lb) and scatters its kept keys; the last tile
+// writes the number kept to *count. Keys at or past *m_dev (when given) are
+// ignored.
 template <typename K>
-__global__ void k_unique_flags(const K* in, int64_t n, const int64_t* m_dev, int32_t* flags) {
-    const int64_t m = m_dev ? min64(n, *m_dev) : n;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        flags[i] = (i < m && (i == 0 || in[i] != in[i - 1])) ? 1 : 0;
-}
-
-template <typename K>
-__global__ void k_unique_scatter(const K* in, int64_t n, const int32_t* flags, const int64_t* pos, K* out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        if (flags[i]) out[pos[i]] = in[i];
-}
-
-// Short inputs: flags, scan and scatter in one CTA (one launch instead of
-// five); *count gets the number of distinct keys.
-template <typename K>
-__global__ void __launch_bounds__(kThreads) k_unique_one_block(const K* in, int64_t n, const int64_t* m_dev, K* out,
-                                                               int64_t* count) {
+__global__ void __launch_bounds__(kThreads) k_unique_lb(const K* __restrict__ in, int64_t n, const int64_t* m_dev,
+                                                        K* __restrict__ out, int64_t* count, int64_t n_tiles,
+                                                        unsigned long long* status, unsigned long long* ticket,
+                                                        int* err, int* fault) {
     __shared__ int64_t s_warp[kThreads / 32 + 1];
+    __shared__ int64_t s_blk, s_pre;
+    if (threadIdx.x == 0) s_blk = (int64_t)atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const int64_t b = s_blk;
     const int64_t m = m_dev ? min64(n, *m_dev) : n;
-    int64_t carry = 0;
-    for (int64_t t0 = 0; t0 < m; t0 += kThreads) {
-        const int64_t i = t0 + threadIdx.x;
-        const bool keep = i < m && (i == 0 || in[i] != in[i - 1]);
-        int64_t tot;
-        const int64_t pos = block_exclusive_scan<int64_t, kThreads>(keep ? 1 : 0, &tot, s_warp) + carry;
-        if (keep) out[pos] = in[i];
-        carry += tot;
+    const int64_t base = b * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    unsigned keep = 0u;
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = base + j;
+        if (i < m && (i == 0 || in[i] != in[i - 1])) {
+            keep |= 1u << j;
+            ++c;
+        }
     }
-    if (threadIdx.x == 0) *count = carry;
+    int64_t tot;
+    const int64_t ex = block_exclusive_scan<int64_t, kThreads>((int64_t)c, &tot, s_warp);
+    if ((threadIdx.x >> 5) == 0) {
+        const int64_t pre = lookback_prefix(status, b, tot, err, kScanWaitNs);
+        if ((threadIdx.x & 31) == 0) {
+            s_pre = pre < 0 ? 0 : pre;
+            if (pre < 0) *static_cast<volatile int*>(fault) = 1;
+        }
+    }
+    __syncthreads();
+    int64_t pos = s_pre + ex;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if ((keep >> j) & 1u) out[pos++] = in[base + j];
+    if (b == n_tiles - 1 && threadIdx.x == 0) *count = s_pre + tot;
 }
 
 template <typename K>
 static const int64_t* unique_enqueue(const K* in, K* out, int64_t n, cudaStream_t s, const int64_t* n_dev,
                                      DevBuf& pos) {
-    if (n > 0 && n <= kScanOneBlockMax) {
-        pos.alloc(sizeof(int64_t), s);
-        k_unique_one_block<K><<<1, kThreads, 0, s>>>(in, n, n_dev, out, pos.as<int64_t>());
-        DIM3_LAUNCHED();
-        return pos.as<int64_t>();
-    }
-    pos.alloc(((size_t)n + 1) * sizeof(int64_t), s);
     if (n == 0) {
+        pos.alloc(sizeof(int64_t), s);
         fill_i64(pos.as<int64_t>(), 0, 1, s);
         return pos.as<int64_t>();
     }
-    DevBuf flags;
-    flags.alloc((size_t)n * sizeof(int32_t), s);
-    unsigned g = (unsigned)std::min<int64_t>(ceil_div(n, kThreads), 8192);
-    k_unique_flags<K><<<g, kThreads, 0, s>>>(in, n, n_dev, flags.as<int32_t>());
+    const int64_t nb = ceil_div(n, kScanTile);
+    DIM3_REQUIRE(nb < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "unique input too long");
+    // count, ticket, error word, then one status word per tile
+    pos.alloc((size_t)(nb + 3) * sizeof(unsigned long long), s);
+    DIM3_CUDA(cudaMemsetAsync(pos.p, 0, pos.bytes, s));
+    unsigned long long* w = pos.as<unsigned long long>();
+    k_unique_lb<K><<<(unsigned)nb, kThreads, 0, s>>>(in, n, n_dev, out, pos.as<int64_t>(), nb, w + 3, w + 1,
+                                                     reinterpret_cast<int*>(w + 2), wait_fault_flag());
     DIM3_LAUNCHED();
-    exclusive_scan_i32_to_i64(flags.as<int32_t>(), pos.as<int64_t>(), n, s);
-    k_unique_scatter<K><<<g, kThreads, 0, s>>>(in, n, flags.as<int32_t>(), pos.as<int64_t>(), out);
-    DIM3_LAUNCHED();
-    return pos.as<int64_t>() + n;
+    return pos.as<int64_t>();
 }
 
 template <typename K>
