@@ -63,20 +63,22 @@ def chain_sizes(tables):
     ea, eb = _distinct_edges(tables[0])
     out_j = [float(ea.size)]
     out_p = [float(ea.size)]
-    # bag sizes: the number of join paths ending at each value, carried along
-    # every table's edges (integer sums, exact in float64 below 2^53)
-    vals, counts = np.unique(eb, return_counts=True)
-    counts = counts.astype(np.float64)
+    # |OUT_J_i| as path counts: paths[v] = the number of join paths through
+    # R_1 .. R_i ending at value v (Python integers, exact); the next table
+    # extends every path ending at u along each of its edges (u, w)
+    paths = {}
+    for v in eb.tolist():
+        paths[v] = paths.get(v, 0) + 1
     x, z = ea, eb
     for t in tables[1:]:
         ua, ub = _distinct_edges(t)
-        pos = np.searchsorted(vals, ua)
-        ok = (pos < vals.size) & (vals[np.minimum(pos, max(vals.size - 1, 0))] == ua) if vals.size else \
-            np.zeros(ua.size, bool)
-        w = counts[pos[ok]]
-        vals, inv = np.unique(ub[ok], return_inverse=True)
-        counts = np.bincount(inv, weights=w, minlength=vals.size)
-        out_j.append(float(counts.sum()))
+        nxt = {}
+        for u, w in zip(ua.tolist(), ub.tolist()):
+            c = paths.get(u, 0)
+            if c:
+                nxt[w] = nxt.get(w, 0) + c
+        paths = nxt
+        out_j.append(float(sum(paths.values())))
         x, z, _ = join_project(z, x, *_edges(t))
         out_p.append(float(x.size))
     return out_j, out_p
