@@ -141,7 +141,10 @@ typedef enum {
                                    chooses, 1 the hybrid DIM^3 path, 2 the classical solution */
     DIM3_OPT_TILE_WORDS = 10,   /* z ranges wider than one shared-memory bitmap (393,216 z): 32-bit words
                                    per z tile, 1024..12288; 0 (default): the fewest tiles, equal sizes */
-    DIM3_OPT_DENSE_TILE_N = 11  /* tensor-core DenseEC: dense z per CTA tile, 128 or 256; 0 (default): 256 */
+    DIM3_OPT_DENSE_TILE_N = 11, /* tensor-core DenseEC: dense z per CTA tile, 128 or 256; 0 (default): 256 */
+    DIM3_OPT_EMIT_PIPELINE = 12 /* single-pass emission with two x rows per CTA: 1 = persistent CTAs that
+                                   build the next row group while the previous one's offset resolves;
+                                   0 (default) = one group per CTA */
 } dim3_option;
 
 /* Phases timed under DIM3_OPT_TIMING. */

@@ -86,6 +86,7 @@ struct Options {
     int64_t path = 0;           // one-call joins: 0 f1 decides, 1 hybrid, 2 classical
     int64_t tile_words = 0;     // z-tiled rows: bitmap words per tile (0: automatic)
     int64_t dense_tile_n = 0;   // tensor-core DenseEC: dense z per CTA tile (128 or 256; 0: 256)
+    int64_t emit_pipe = 0;      // single pass, two rows per CTA: persistent pipelined kernel (1) or not (0)
     // f1 constants (Section 2.6), seconds: t_map per input row, t_randRW per
     // join tuple of the hybrid path, t_hash per join tuple of the classical path
     double f1c[3] = {kF1TMap, kF1TRand, kF1THash};

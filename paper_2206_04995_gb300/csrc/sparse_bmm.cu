@@ -538,19 +538,347 @@ __global__ void __launch_bounds__(kThreads, kEmit ? 4 : 8) k_xrow_bits(const XRo
 // into registers half a slice at a time (lane l holds entries 32 j + l of 16
 // words j) and used for all G rows, which divides the dictionary's L2 traffic
 // and the block barriers per row by G; a half (at most 512 pairs) is staged
-// and flushed, so the per-warp stage is 528 entries.
+// and flushed, so the per-warp stage is 528 entries. The steps are device
+// functions shared by the plain kernel and the pipelined persistent one.
+
+// Build scratch of a row group.
+struct GroupSmem {
+    int32_t list[kThreads];
+    int32_t lk[kThreads];
+    int32_t ny[kThreads];
+    int32_t nk[kThreads];
+    int64_t woff[kThreads];
+    int32_t wc[kWarps + 1];
+    int32_t cw[kWarps], cn[kWarps];
+};
+
+// Row group number blk: its first row (relative to x_begin) and row count;
+// false past the last group.
+template <int G>
+__device__ __forceinline__ bool g_locate(const XRowArgs& a, int64_t blk, int64_t& xr0, int& ng) {
+    if (a.groups) {
+        if (blk >= a.n_groups) return false;
+        const int2 g = a.groups[blk];
+        xr0 = g.x;
+        ng = g.y;
+        return true;
+    }
+    xr0 = blk * G;
+    if (xr0 >= a.n_rows) return false;
+    ng = (int)min64(G, a.n_rows - xr0);
+    return true;
+}
+
+// Which of the group's rows holds R_CSR entry p (rb = the rows' starts).
+template <int G>
+__device__ __forceinline__ int g_row_of(int64_t p, const int64_t (&rb)[G + 1], int ng) {
+    int k = 0;
+#pragma unroll
+    for (int q = 1; q < G; ++q) k += (q < ng && p >= rb[q]) ? 1 : 0;
+    return k;
+}
+
+// At most flat_max R entries (the usual case): one thread per entry sorts
+// them once into per-warp lists of narrow rows (y, row) and wide rows
+// (bitmap, row); every tile then builds its bitmaps in ONE barrier-free phase,
+// warps walking narrow rows while every thread ORs wide rows into its words
+// (both with shared atomics). Returns whether the group is flat (block-
+// uniform); the lists are ready after the next block barrier.
+template <int G>
+__device__ __forceinline__ bool g_prepare(const XRowArgs& a, const int64_t (&rb)[G + 1], int ng, GroupSmem& gs) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = lanemask_lt();
+    const int64_t n_ent = rb[G] - rb[0];
+    const bool flat = n_ent <= a.flat_max;
+    if (flat) {
+        const int64_t p = rb[0] + tid;
+        int32_t y = -1, b = -1;
+        if (tid < n_ent) {
+            y = a.r_col[p];
+            b = a.bm_row_of_y[y];
+        }
+        const bool isw = b >= 0, isn = tid < n_ent && b < 0;
+        const unsigned bw = __ballot_sync(kFull, isw), bn = __ballot_sync(kFull, isn);
+        const int k = tid < n_ent ? g_row_of<G>(p, rb, ng) : 0;
+        if (isw) {
+            const int slot = (warp << 5) + __popc(bw & lt);
+            gs.woff[slot] = a.bm_off[b];
+            gs.lk[slot] = k;
+        }
+        if (isn) {
+            const int slot = (warp << 5) + __popc(bn & lt);
+            gs.ny[slot] = y;
+            gs.nk[slot] = k;
+        }
+        if (lane == 0) {
+            gs.cw[warp] = __popc(bw);
+            gs.cn[warp] = __popc(bn);
+        }
+    }
+    return flat;
+}
+
+// The group's bitmaps over z tile [zt0, zt1) (window start zb of instance tg):
+// clear, narrow S rows, wide S rows, DenseEC bits. Ends with a block barrier.
+template <int G>
+__device__ __forceinline__ void g_build(const XRowArgs& a, const int64_t (&rb)[G + 1], int ng, bool flat, int tg,
+                                        int64_t xr0, int64_t zb, int64_t zt0, int64_t zt1, bool tiled,
+                                        uint32_t* bm_all, int64_t tile_words, GroupSmem& gs) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = lanemask_lt();
+    const int64_t r_end = rb[G];
+    const int tw = (int)((zt1 - zt0 + 31) >> 5);
+    clear_words(bm_all, (int)(ng * tile_words));
+    __syncthreads();
+    if (flat) {
+        int n_nar = 0;
+        unsigned wmask = 0u;  // warps whose list holds wide rows
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            n_nar += gs.cn[w];
+            wmask |= gs.cw[w] > 0 ? 1u << w : 0u;
+        }
+        for (int e = warp; e < n_nar; e += kWarps) {
+            int sg = 0, base = 0;
+            while (e - base >= gs.cn[sg]) base += gs.cn[sg++];
+            const int slot = (sg << 5) + (e - base);
+            const int32_t y = gs.ny[slot];
+            uint32_t* bm = bm_all + gs.nk[slot] * tile_words;
+            int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+            if (tiled) {
+                s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
+                s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
+            }
+            for (int64_t q = s0 + lane; q < s1; q += 32) {
+                const int32_t z = a.ss_col[q] - (int32_t)zt0;
+                atomicOr(&bm[z >> 5], 1u << (z & 31));
+            }
+        }
+        if (wmask) {
+            const uint32_t* bits = a.ss_bits + ((zt0 - zb) >> 5);
+            for (int w = tid; w < tw; w += kThreads) {
+                uint32_t acc[G];
+#pragma unroll
+                for (int k = 0; k < G; ++k) acc[k] = 0u;
+                for (unsigned m = wmask; m; m &= m - 1) {
+                    const int sg = __ffs(m) - 1, c = gs.cw[sg];
+                    for (int i = sg << 5; i < (sg << 5) + c; ++i) {
+                        const uint32_t v = __ldg(bits + gs.woff[i] + w);
+                        const int k = gs.lk[i];
+#pragma unroll
+                        for (int q = 0; q < G; ++q) acc[q] |= (k == q) ? v : 0u;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < G; ++k)
+                    if (k < ng && acc[k]) atomicOr(&bm_all[k * tile_words + w], acc[k]);
+            }
+        }
+    } else {
+        // narrow S_sparse rows of all G rows: one warp per R entry
+        for (int64_t p = rb[0] + warp; p < r_end; p += kWarps) {
+            const int32_t y = a.r_col[p];
+            if (a.bm_row_of_y[y] >= 0) continue;
+            uint32_t* bm = bm_all + g_row_of<G>(p, rb, ng) * tile_words;
+            int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
+            if (tiled) {
+                s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
+                s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
+            }
+            for (int64_t q = s0 + lane; q < s1; q += 32) {
+                const int32_t z = a.ss_col[q] - (int32_t)zt0;
+                atomicOr(&bm[z >> 5], 1u << (z & 31));
+            }
+        }
+        // wide S_sparse rows
+        for (int64_t base = rb[0]; base < r_end; base += kThreads) {
+            const int64_t p = base + tid;
+            const int32_t b = p < r_end ? a.bm_row_of_y[a.r_col[p]] : -1;
+            const unsigned bal = __ballot_sync(kFull, b >= 0);
+            if (lane == 0) gs.wc[warp] = __popc(bal);
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int w = 0; w < kWarps; ++w) {
+                    const int c = gs.wc[w];
+                    gs.wc[w] = run;
+                    run += c;
+                }
+                gs.wc[kWarps] = run;
+            }
+            __syncthreads();
+            if (b >= 0) {
+                const int slot = gs.wc[warp] + __popc(bal & lt);
+                gs.list[slot] = b;
+                gs.lk[slot] = g_row_of<G>(p, rb, ng);
+            }
+            __syncthreads();
+            const int nl = gs.wc[kWarps];
+            if (nl > 0) {
+                const uint32_t* bits = a.ss_bits + ((zt0 - zb) >> 5);
+                for (int w = tid; w < tw; w += kThreads) {
+                    uint32_t acc[G];
+#pragma unroll
+                    for (int k = 0; k < G; ++k) acc[k] = 0u;
+                    for (int i = 0; i < nl; ++i) {
+                        const uint32_t v = __ldg(bits + a.bm_off[gs.list[i]] + w);
+                        const int k = gs.lk[i];
+#pragma unroll
+                        for (int q = 0; q < G; ++q) acc[q] |= (k == q) ? v : 0u;
+                    }
+#pragma unroll
+                    for (int k = 0; k < G; ++k)
+                        if (k < ng && acc[k]) bm_all[k * tile_words + w] |= acc[k];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (a.n_zd > 0) {
+        // DenseEC results, one thread per dense index of the instance (see k_xrow_bits)
+        const int64_t d0 = a.x_tag ? a.zd_lo[tg] : 0, d1 = a.x_tag ? a.zd_lo[tg + 1] : a.n_zd;
+        for (int k = 0; k < ng; ++k) {
+            const uint32_t* drow = a.d_bits + (xr0 + k) * a.zdw;
+            uint32_t* bm = bm_all + k * tile_words;
+            for (int64_t d = d0 + tid; d < d1; d += kThreads) {
+                if ((drow[d >> 5] >> (d & 31)) & 1u) {
+                    int32_t z = a.zd_list[d];
+                    if (z >= zt0 && z < zt1) {
+                        z -= (int32_t)zt0;
+                        atomicOr(&bm[z >> 5], 1u << (z & 31));
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Per-warp segment sizes of every row of the group (warp w owns groups of 32
+// words [g0, g1) of the tile). Ends with a block barrier.
+template <int G>
+__device__ __forceinline__ void g_counts(const uint32_t* bm_all, int64_t tile_words, int tw, int ng,
+                                         int32_t (&seg)[G][kWarps]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int groups = (tw + 31) >> 5;
+    const int gpw = (groups + kWarps - 1) / kWarps;
+    const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        int mine = 0;
+        if (k < ng) {
+            const uint32_t* bm = bm_all + k * tile_words;
+            for (int g = g0; g < g1; ++g) {
+                const int w = (g << 5) + lane;
+                mine += w < tw ? __popc(bm[w]) : 0;
+            }
+        }
+        mine = warp_sum(mine);
+        if (lane == 0) seg[k][warp] = mine;
+    }
+    __syncthreads();
+}
+
+// Compaction of the group's tile: every warp writes the z values of its run
+// of 32-word groups for each row, row k's run starting at row_pos[k] plus the
+// earlier warps' segments of that row. No block barrier.
+template <int G>
+__device__ __forceinline__ void g_emit(const XRowArgs& a, const uint32_t* bm_all, int64_t tile_words, int tw, int ng,
+                                       int64_t zt0, const int32_t (&seg)[G][kWarps], const int64_t (&row_pos)[G],
+                                       int32_t* stage) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    const int groups = (tw + 31) >> 5;
+    const int gpw = (groups + kWarps - 1) / kWarps;
+    const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
+    int64_t wpos[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        int64_t before = 0;
+        for (int w = 0; w < warp; ++w) before += seg[k][w];
+        wpos[k] = (k < ng ? row_pos[k] : 0) + before;
+    }
+    int32_t* st = stage + warp * kWarpStageIds;
+    const int64_t zlim = a.n_z - zt0;
+    for (int g = g0; g < g1; ++g) {
+        const int w = (g << 5) + lane;
+        uint32_t word[G];
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            word[k] = (k < ng && w < tw) ? bm_all[k * tile_words + w] : 0u;
+            any |= word[k] != 0u;
+        }
+        if (!__any_sync(kFull, any)) continue;
+        const int64_t gb = (int64_t)g << 10;
+        const int32_t* dz = a.dict_z + zt0 + gb;
+        int excl[G], total[G], half0[G];
+        bool dense = false;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int c = __popc(word[k]);
+            const int incl = warp_inclusive_scan(c);
+            total[k] = __shfl_sync(kFull, incl, 31);
+            half0[k] = __shfl_sync(kFull, incl, 15);
+            excl[k] = incl - c;
+            if (total[k] > 64) {
+                dense = true;
+            } else if (total[k] > 0) {
+                // few bits: each lane writes its own word's bits
+                const int sh = (int)(wpos[k] & 3);
+                int pos = sh + excl[k];
+                uint32_t wv = word[k];
+                while (wv) {
+                    const int b = __ffs(wv) - 1;
+                    wv &= wv - 1;
+                    st[pos++] = __ldg(dz + (lane << 5) + b);
+                }
+                __syncwarp();
+                flush_warp(a.out_z + (wpos[k] - sh), st, sh, total[k], a.vec_ok);
+                __syncwarp();
+                wpos[k] += total[k];
+            }
+        }
+        if (!dense) continue;
+        // dense rows: the group's dictionary slice is read once per half
+        // (lane l holds entry 32 j + l of the 16 words j) and shared by the
+        // rows; each half (at most 512 pairs) is staged and flushed
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int32_t dreg[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int64_t idx = gb + ((16 * h + i) << 5) + lane;
+                dreg[i] = idx < zlim ? __ldg(a.dict_z + zt0 + idx) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                if (total[k] <= 64) continue;
+                const int base = h ? half0[k] : 0;
+                const int cnt = h ? total[k] - half0[k] : half0[k];
+                if (cnt == 0) continue;
+                const int sh = (int)(wpos[k] & 3);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const uint32_t wj = __shfl_sync(kFull, word[k], 16 * h + i);
+                    const int pj = __shfl_sync(kFull, excl[k], 16 * h + i) - base;
+                    if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = dreg[i];
+                }
+                __syncwarp();
+                flush_warp(a.out_z + (wpos[k] - sh), st, sh, cnt, a.vec_ok);
+                __syncwarp();
+                wpos[k] += cnt;
+            }
+        }
+    }
+}
+
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     int32_t* stage = reinterpret_cast<int32_t*>(smem);  // kWarps x kWarpStageIds
     uint32_t* bm_all = smem + kWarps * kWarpStageIds;   // G bitmaps of tile_words words
-    __shared__ int32_t s_list[kThreads];
-    __shared__ int32_t s_lk[kThreads];
-    __shared__ int32_t s_ny[kThreads];
-    __shared__ int32_t s_nk[kThreads];
-    __shared__ int64_t s_woff[kThreads];
-    __shared__ int32_t s_wc[kWarps + 1];
-    __shared__ int32_t s_cw[kWarps], s_cn[kWarps];
+    __shared__ GroupSmem gs;
     __shared__ int32_t s_seg[G][kWarps];
     __shared__ int64_t s_blk, s_prefix;
 
@@ -563,19 +891,9 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
     }
     int64_t xr0;
     int ng;
-    if (a.groups) {
-        if (blk >= a.n_groups) return;
-        const int2 g = a.groups[blk];
-        xr0 = g.x;
-        ng = g.y;
-    } else {
-        xr0 = blk * G;
-        if (xr0 >= a.n_rows) return;
-        ng = (int)min64(G, a.n_rows - xr0);
-    }
+    if (!g_locate<G>(a, blk, xr0, ng)) return;
     const int64_t x0 = a.x_begin + xr0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt = lanemask_lt();
     const int64_t tile_words = a.tile_bits >> 5;
     // z window of the group's instance (all of Z for a single instance; the
     // rows of a group share their instance), from a 32-aligned start so that
@@ -583,12 +901,11 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
     const int tg = a.x_tag ? a.x_tag[x0] : 0;
     const int64_t zb = a.z_lo[tg] & ~int64_t(31), ze = a.z_lo[tg + 1];
     const bool tiled = a.tile_bits < ze - zb;
-    // R_CSR rows of the group are adjacent: [rb[0], r_end); rb is indexed
-    // only with unrolled constants so that it stays in registers
+    // R_CSR rows of the group are adjacent; rb is indexed only with unrolled
+    // constants so that it stays in registers
     int64_t rb[G + 1];
 #pragma unroll
     for (int k = 0; k <= G; ++k) rb[k] = a.r_rowptr[x0 + min(k, ng)];
-    const int64_t r_end = a.r_rowptr[x0 + ng];
     int64_t out_pos[G];
     bool write = true;
 #pragma unroll
@@ -599,191 +916,12 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
             fill_range(a.out_x, out_pos[k], a.off[xr0 + k + 1], a.dict_x[x0 + k], a.vec_ok);
         }
     }
-    auto row_of = [&](int64_t p) {
-        int k = 0;
-#pragma unroll
-        for (int q = 1; q < G; ++q) k += (q < ng && p >= rb[q]) ? 1 : 0;
-        return k;
-    };
-
-    // At most kThreads R entries (the usual case): one thread per entry sorts
-    // them once into per-warp lists of narrow rows (y, row) and wide rows
-    // (bitmap, row); each tile then builds its bitmaps in ONE barrier-free
-    // phase, warps walking narrow rows while every thread ORs wide rows into
-    // its words (both with shared atomics).
-    const int64_t n_ent = r_end - rb[0];
-    const bool flat = n_ent <= a.flat_max;  // block-uniform
-    if (flat) {
-        const int64_t p = rb[0] + tid;
-        int32_t y = -1, b = -1;
-        if (tid < n_ent) {
-            y = a.r_col[p];
-            b = a.bm_row_of_y[y];
-        }
-        const bool isw = b >= 0, isn = tid < n_ent && b < 0;
-        const unsigned bw = __ballot_sync(kFull, isw), bn = __ballot_sync(kFull, isn);
-        const int k = tid < n_ent ? row_of(p) : 0;
-        if (isw) {
-            const int slot = (warp << 5) + __popc(bw & lt);
-            s_woff[slot] = a.bm_off[b];
-            s_lk[slot] = k;
-        }
-        if (isn) {
-            const int slot = (warp << 5) + __popc(bn & lt);
-            s_ny[slot] = y;
-            s_nk[slot] = k;
-        }
-        if (lane == 0) {
-            s_cw[warp] = __popc(bw);
-            s_cn[warp] = __popc(bn);
-        }
-    }
-
+    const bool flat = g_prepare<G>(a, rb, ng, gs);
     for (int64_t zt0 = zb; zt0 < ze; zt0 += a.tile_bits) {
         const int64_t zt1 = min64(zt0 + a.tile_bits, ze);
         const int tw = (int)((zt1 - zt0 + 31) >> 5);
-        clear_words(bm_all, (int)(ng * tile_words));
-        __syncthreads();
-        if (flat) {
-            int n_nar = 0;
-            unsigned wmask = 0u;  // warps whose list holds wide rows
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                n_nar += s_cn[w];
-                wmask |= s_cw[w] > 0 ? 1u << w : 0u;
-            }
-            for (int e = warp; e < n_nar; e += kWarps) {
-                int sg = 0, base = 0;
-                while (e - base >= s_cn[sg]) base += s_cn[sg++];
-                const int slot = (sg << 5) + (e - base);
-                const int32_t y = s_ny[slot];
-                uint32_t* bm = bm_all + s_nk[slot] * tile_words;
-                int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
-                if (tiled) {
-                    s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
-                    s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
-                }
-                for (int64_t q = s0 + lane; q < s1; q += 32) {
-                    const int32_t z = a.ss_col[q] - (int32_t)zt0;
-                    atomicOr(&bm[z >> 5], 1u << (z & 31));
-                }
-            }
-            if (wmask) {
-                const uint32_t* bits = a.ss_bits + ((zt0 - zb) >> 5);
-                for (int w = tid; w < tw; w += kThreads) {
-                    uint32_t acc[G];
-#pragma unroll
-                    for (int k = 0; k < G; ++k) acc[k] = 0u;
-                    for (unsigned m = wmask; m; m &= m - 1) {
-                        const int sg = __ffs(m) - 1, c = s_cw[sg];
-                        for (int i = sg << 5; i < (sg << 5) + c; ++i) {
-                            const uint32_t v = __ldg(bits + s_woff[i] + w);
-                            const int k = s_lk[i];
-#pragma unroll
-                            for (int q = 0; q < G; ++q) acc[q] |= (k == q) ? v : 0u;
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < G; ++k)
-                        if (k < ng && acc[k]) atomicOr(&bm_all[k * tile_words + w], acc[k]);
-                }
-            }
-        } else {
-            // narrow S_sparse rows of all G rows: one warp per R entry
-            for (int64_t p = rb[0] + warp; p < r_end; p += kWarps) {
-                const int32_t y = a.r_col[p];
-                if (a.bm_row_of_y[y] >= 0) continue;
-                uint32_t* bm = bm_all + row_of(p) * tile_words;
-                int64_t s0 = a.ss_rowptr[y], s1 = a.ss_rowptr[y + 1];
-                if (tiled) {
-                    s0 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt0);
-                    s1 = lower_bound_dev<int32_t>(a.ss_col, s0, s1, (int32_t)zt1);
-                }
-                for (int64_t q = s0 + lane; q < s1; q += 32) {
-                    const int32_t z = a.ss_col[q] - (int32_t)zt0;
-                    atomicOr(&bm[z >> 5], 1u << (z & 31));
-                }
-            }
-            // wide S_sparse rows
-            for (int64_t base = rb[0]; base < r_end; base += kThreads) {
-                const int64_t p = base + tid;
-                const int32_t b = p < r_end ? a.bm_row_of_y[a.r_col[p]] : -1;
-                const unsigned bal = __ballot_sync(kFull, b >= 0);
-                if (lane == 0) s_wc[warp] = __popc(bal);
-                __syncthreads();
-                if (tid == 0) {
-                    int run = 0;
-                    for (int w = 0; w < kWarps; ++w) {
-                        const int c = s_wc[w];
-                        s_wc[w] = run;
-                        run += c;
-                    }
-                    s_wc[kWarps] = run;
-                }
-                __syncthreads();
-                if (b >= 0) {
-                    const int slot = s_wc[warp] + __popc(bal & lt);
-                    s_list[slot] = b;
-                    s_lk[slot] = row_of(p);
-                }
-                __syncthreads();
-                const int nl = s_wc[kWarps];
-                if (nl > 0) {
-                    const uint32_t* bits = a.ss_bits + ((zt0 - zb) >> 5);
-                    for (int w = tid; w < tw; w += kThreads) {
-                        uint32_t acc[G];
-#pragma unroll
-                        for (int k = 0; k < G; ++k) acc[k] = 0u;
-                        for (int i = 0; i < nl; ++i) {
-                            const uint32_t v = __ldg(bits + a.bm_off[s_list[i]] + w);
-                            const int k = s_lk[i];
-#pragma unroll
-                            for (int q = 0; q < G; ++q) acc[q] |= (k == q) ? v : 0u;
-                        }
-#pragma unroll
-                        for (int k = 0; k < G; ++k)
-                            if (k < ng && acc[k]) bm_all[k * tile_words + w] |= acc[k];
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        if (a.n_zd > 0) {
-            // DenseEC results, one thread per dense index of the instance (see k_xrow_bits)
-            const int64_t d0 = a.x_tag ? a.zd_lo[tg] : 0, d1 = a.x_tag ? a.zd_lo[tg + 1] : a.n_zd;
-            for (int k = 0; k < ng; ++k) {
-                const uint32_t* drow = a.d_bits + (xr0 + k) * a.zdw;
-                uint32_t* bm = bm_all + k * tile_words;
-                for (int64_t d = d0 + tid; d < d1; d += kThreads) {
-                    if ((drow[d >> 5] >> (d & 31)) & 1u) {
-                        int32_t z = a.zd_list[d];
-                        if (z >= zt0 && z < zt1) {
-                            z -= (int32_t)zt0;
-                            atomicOr(&bm[z >> 5], 1u << (z & 31));
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // per-warp segment sizes of every row
-        const int groups = (tw + 31) >> 5;
-        const int gpw = (groups + kWarps - 1) / kWarps;
-        const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
-#pragma unroll
-        for (int k = 0; k < G; ++k) {
-            int mine = 0;
-            if (k < ng) {
-                const uint32_t* bm = bm_all + k * tile_words;
-                for (int g = g0; g < g1; ++g) {
-                    const int w = (g << 5) + lane;
-                    mine += w < tw ? __popc(bm[w]) : 0;
-                }
-            }
-            mine = warp_sum(mine);
-            if (lane == 0) s_seg[k][warp] = mine;
-        }
-        __syncthreads();
+        g_build<G>(a, rb, ng, flat, tg, xr0, zb, zt0, zt1, tiled, bm_all, tile_words, gs);
+        g_counts<G>(bm_all, tile_words, tw, ng, s_seg);
         if (a.lb_status) {
             // single pass (one z tile): this block's rows start after all
             // earlier blocks' pairs
@@ -809,92 +947,100 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
                 run += ck;
             }
         }
-        int64_t wpos[G];
+        if (write) g_emit<G>(a, bm_all, tile_words, tw, ng, zt0, s_seg, out_pos, stage);
 #pragma unroll
         for (int k = 0; k < G; ++k) {
-            int64_t before = 0, all = 0;
-            for (int w = 0; w < kWarps; ++w) {
-                const int c = s_seg[k][w];
-                if (w < warp) before += c;
-                all += c;
-            }
-            wpos[k] = (k < ng ? out_pos[k] : 0) + before;
+            int64_t all = 0;
+            for (int w = 0; w < kWarps; ++w) all += s_seg[k][w];
             if (k < ng) out_pos[k] += all;
         }
-        int32_t* st = stage + warp * kWarpStageIds;
-        const int64_t zlim = a.n_z - zt0;
-        for (int g = g0; write && g < g1; ++g) {
-            const int w = (g << 5) + lane;
-            uint32_t word[G];
-            bool any = false;
-#pragma unroll
-            for (int k = 0; k < G; ++k) {
-                word[k] = (k < ng && w < tw) ? bm_all[k * tile_words + w] : 0u;
-                any |= word[k] != 0u;
-            }
-            if (!__any_sync(kFull, any)) continue;
-            const int64_t gb = (int64_t)g << 10;
-            const int32_t* dz = a.dict_z + zt0 + gb;
-            int excl[G], total[G], half0[G];
-            bool dense = false;
-#pragma unroll
-            for (int k = 0; k < G; ++k) {
-                const int c = __popc(word[k]);
-                const int incl = warp_inclusive_scan(c);
-                total[k] = __shfl_sync(kFull, incl, 31);
-                half0[k] = __shfl_sync(kFull, incl, 15);
-                excl[k] = incl - c;
-                if (total[k] > 64) {
-                    dense = true;
-                } else if (total[k] > 0) {
-                    // few bits: each lane writes its own word's bits
-                    const int sh = (int)(wpos[k] & 3);
-                    int pos = sh + excl[k];
-                    uint32_t wv = word[k];
-                    while (wv) {
-                        const int b = __ffs(wv) - 1;
-                        wv &= wv - 1;
-                        st[pos++] = __ldg(dz + (lane << 5) + b);
-                    }
-                    __syncwarp();
-                    flush_warp(a.out_z + (wpos[k] - sh), st, sh, total[k], a.vec_ok);
-                    __syncwarp();
-                    wpos[k] += total[k];
-                }
-            }
-            if (!dense) continue;
-            // dense rows: the group's dictionary slice is read once per half
-            // (lane l holds entry 32 j + l of the 16 words j) and shared by
-            // the rows; each half (at most 512 pairs) is staged and flushed
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int32_t dreg[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int64_t idx = gb + ((16 * h + i) << 5) + lane;
-                    dreg[i] = idx < zlim ? __ldg(a.dict_z + zt0 + idx) : 0;
-                }
-#pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    if (total[k] <= 64) continue;
-                    const int base = h ? half0[k] : 0;
-                    const int cnt = h ? total[k] - half0[k] : half0[k];
-                    if (cnt == 0) continue;
-                    const int sh = (int)(wpos[k] & 3);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const uint32_t wj = __shfl_sync(kFull, word[k], 16 * h + i);
-                        const int pj = __shfl_sync(kFull, excl[k], 16 * h + i) - base;
-                        if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = dreg[i];
-                    }
-                    __syncwarp();
-                    flush_warp(a.out_z + (wpos[k] - sh), st, sh, cnt, a.vec_ok);
-                    __syncwarp();
-                    wpos[k] += cnt;
-                }
-            }
-        }
         __syncthreads();
+    }
+}
+
+// Persistent single pass with one row group in flight per CTA. A CTA takes a
+// ticket, builds that group's bitmaps and publishes its pair count (the
+// look-back aggregate) at once; only then does it resolve the offset of the
+// group it built in the previous round -- every earlier group has published
+// on being built, so the wait is short -- and write that group, while the new
+// one waits in the second bitmap buffer. Output writes no longer stall behind
+// the look-back. Rows whose whole z window fits one bitmap only (the
+// single-pass condition). Every earlier ticket belongs to a CTA that published
+// before waiting on anything, so the waits end; each is bounded all the same.
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_xrow_emit_pipe(const XRowArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);   // kWarps x kWarpStageIds
+    const int64_t tile_words = a.tile_bits >> 5;
+    uint32_t* bm_base = smem + kWarps * kWarpStageIds;   // two buffers of G bitmaps
+    __shared__ GroupSmem gs;
+    __shared__ int32_t s_seg[2][G][kWarps];
+    __shared__ int64_t s_blk, s_prefix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int buf = 0;
+    bool have_prev = false;
+    int64_t p_blk = 0, p_xr0 = 0, p_agg = 0, p_zb = 0;
+    int p_ng = 0, p_tw = 0;
+    for (;;) {
+        if (tid == 0) s_blk = (int64_t)atomicAdd(a.lb_ticket, 1ull);
+        __syncthreads();
+        const int64_t blk = s_blk;
+        int64_t xr0 = 0, agg = 0, zb = 0;
+        int ng = 0, tw = 0;
+        const bool have_cur = g_locate<G>(a, blk, xr0, ng);
+        if (have_cur) {
+            const int64_t x0 = a.x_begin + xr0;
+            const int tg = a.x_tag ? a.x_tag[x0] : 0;
+            zb = a.z_lo[tg] & ~int64_t(31);
+            const int64_t ze = a.z_lo[tg + 1];
+            tw = (int)((ze - zb + 31) >> 5);
+            int64_t rb[G + 1];
+#pragma unroll
+            for (int k = 0; k <= G; ++k) rb[k] = a.r_rowptr[x0 + min(k, ng)];
+            uint32_t* bm = bm_base + (int64_t)buf * G * tile_words;
+            const bool flat = g_prepare<G>(a, rb, ng, gs);
+            g_build<G>(a, rb, ng, flat, tg, xr0, zb, zb, ze, false, bm, tile_words, gs);
+            g_counts<G>(bm, tile_words, tw, ng, s_seg[buf]);
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                for (int w = 0; w < kWarps; ++w) agg += k < ng ? s_seg[buf][k][w] : 0;
+            if (tid == 0) lookback_publish(a.lb_status, blk, agg);
+        }
+        if (have_prev) {
+            const int pb = buf ^ 1;
+            if (warp == 0) {
+                const int64_t pre = lookback_resolve(a.lb_status, p_blk, p_agg, a.lb_err, kLookbackWaitNs);
+                if (lane == 0) s_prefix = pre;
+            }
+            __syncthreads();
+            const int64_t pre = s_prefix;
+            const bool write = pre >= 0 && pre + p_agg <= a.capacity;
+            const int64_t px0 = a.x_begin + p_xr0;
+            int64_t row_pos[G];
+            int64_t run = pre;
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                int64_t ck = 0;
+                for (int w = 0; w < kWarps; ++w) ck += k < p_ng ? s_seg[pb][k][w] : 0;
+                row_pos[k] = run;
+                if (write && k < p_ng) fill_range(a.out_x, run, run + ck, a.dict_x[px0 + k], a.vec_ok);
+                if (a.cnt && tid == 0 && k < p_ng) a.cnt[p_xr0 + k] = ck;
+                run += ck;
+            }
+            if (write)
+                g_emit<G>(a, bm_base + (int64_t)pb * G * tile_words, tile_words, p_tw, p_ng, p_zb, s_seg[pb], row_pos,
+                          stage);
+            __syncthreads();
+        }
+        if (!have_cur) break;
+        have_prev = true;
+        p_blk = blk;
+        p_xr0 = xr0;
+        p_ng = ng;
+        p_agg = agg;
+        p_zb = zb;
+        p_tw = tw;
+        buf ^= 1;
     }
 }
 
@@ -1735,8 +1881,24 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
                     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_emit_g<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg));
                 *cur = (int)smg;
             }
-            if (grp == 2) k_xrow_emit_g<2><<<gg, kThreads, smg, s>>>(a);
-            else k_xrow_emit_g<4><<<gg, kThreads, smg, s>>>(a);
+            if (grp == 2 && a.lb_status && ctx.opt.emit_pipe) {
+                // persistent, one group in flight per CTA: two bitmap buffers
+                const size_t smp = (size_t)kWarps * kWarpStageIds * 4 + (size_t)4 * (size_t)(a.tile_bits / 32) * 4;
+                static int curp[64] = {0};
+                if ((int)smp > curp[ctx.device & 63]) {
+                    DIM3_CUDA(cudaFuncSetAttribute(k_xrow_emit_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smp));
+                    curp[ctx.device & 63] = (int)smp;
+                }
+                int per_sm = 0;
+                DIM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xrow_emit_pipe<2>, kThreads, smp));
+                const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>(gg, (int64_t)ctx.sm_count * std::max(per_sm, 1)));
+                k_xrow_emit_pipe<2><<<gp, kThreads, smp, s>>>(a);
+            } else if (grp == 2) {
+                k_xrow_emit_g<2><<<gg, kThreads, smg, s>>>(a);
+            } else {
+                k_xrow_emit_g<4><<<gg, kThreads, smg, s>>>(a);
+            }
         } else if (emit) {
             k_xrow_bits<true><<<g, kThreads, sm, s>>>(a);
         } else {
