@@ -972,7 +972,10 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_pipe(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     int32_t* stage = reinterpret_cast<int32_t*>(smem);   // kWarps x kWarpStageIds
     const int64_t tile_words = a.tile_bits >> 5;
-    uint32_t* bm_base = smem + kWarps * kWarpStageIds;   // two buffers of G bitmaps
+    // two buffers of G bitmaps; the second starts on a 16-byte boundary
+    // (clear_words stores 16 bytes at a time)
+    const int64_t buf_words = (G * tile_words + 3) & ~int64_t(3);
+    uint32_t* bm_base = smem + kWarps * kWarpStageIds;
     __shared__ GroupSmem gs;
     __shared__ int32_t s_seg[2][G][kWarps];
     __shared__ int64_t s_blk, s_prefix;
@@ -997,7 +1000,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_pipe(const XRowArgs a) {
             int64_t rb[G + 1];
 #pragma unroll
             for (int k = 0; k <= G; ++k) rb[k] = a.r_rowptr[x0 + min(k, ng)];
-            uint32_t* bm = bm_base + (int64_t)buf * G * tile_words;
+            uint32_t* bm = bm_base + (int64_t)buf * buf_words;
             const bool flat = g_prepare<G>(a, rb, ng, gs);
             g_build<G>(a, rb, ng, flat, tg, xr0, zb, zb, ze, false, bm, tile_words, gs);
             g_counts<G>(bm, tile_words, tw, ng, s_seg[buf]);
@@ -1028,7 +1031,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_pipe(const XRowArgs a) {
                 run += ck;
             }
             if (write)
-                g_emit<G>(a, bm_base + (int64_t)pb * G * tile_words, tile_words, p_tw, p_ng, p_zb, s_seg[pb], row_pos,
+                g_emit<G>(a, bm_base + (int64_t)pb * buf_words, tile_words, p_tw, p_ng, p_zb, s_seg[pb], row_pos,
                           stage);
             __syncthreads();
         }
@@ -1883,7 +1886,8 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
             }
             if (grp == 2 && a.lb_status && ctx.opt.emit_pipe) {
                 // persistent, one group in flight per CTA: two bitmap buffers
-                const size_t smp = (size_t)kWarps * kWarpStageIds * 4 + (size_t)4 * (size_t)(a.tile_bits / 32) * 4;
+                const size_t buf_words = ((size_t)2 * (size_t)(a.tile_bits / 32) + 3) & ~size_t(3);
+                const size_t smp = (size_t)kWarps * kWarpStageIds * 4 + 2 * buf_words * 4;
                 static int curp[64] = {0};
                 if ((int)smp > curp[ctx.device & 63]) {
                     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_emit_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
