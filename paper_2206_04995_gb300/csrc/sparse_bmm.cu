@@ -29,6 +29,7 @@ namespace dimcube {
 constexpr int kWarps = kThreads / 32;
 constexpr int kWarpStage = 1040;        // staged output values per warp (1024 + alignment shift, 16-byte multiple)
 constexpr int kWarpStageIds = 528;      // staged z ids per warp in the one-row kernel (512 + shift)
+constexpr int kWarpStageQ = 272;        // staged values per warp, quarter groups (256 + shift)
 constexpr int64_t kMaxTileWords = 12 * 1024;   // 48 KiB bitmap tile = 393,216 z (three emitting CTAs per SM)
 constexpr int kCntChunk = 4096;         // z per compaction chunk (count mode)
 constexpr int64_t kMaxCntTile = 16 * 1024;     // counters per tile (64 KiB)
@@ -781,11 +782,14 @@ __device__ __forceinline__ void g_counts(const uint32_t* bm_all, int64_t tile_wo
 
 // Compaction of the group's tile: every warp writes the z values of its run
 // of 32-word groups for each row, row k's run starting at row_pos[k] plus the
-// earlier warps' segments of that row. No block barrier.
-template <int G>
+// earlier warps' segments of that row. A dense 32-word group is staged and
+// flushed in P parts of 32 / P words (at most 1024 / P pairs each), so the
+// per-warp stage holds 1024 / P + 16 entries (stage_ints). No block barrier.
+template <int G, int P>
 __device__ __forceinline__ void g_emit(const XRowArgs& a, const uint32_t* bm_all, int64_t tile_words, int tw, int ng,
                                        int64_t zt0, const int32_t (&seg)[G][kWarps], const int64_t (&row_pos)[G],
-                                       int32_t* stage) {
+                                       int32_t* stage, int stage_ints) {
+    constexpr int W = 32 / P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     const int groups = (tw + 31) >> 5;
@@ -798,7 +802,7 @@ __device__ __forceinline__ void g_emit(const XRowArgs& a, const uint32_t* bm_all
         for (int w = 0; w < warp; ++w) before += seg[k][w];
         wpos[k] = (k < ng ? row_pos[k] : 0) + before;
     }
-    int32_t* st = stage + warp * kWarpStageIds;
+    int32_t* st = stage + warp * stage_ints;
     const int64_t zlim = a.n_z - zt0;
     for (int g = g0; g < g1; ++g) {
         const int w = (g << 5) + lane;
@@ -812,14 +816,14 @@ __device__ __forceinline__ void g_emit(const XRowArgs& a, const uint32_t* bm_all
         if (!__any_sync(kFull, any)) continue;
         const int64_t gb = (int64_t)g << 10;
         const int32_t* dz = a.dict_z + zt0 + gb;
-        int excl[G], total[G], half0[G];
+        int excl[G], total[G], mid[G];  // mid: the count before word 16 (two parts)
         bool dense = false;
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             const int c = __popc(word[k]);
             const int incl = warp_inclusive_scan(c);
             total[k] = __shfl_sync(kFull, incl, 31);
-            half0[k] = __shfl_sync(kFull, incl, 15);
+            mid[k] = P == 2 ? __shfl_sync(kFull, incl, 15) : 0;
             excl[k] = incl - c;
             if (total[k] > 64) {
                 dense = true;
@@ -840,28 +844,30 @@ __device__ __forceinline__ void g_emit(const XRowArgs& a, const uint32_t* bm_all
             }
         }
         if (!dense) continue;
-        // dense rows: the group's dictionary slice is read once per half
-        // (lane l holds entry 32 j + l of the 16 words j) and shared by the
-        // rows; each half (at most 512 pairs) is staged and flushed
+        // dense rows: the group's dictionary slice is read once per part
+        // (lane l holds entry 32 j + l of the W words j) and shared by the
+        // rows; each part is staged and flushed
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int32_t dreg[16];
+        for (int h = 0; h < P; ++h) {
+            int32_t dreg[W];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int64_t idx = gb + ((16 * h + i) << 5) + lane;
+            for (int i = 0; i < W; ++i) {
+                const int64_t idx = gb + ((W * h + i) << 5) + lane;
                 dreg[i] = idx < zlim ? __ldg(a.dict_z + zt0 + idx) : 0;
             }
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 if (total[k] <= 64) continue;
-                const int base = h ? half0[k] : 0;
-                const int cnt = h ? total[k] - half0[k] : half0[k];
+                // the part's first pair and its end (lane 0's exclusive count is 0)
+                const int base = h == 0 ? 0 : P == 2 ? mid[k] : __shfl_sync(kFull, excl[k], W * h);
+                const int end = h + 1 == P ? total[k] : P == 2 ? mid[k] : __shfl_sync(kFull, excl[k], W * (h + 1));
+                const int cnt = end - base;
                 if (cnt == 0) continue;
                 const int sh = (int)(wpos[k] & 3);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const uint32_t wj = __shfl_sync(kFull, word[k], 16 * h + i);
-                    const int pj = __shfl_sync(kFull, excl[k], 16 * h + i) - base;
+                for (int i = 0; i < W; ++i) {
+                    const uint32_t wj = __shfl_sync(kFull, word[k], W * h + i);
+                    const int pj = __shfl_sync(kFull, excl[k], W * h + i) - base;
                     if ((wj >> lane) & 1u) st[sh + pj + __popc(wj & lt)] = dreg[i];
                 }
                 __syncwarp();
@@ -947,7 +953,7 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
                 run += ck;
             }
         }
-        if (write) g_emit<G>(a, bm_all, tile_words, tw, ng, zt0, s_seg, out_pos, stage);
+        if (write) g_emit<G, 2>(a, bm_all, tile_words, tw, ng, zt0, s_seg, out_pos, stage, kWarpStageIds);
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             int64_t all = 0;
@@ -970,12 +976,12 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_g(const XRowArgs a) {
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_xrow_emit_pipe(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
-    int32_t* stage = reinterpret_cast<int32_t*>(smem);   // kWarps x kWarpStageIds
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);   // kWarps x kWarpStageQ (quarter groups)
     const int64_t tile_words = a.tile_bits >> 5;
     // two buffers of G bitmaps; the second starts on a 16-byte boundary
     // (clear_words stores 16 bytes at a time)
     const int64_t buf_words = (G * tile_words + 3) & ~int64_t(3);
-    uint32_t* bm_base = smem + kWarps * kWarpStageIds;
+    uint32_t* bm_base = smem + kWarps * kWarpStageQ;
     __shared__ GroupSmem gs;
     __shared__ int32_t s_seg[2][G][kWarps];
     __shared__ int64_t s_blk, s_prefix;
@@ -1031,8 +1037,8 @@ __global__ void __launch_bounds__(kThreads) k_xrow_emit_pipe(const XRowArgs a) {
                 run += ck;
             }
             if (write)
-                g_emit<G>(a, bm_base + (int64_t)pb * buf_words, tile_words, p_tw, p_ng, p_zb, s_seg[pb], row_pos,
-                          stage);
+                g_emit<G, 4>(a, bm_base + (int64_t)pb * buf_words, tile_words, p_tw, p_ng, p_zb, s_seg[pb], row_pos,
+                             stage, kWarpStageQ);
             __syncthreads();
         }
         if (!have_cur) break;
@@ -1887,7 +1893,7 @@ static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, 
             if (grp == 2 && a.lb_status && ctx.opt.emit_pipe) {
                 // persistent, one group in flight per CTA: two bitmap buffers
                 const size_t buf_words = ((size_t)2 * (size_t)(a.tile_bits / 32) + 3) & ~size_t(3);
-                const size_t smp = (size_t)kWarps * kWarpStageIds * 4 + 2 * buf_words * 4;
+                const size_t smp = (size_t)kWarps * kWarpStageQ * 4 + 2 * buf_words * 4;
                 static int curp[64] = {0};
                 if ((int)smp > curp[ctx.device & 63]) {
                     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_emit_pipe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
