@@ -514,6 +514,7 @@ def main():
                        "join_tuples_per_s": info["out_j"] * args.steps * (pairs_all / total_pairs) / busy_max},
             "roofline": roofline,
             "phase_ms": phases,
+            "partition_roofline": partition_roofline(info, phases, peaks["hbm"]),
             "wall_s": t_wall,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -526,6 +527,18 @@ def main():
     if dist:
         dist.destroy_process_group()
     ctx.close()
+
+
+def partition_roofline(info: dict, phase_ms: dict, peak_gbs: float) -> dict:
+    """Mapping + partition (a2-a6) against HBM: algorithmic bytes per call =
+    16 B per input tuple (key and value read, two ids written), 4 B per
+    dictionary entry, 12 B per R' and S tuple for the CSRs (8 B read, 4 B
+    column written), 8 B per row pointer; over the phases' device time."""
+    alg = (16 * (info["n_r"] + info["n_s"]) + 4 * (info["n_x"] + info["n_y"] + info["n_z"]) +
+           12 * (info["n_r_kept"] + info["n_s"]) + 8 * (info["n_x"] + info["n_y"] + 2))
+    ms = phase_ms.get("map", 0.0) + phase_ms.get("partition", 0.0)
+    gbs = alg / (ms / 1e3) / 1e9 if ms > 0 else None
+    return {"alg_bytes": alg, "ms": ms, "achieved_gbs": gbs, "frac": gbs / peak_gbs if gbs else None}
 
 
 def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, tune_it: bool = True):
@@ -590,7 +603,10 @@ def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, 
                          "k_xrow_emit_g)", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm"] if achieved else None, "peak_source": peaks["source"],
                          "alg_bytes_per_launch": alg_bytes, "launch_ms": emit_s * 1e3},
-            "dense_roofline": dense, "tuner": tuned, "l2": "flushed between steps"}
+            "dense_roofline": dense,
+            "partition_roofline": partition_roofline(info, {k: v[0] / steps for k, v in tm.items() if v[1]},
+                                                     peaks["hbm"]),
+            "tuner": tuned, "l2": "flushed between steps"}
 
 
 def serve_record(args, local_rank: int):
@@ -714,7 +730,8 @@ def run_batch(args, rank, world, local_rank, sub=False):
         return {"pairs_per_s": value, "ms_per_step": sum(batch_ms) / len(batch_ms), "steps": steps,
                 "plain_pairs_per_s": plain_value, "plain_ms_per_step": sum(plain_ms) / len(plain_ms),
                 "batched_over_plain": value / plain_value, "out_p": out_p, "n_inst": len(insts),
-                "roofline": roofline, "phase_ms": phase_ms, "gpu_launches": launches, "tuner": tuned}
+                "roofline": roofline, "phase_ms": phase_ms, "gpu_launches": launches, "tuner": tuned,
+                "partition_roofline": partition_roofline(info, phase_ms, peaks["hbm"])}
     e2e = None
     if not args.no_e2e:
         h_in = [[c.cpu().pin_memory() for c in cc] for cc in cols]
@@ -1049,12 +1066,86 @@ def device_columns(torch, host_cols, dev):
     return out
 
 
-def pinned_host_empty(torch, n):
-    """(tensor, release) for an int32 CPU tensor of n elements in page-locked
-    memory on transparent huge pages (anonymous mmap + MADV_HUGEPAGE, then
+def gpu_numa(torch, dev) -> dict:
+    """The GPU's PCI address and what sysfs says of its NUMA placement: its
+    node and the CPUs local to it, with the node those CPUs belong to."""
+    out = {"pci": None, "numa_node": None, "local_cpus": None, "cpu_node": None}
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        pci = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        out["pci"] = pci
+        base = f"/sys/bus/pci/devices/{pci}"
+        with open(base + "/numa_node") as f:
+            out["numa_node"] = int(f.read().strip())
+        with open(base + "/local_cpulist") as f:
+            out["local_cpus"] = f.read().strip()
+        first = int(out["local_cpus"].split(",")[0].split("-")[0])
+        import glob
+
+        for nd in glob.glob("/sys/devices/system/node/node*/cpu%d" % first):
+            out["cpu_node"] = int(nd.split("/node")[-1].split("/")[0].replace("node", ""))
+    except Exception:  # noqa: BLE001
+        pass
+    return out
+
+
+def host_region_info(addr: int) -> dict:
+    """Where the pages of the mapping holding host address addr live: pages per
+    NUMA node (/proc/self/numa_maps) and the bytes on transparent huge pages
+    (AnonHugePages of /proc/self/smaps)."""
+    out = {"numa_pages": None, "anon_huge_bytes": None}
+    try:
+        start = None
+        with open("/proc/self/smaps") as f:
+            cur = None
+            for line in f:
+                head = line.split()[0]
+                if "-" in head and ":" not in head:
+                    lo, hi = (int(v, 16) for v in head.split("-"))
+                    cur = lo if lo <= addr < hi else None
+                    if cur is not None:
+                        start = cur
+                elif cur is not None and line.startswith("AnonHugePages:"):
+                    out["anon_huge_bytes"] = int(line.split()[1]) * 1024
+        if start is not None:
+            with open("/proc/self/numa_maps") as f:
+                for line in f:
+                    parts = line.split()
+                    if int(parts[0], 16) == start:
+                        out["numa_pages"] = {p.split("=")[0]: int(p.split("=")[1]) for p in parts
+                                             if p[:1] == "N" and "=" in p}
+                        break
+    except Exception:  # noqa: BLE001
+        pass
+    return out
+
+
+def bind_to_node(addr: int, nbytes: int, node: int) -> bool:
+    """mbind(MPOL_BIND) of [addr, addr + nbytes) to one NUMA node, before its
+    pages are touched (Linux syscall, x86_64 and aarch64 numbers)."""
+    import ctypes
+    import platform
+
+    nr = {"x86_64": 237, "aarch64": 235}.get(platform.machine())
+    if nr is None or node is None or node < 0 or node >= 64:
+        return False
+    try:
+        libc = ctypes.CDLL(None, use_errno=True)
+        mask = ctypes.c_ulong(1 << node)
+        rc = libc.syscall(ctypes.c_long(nr), ctypes.c_void_p(addr), ctypes.c_ulong(nbytes), ctypes.c_int(2),
+                          ctypes.byref(mask), ctypes.c_ulong(64), ctypes.c_uint(0))
+        return rc == 0
+    except Exception:  # noqa: BLE001
+        return False
+
+
+def pinned_host_empty(torch, n, node=None):
+    """(tensor, release, info) for an int32 CPU tensor of n elements in
+    page-locked memory on transparent huge pages (anonymous mmap +
+    MADV_HUGEPAGE, bound to NUMA node `node` when given, then
     cudaHostRegister), on which large device-to-host copies run at link speed
-    consistently; release() undoes the registration. The fallback is torch's
-    pinned allocator, with release None."""
+    consistently; release() undoes the registration; info says where the
+    pages landed. The fallback is torch's pinned allocator (release None)."""
     import mmap
 
     try:
@@ -1063,6 +1154,7 @@ def pinned_host_empty(torch, n):
         if hasattr(mmap, "MADV_HUGEPAGE"):
             m.madvise(mmap.MADV_HUGEPAGE)
         a = np.frombuffer(m, dtype=np.int32, count=max(n, 1))
+        bound = bind_to_node(a.ctypes.data, nbytes, node) if node is not None else False
         for o in range(0, a.size, 1 << 26):  # fault the pages in (huge pages where the kernel has them)
             a[o:o + (1 << 26)] = 0
         rt = torch.cuda.cudart()
@@ -1074,14 +1166,17 @@ def pinned_host_empty(torch, n):
         def release():
             rt.cudaHostUnregister(a.ctypes.data)
 
-        return t, release
+        return t, release, dict(host_region_info(a.ctypes.data), bound_node=node if bound else None)
     except Exception:  # noqa: BLE001
-        return torch.empty(n, dtype=torch.int32, pin_memory=True), None
+        return torch.empty(n, dtype=torch.int32, pin_memory=True), None, None
 
 
 def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
     """Same metric through the public call with HOST buffers: pinned host
-    inputs copied in, the join (``join_call``), both output columns copied out."""
+    inputs copied in, the join (``join_call``), both output columns copied out.
+    The output columns are placed on the NUMA node of the CPUs local to the
+    GPU when sysfs names one. A further, separately timed step records each
+    copy's time and rate, and the record says where the host pages landed."""
     pin = True
     # a column given twice (a self-join's R and S) is copied once
     uniq, idx = [], []
@@ -1091,11 +1186,14 @@ def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
             uniq.append(a)
             k = len(uniq) - 1
         idx.append(k)
-    releases = []
+    releases, placement = [], []
+    gpu = gpu_numa(torch, dev)
     try:
         h_in = [torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory() for a in uniq]
-        (h_x, rx), (h_z, rz) = pinned_host_empty(torch, out_p), pinned_host_empty(torch, out_p)
+        (h_x, rx, ix), (h_z, rz, iz) = (pinned_host_empty(torch, out_p, gpu["cpu_node"]),
+                                        pinned_host_empty(torch, out_p, gpu["cpu_node"]))
         releases = [r for r in (rx, rz) if r is not None]
+        placement = [ix, iz]
         pin = h_x.is_pinned() and h_z.is_pinned()
     except Exception:  # noqa: BLE001
         pin = False
@@ -1109,12 +1207,22 @@ def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
     h2d = sum(h.numel() * 4 for h in h_in)
     d2h = 2 * out_p * 4
 
-    def one():
+    def one(ev=None):
+        if ev:
+            ev[0].record()
         for d, h in zip(d_in, h_in):
             d.copy_(h, non_blocking=pin)
+        if ev:
+            ev[1].record()
         x, z = join_call(d_cols, d_x, d_z)
+        if ev:
+            ev[2].record()
         h_x.copy_(x, non_blocking=pin)
+        if ev:
+            ev[3].record()
         h_z.copy_(z, non_blocking=pin)
+        if ev:
+            ev[4].record()
 
     one()
     torch.cuda.synchronize()
@@ -1127,14 +1235,22 @@ def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
+    # one more step with an event between every part
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    one(ev)
     torch.cuda.synchronize()
+    part = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+    parts = {"h2d_ms": part[0], "join_ms": part[1], "d2h_x_ms": part[2], "d2h_z_ms": part[3],
+             "h2d_gbs": h2d / max(part[0], 1e-6) / 1e6, "d2h_x_gbs": out_p * 4 / max(part[2], 1e-6) / 1e6,
+             "d2h_z_gbs": out_p * 4 / max(part[3], 1e-6) / 1e6}
     del d_in, d_x, d_z
     for rel in releases:
         rel()
     return {"value": out_p * steps / sum(times), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h,
             "host_memory": ("pinned, huge pages" if len(releases) == 2 else "pinned") if pin else "pageable",
-            "ms_per_step": 1e3 * sum(times) / steps}
+            "ms_per_step": 1e3 * sum(times) / steps, "parts": parts, "gpu_numa": gpu,
+            "out_columns": placement}
 
 
 if __name__ == "__main__":

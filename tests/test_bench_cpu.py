@@ -79,3 +79,23 @@ def test_cpu_baseline_checks_sampled_rows():
     _, ver = bench.cpu_baseline(inst, 0.01, check=(np.array([mid], np.int32),
                                                     lambda xs: bench.rows_on_device(torch, tx, tz, xs)))
     assert not ver["ok"]
+
+
+def test_partition_roofline_formula():
+    info = {"n_r": 100, "n_s": 50, "n_x": 10, "n_y": 5, "n_z": 7, "n_r_kept": 90}
+    r = bench.partition_roofline(info, {"partition": 0.002}, 1000.0)
+    alg = 16 * 150 + 4 * 22 + 12 * 140 + 8 * 17
+    assert r["alg_bytes"] == alg and abs(r["achieved_gbs"] - alg / 2e-6 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved_gbs"] / 1000.0) < 1e-12
+    assert bench.partition_roofline(info, {}, 1000.0)["frac"] is None
+
+
+def test_host_region_info_finds_the_mapping():
+    import mmap
+
+    m = mmap.mmap(-1, 8 << 20, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+    a = np.frombuffer(m, dtype=np.int32)
+    a[:] = 1
+    info = bench.host_region_info(a.ctypes.data)
+    assert info["anon_huge_bytes"] is not None and info["anon_huge_bytes"] >= 0
+    assert info["numa_pages"] is None or sum(info["numa_pages"].values()) >= 1
