@@ -1249,7 +1249,8 @@ def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
     return {"value": out_p * steps / sum(times), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h,
             "host_memory": ("pinned, huge pages" if len(releases) == 2 else "pinned") if pin else "pageable",
-            "ms_per_step": 1e3 * sum(times) / steps, "parts": parts, "gpu_numa": gpu,
+            "ms_per_step": 1e3 * sum(times) / steps, "step_ms": [round(1e3 * t, 2) for t in times],
+            "parts": parts, "gpu_numa": gpu,
             "out_columns": placement}
 
 

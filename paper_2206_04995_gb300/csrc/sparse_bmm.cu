@@ -257,12 +257,21 @@ __device__ __forceinline__ void compact_run(const XRowArgs& a, const uint32_t* b
         const int wl = (gc << 5) + (lane << 2);
         const int wlim = min(tw, g1 << 5);
         uint32_t wv[4];
+        if (wl + 4 <= wlim) {
+            // one 16-byte load per lane (wl is a multiple of 4 and bm 16-byte
+            // aligned): no bank conflicts, unlike four stride-4 word loads
+            const uint4 q = *reinterpret_cast<const uint4*>(bm + wl);
+            wv[0] = q.x;
+            wv[1] = q.y;
+            wv[2] = q.z;
+            wv[3] = q.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) wv[k] = wl + k < wlim ? bm[wl + k] : 0u;
+        }
         int c4 = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            wv[k] = wl + k < wlim ? bm[wl + k] : 0u;
-            c4 += __popc(wv[k]);
-        }
+        for (int k = 0; k < 4; ++k) c4 += __popc(wv[k]);
         const int incl4 = warp_inclusive_scan(c4);
         const int total_c = __shfl_sync(kFull, incl4, 31);
         if (total_c == 0) continue;
