@@ -139,8 +139,9 @@ typedef enum {
                                    0: always group by group; <0: default (512); at most 1024 */
     DIM3_OPT_PATH = 9,          /* dim3_join_project / dim3_join_count: 0 (default) f1 of Section 2.6
                                    chooses, 1 the hybrid DIM^3 path, 2 the classical solution */
-    DIM3_OPT_TILE_WORDS = 10,   /* z ranges wider than one shared-memory bitmap (393,216 z): 32-bit words
-                                   per z tile, 1024..12288; 0 (default): the fewest tiles, equal sizes */
+    DIM3_OPT_TILE_WORDS = 10,   /* 32-bit words per z tile, 1024..12288, of the bitmap over z ranges wider
+                                   than 393,216 z and of Join-Count's packed counters; 0 (default): the
+                                   fewest tiles of at most 12,288 (bitmap) / 7,168 (counters) words */
     DIM3_OPT_DENSE_TILE_N = 11, /* tensor-core DenseEC: dense z per CTA tile, 128 or 256; 0 (default): 256 */
     DIM3_OPT_EMIT_PIPELINE = 12 /* single-pass emission with two x rows per CTA: 1 = persistent CTAs that
                                    build the next row group while the previous one's offset resolves;

@@ -1952,11 +1952,12 @@ static int counter_bits(Plan& p, cudaStream_t s) {
 
 // Arguments of k_cnt_rows: z per tile = counter words (at most kMaxPackedWords,
 // equal tiles) x counters per word; tile starts when there are several tiles.
-static XRowArgs cnt_args(Plan& p, int64_t x_begin, int64_t rows, int cb, cudaStream_t s) {
+static XRowArgs cnt_args(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t rows, int cb, cudaStream_t s) {
     XRowArgs a = make_args(p, x_begin, rows, 1);
     const int64_t cpw = 32 / cb;
     const int64_t words = std::max<int64_t>(1, ceil_div(p.info.n_z, cpw));
-    const int64_t n_tiles = ceil_div(words, kMaxPackedWords);
+    const int64_t max_words = ctx.opt.tile_words > 0 ? ctx.opt.tile_words : kMaxPackedWords;
+    const int64_t n_tiles = ceil_div(words, max_words);
     a.tile_bits = ceil_div(words, n_tiles) * cpw;
     a.n_tiles = (int)ceil_div(std::max<int64_t>(p.info.n_z, 1), a.tile_bits);
     a.tile_ptr = nullptr;
@@ -1972,7 +1973,7 @@ static void launch_cnt(const Ctx& ctx, const XRowArgs& a, int cb, bool emit, cud
     if (a.n_rows <= 0 || a.n_z <= 0) return;
     static bool done[64] = {false};
     if (!done[ctx.device & 63]) {
-        const int mx = (int)((size_t)2 * kWarps * kCntStageP * 4 + (size_t)kMaxPackedWords * 4);
+        const int mx = (int)((size_t)2 * kWarps * kCntStageP * 4 + (size_t)12288 * 4);  // the largest tile option
         DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -2053,7 +2054,7 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
         if (p.info.n_z <= 0 || p.info.n_r_kept == 0) {
             DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
         } else if (use_packed_counts(p, kind)) {
-            XRowArgs a = cnt_args(p, x_begin, rows, counter_bits(p, s), s);
+            XRowArgs a = cnt_args(ctx, p, x_begin, rows, counter_bits(p, s), s);
             a.d_cnt = p.cache_dcnt.as<int32_t>();
             a.cnt = cnt.as<int64_t>();
             launch_cnt(ctx, a, counter_bits(p, s), false, s);
@@ -2219,7 +2220,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
     if (total > 0 && use_packed_counts(p, kind)) {
         DIM3_REQUIRE(out_x && out_z && out_cnt, DIM3_ERR_ARG, "null output buffer");
         const int cb = counter_bits(p, s);
-        XRowArgs a = cnt_args(p, x_begin, rows, cb, s);
+        XRowArgs a = cnt_args(ctx, p, x_begin, rows, cb, s);
         a.d_cnt = p.cache_dcnt.as<int32_t>();
         a.off = p.cache_off.as<int64_t>();
         a.out_x = out_x;
