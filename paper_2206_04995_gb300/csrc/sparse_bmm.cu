@@ -78,8 +78,7 @@ struct XRowArgs {
     const int32_t* unit_rows;  // row numbers (x - x_begin) of the rows to run, or null (rows 0 .. n_list-1)
     int64_t n_list;            // rows in the list
     int n_tiles;               // z tiles per row
-    int32_t* tcnt;             // counting pass (and single pass) out: pairs of every unit [n_list * n_tiles]
-    const int64_t* lpre;       // single pass: exclusive scan over rows of the light rows' counts, or null
+    int32_t* tcnt;             // counting pass out: pairs of every unit [n_list * n_tiles]
     const int32_t* tcnt_in;    // emitting pass: the counting pass's unit pairs
     // k_xrow_emit_g over a batch: groups of up to G rows of one instance,
     // (first row, rows) each; null = consecutive groups of G rows
@@ -1259,18 +1258,8 @@ __device__ __forceinline__ void visit_chunk(const XRowArgs& a, int64_t c0, int n
     }
 }
 
-// Modes of k_tile_rows: counting pass (unit pairs to a.tcnt), emitting pass
-// after it (offsets from a.off and a.tcnt_in), or ONE pass: units take
-// tickets in (row, tile) order and find their offsets by decoupled look-back;
-// a unit's aggregate is its pairs plus, for a row's first tile, the pairs of
-// the light rows between the previous listed row and this one (a.lpre: the
-// exclusive scan of the light rows' counts, counted beforehand), so the light
-// rows' places are kept free for their own kernel.
-constexpr int kTileCount = 0, kTileEmit = 1, kTileSingle = 2;
-
-template <int kMode>
+template <bool kEmit>
 __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
-    constexpr bool kEmit = kMode != kTileCount;
     extern __shared__ __align__(16) uint32_t smem[];
     int32_t* stage = reinterpret_cast<int32_t*>(smem);           // emit: kWarps x a.stage_ints
     uint32_t* bm = smem + (kEmit ? kWarps * a.stage_ints : 0);  // tile words
@@ -1278,15 +1267,9 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
     __shared__ int32_t s_wide[kTileChunk];   // bitmap rows of the chunk's wide S rows
     __shared__ int32_t s_wc[kWarps];
     __shared__ int64_t s_scan[kWarps + 1];
-    __shared__ int64_t s_blk, s_prefix;
     __shared__ int s_nwide[2];  // wide rows of the current chunk; the two alternate between chunks
 
-    int64_t unit = blockIdx.x;
-    if (kMode == kTileSingle) {
-        if (threadIdx.x == 0) s_blk = (int64_t)atomicAdd(a.lb_ticket, 1ull);
-        __syncthreads();
-        unit = s_blk;
-    }
+    const int64_t unit = blockIdx.x;
     const int T = a.n_tiles;
     const int64_t li = unit / T;
     const int t = (int)(unit - li * T);
@@ -1296,7 +1279,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t zt0 = (int64_t)t * a.tile_bits, zt1 = min64(zt0 + a.tile_bits, a.n_z);
     const int tw = (int)((zt1 - zt0 + 31) >> 5);
-    if (kMode == kTileEmit && a.tcnt_in[unit] == 0) return;  // nothing of this row in this tile
+    if (kEmit && a.tcnt_in[unit] == 0) return;  // nothing of this row in this tile
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
     clear_words(bm, tw);
     if (tid == 0) s_nwide[0] = 0;
@@ -1340,6 +1323,9 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
         if (tid == 0) a.tcnt[unit] = (int32_t)c;
         return;
     }
+    int64_t o = a.off[xr];
+    for (int u = 0; u < t; ++u) o += a.tcnt_in[li * T + u];
+    fill_range(a.out_x, o, o + a.tcnt_in[unit], a.dict_x[x], a.vec_ok);
     const int groups = (tw + 31) >> 5;
     const int gpw = (groups + kWarps - 1) / kWarps;
     const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
@@ -1351,29 +1337,6 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
     mine = warp_sum(mine);
     if (lane == 0) s_wc[warp] = mine;
     __syncthreads();
-    int64_t o, n_unit;
-    if (kMode == kTileEmit) {
-        o = a.off[xr];
-        for (int u = 0; u < t; ++u) o += a.tcnt_in[li * T + u];
-        n_unit = a.tcnt_in[unit];
-    } else {
-        n_unit = 0;
-        for (int w = 0; w < kWarps; ++w) n_unit += s_wc[w];
-        int64_t gap = 0;  // light rows' pairs before this row (after the previous listed row)
-        if (t == 0 && a.lpre)
-            gap = a.lpre[xr] - (li > 0 ? a.lpre[(a.unit_rows ? (int64_t)a.unit_rows[li - 1] : li - 1) + 1] : 0);
-        const int64_t agg = n_unit + gap;
-        if (warp == 0) {
-            const int64_t pre = lookback_prefix(a.lb_status, unit, agg, a.lb_err, kLookbackWaitNs);
-            if (lane == 0) s_prefix = pre;
-        }
-        if (tid == 0) a.tcnt[unit] = (int32_t)n_unit;
-        __syncthreads();
-        const int64_t pre = s_prefix;
-        if (pre < 0 || pre + agg > a.capacity) return;  // gave up, or past the buffer: write nothing
-        o = pre + gap;
-    }
-    fill_range(a.out_x, o, o + n_unit, a.dict_x[x], a.vec_ok);
     int64_t wpos = o;
     for (int w = 0; w < warp; ++w) wpos += s_wc[w];
     compact_run(a, bm, tw, g0, g1, mine, zt0, wpos, stage + warp * a.stage_ints);
@@ -1550,9 +1513,8 @@ static void setup_attrs(const Ctx& ctx) {
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
-    DIM3_CUDA(cudaFuncSetAttribute(k_tile_rows<kTileCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
-    DIM3_CUDA(cudaFuncSetAttribute(k_tile_rows<kTileEmit>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
-    DIM3_CUDA(cudaFuncSetAttribute(k_tile_rows<kTileSingle>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_tile_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_tile_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     done[d] = true;
 }
 
@@ -2037,8 +1999,7 @@ static void launch_cnt(const Ctx& ctx, const XRowArgs& a, int cb, bool emit, cud
     DIM3_LAUNCHED();
 }
 
-// One (row, tile) unit per CTA: counting (a.tcnt), emitting (a.tcnt_in), or
-// one pass (a.lb_status set).
+// One (row, tile) unit per CTA: counting (a.tcnt) or emitting (a.tcnt_in).
 static void launch_tiles(const Ctx& ctx, const XRowArgs& a, bool emit, cudaStream_t s) {
     const int64_t units = a.n_list * a.n_tiles;
     if (units <= 0) return;
@@ -2046,9 +2007,8 @@ static void launch_tiles(const Ctx& ctx, const XRowArgs& a, bool emit, cudaStrea
     setup_attrs(ctx);
     PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
     const size_t sm = bits_smem(a.tile_bits, emit, a.stage_ints);
-    if (emit && a.lb_status) k_tile_rows<kTileSingle><<<(unsigned)units, kThreads, sm, s>>>(a);
-    else if (emit) k_tile_rows<kTileEmit><<<(unsigned)units, kThreads, sm, s>>>(a);
-    else k_tile_rows<kTileCount><<<(unsigned)units, kThreads, sm, s>>>(a);
+    if (emit) k_tile_rows<true><<<(unsigned)units, kThreads, sm, s>>>(a);
+    else k_tile_rows<false><<<(unsigned)units, kThreads, sm, s>>>(a);
     DIM3_LAUNCHED();
 }
 
@@ -2243,94 +2203,10 @@ static int64_t plan_join_single_pass(const Ctx& ctx, Plan& p, int64_t x_begin, i
     return total;
 }
 
-// Join-Project of a range of a z-tiled plan with ONE emitting pass over the
-// (row, tile) units: the light rows are counted first (their own kernel), the
-// units count, find their offsets by look-back and write at once, then the
-// row counts are summed and scanned (kept as the plan's counting-pass cache)
-// and the light rows are written at their offsets.
-static int64_t plan_join_tiled_single(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int32_t* out_x,
-                                      int32_t* out_z, int64_t capacity, int64_t* count, cudaStream_t s) {
-    const int64_t rows = x_end - x_begin;
-    DevBuf dbits;
-    if (p.n_zd_total > 0) {
-        dbits.alloc((size_t)(rows * p.zdw) * 4, s);
-        dense_ec(ctx, p, x_begin, rows, 0, dbits.as<uint32_t>(), nullptr, s);
-    }
-    XRowArgs a = tile_args(p, x_begin, rows, tile_words_for(ctx, p) * 32, s);
-    a.d_bits = dbits.as<uint32_t>();
-    const uint8_t* light = ensure_light(ctx, p, s);
-    DevBuf units, cnt, lpre, tcnt, status, err;
-    a.n_list = light ? list_rows(light, x_begin, rows, 0, units, s) : rows;
-    a.unit_rows = units.as<int32_t>();
-    cnt.alloc((size_t)rows * 8, s);
-    DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
-    if (light) {
-        {
-            PhaseScope phase(ctx.stats, PH_COUNT, s);
-            launch_light(p, x_begin, rows, cnt.as<int64_t>(), nullptr, nullptr, nullptr, s);
-        }
-        lpre.alloc((size_t)(rows + 1) * 8, s);
-        exclusive_scan_i64(cnt.as<int64_t>(), lpre.as<int64_t>(), rows, s);
-        a.lpre = lpre.as<int64_t>();
-    }
-    const int64_t n_units = a.n_list * a.n_tiles;
-    tcnt.alloc((size_t)std::max<int64_t>(n_units, 1) * 4, s);
-    a.tcnt = tcnt.as<int32_t>();
-    a.out_x = out_x;
-    a.out_z = out_z;
-    a.vec_ok = ((reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z)) & 15u) == 0;
-    a.capacity = capacity;
-    set_stage(ctx, p, a, std::min<int64_t>(p.info.out_j, capacity));
-    if (n_units > 0) {
-        status.alloc((size_t)(n_units + 1) * 8, s);  // ticket, then one status per unit
-        err.alloc(4, s);
-        DIM3_CUDA(cudaMemsetAsync(status.p, 0, status.bytes, s));
-        DIM3_CUDA(cudaMemsetAsync(err.p, 0, 4, s));
-        a.lb_ticket = status.as<unsigned long long>();
-        a.lb_status = a.lb_ticket + 1;
-        a.lb_err = err.as<int>();
-        launch_tiles(ctx, a, true, s);
-        int h_err = 0;
-        DIM3_CUDA(cudaMemcpyAsync(&h_err, err.p, 4, cudaMemcpyDeviceToHost, s));
-        DIM3_CUDA(cudaStreamSynchronize(s));
-        DIM3_REQUIRE(h_err == 0, DIM3_ERR_TIMEOUT, "single-pass compaction: a unit's offset was not published in time");
-        k_tile_sum<<<blocks_for(a.n_list), kThreads, 0, s>>>(a.tcnt, a.unit_rows, a.n_list, a.n_tiles,
-                                                            cnt.as<int64_t>());
-        DIM3_LAUNCHED();
-    }
-    p.cache_off.alloc((size_t)(rows + 1) * 8, s);
-    exclusive_scan_i64(cnt.as<int64_t>(), p.cache_off.as<int64_t>(), rows, s);
-    const int64_t total = read_i64(p.cache_off.as<int64_t>() + rows, s);
-    // the counts are the plan's counting-pass cache for later calls on the range
-    p.cache_dbits = std::move(dbits);
-    p.cache_dcnt.release();
-    p.cache_units = std::move(units);
-    p.cache_tcnt = std::move(tcnt);
-    p.cache_n_list = a.n_list;
-    p.cache_tiles = a.n_tiles;
-    p.cache_tile_bits = a.tile_bits;
-    p.cache_begin = x_begin;
-    p.cache_end = x_end;
-    p.cache_kind = 0;
-    if (count) *count = total;
-    if (total > capacity)
-        throw Error(DIM3_ERR_CAPACITY,
-                    "output capacity " + std::to_string(capacity) + " < result size " + std::to_string(total));
-    if (light) {
-        PhaseScope phase(ctx.stats, PH_EMIT, s);
-        launch_light(p, x_begin, rows, nullptr, p.cache_off.as<int64_t>(), out_x, out_z, s);
-    }
-    DIM3_CUDA(cudaStreamSynchronize(s));
-    return total;
-}
-
 int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int kind, int32_t* out_x, int32_t* out_z,
                   int32_t* out_cnt, int64_t capacity, int64_t* count, cudaStream_t s) {
     check_range(p, x_begin, x_end);
     const bool cached = p.cache_begin == x_begin && p.cache_end == x_end && p.cache_kind == kind;
-    if (!cached && kind == 0 && capacity > 0 && out_x && out_z && x_end > x_begin && p.info.n_z > 0 &&
-        p.info.n_r_kept > 0 && use_tiles(ctx, p, 0) && !ctx.opt.two_pass)
-        return plan_join_tiled_single(ctx, p, x_begin, x_end, out_x, out_z, capacity, count, s);
     if (!cached && kind == 0 && capacity > 0 && out_x && out_z && x_end > x_begin && p.info.n_z > 0 &&
         p.info.n_r_kept > 0 && !use_tiles(ctx, p, 0) && p.zw <= kMaxTileWords && !ctx.opt.two_pass &&
         !ensure_light(ctx, p, s))
