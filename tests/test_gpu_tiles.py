@@ -90,3 +90,34 @@ def test_tile_option_range():
         c.set_option(dim3.OPT_TILE_WORDS, 0)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("light", [-1, 0, 64])
+def test_tiles_plan_range_row_counts_and_capacity(light, cases):
+    """Tiled rows on a plan x range into caller buffers: exact pairs, the row
+    counts the plan keeps for later queries, and a short buffer reported with
+    the exact size."""
+    c = ctx_with({dim3.OPT_TILE_WORDS: 1024, dim3.OPT_LIGHT_ROW_MAX: light})
+    try:
+        for inst, ox, oz in cases:
+            cols = inst_dev(inst)
+            plan = c.partition(*cols)
+            n_x = plan.info["n_x"]
+            a, b = n_x // 5, n_x - n_x // 7
+            dx = host(plan.export("dict_x"))
+            sel = (ox >= dx[a]) & (ox <= dx[b - 1])
+            bx = torch.empty(int(sel.sum()) + 2, dtype=torch.int32, device="cuda")
+            bz = torch.empty(int(sel.sum()) + 2, dtype=torch.int32, device="cuda")
+            x, z = plan.join_project(a, b, out_x=bx[1:], out_z=bz[1:])
+            assert np.array_equal(host(x), ox[sel]) and np.array_equal(host(z), oz[sel]), inst.name
+            ux, cnt = np.unique(ox[sel], return_counts=True)
+            exp = np.zeros(b - a, np.int64)
+            exp[np.searchsorted(dx[a:b], ux)] = cnt
+            assert np.array_equal(host(plan.row_counts(a, b)), exp), inst.name
+            plan.close()
+            short = torch.empty(ox.size // 2 + 1, dtype=torch.int32, device="cuda")
+            with pytest.raises(dim3.Dim3Error) as ei:
+                c.join_project(*cols, out_x=short, out_z=short.clone())
+            assert ei.value.status == dim3.DIM3_ERR_CAPACITY and str(ox.size) in str(ei.value)
+    finally:
+        c.close()
