@@ -1695,6 +1695,8 @@ struct LightArgs {
     const int64_t* off;   // emitting pass: row offsets
     int32_t* out_x;
     int32_t* out_z;
+    int64_t n_z;          // medium rows: the z range (bucket count)
+    int vec_ok;           // medium rows: out_x 16-byte aligned at 16-byte offsets
 };
 
 template <bool kEmit>
@@ -1773,9 +1775,169 @@ __global__ void __launch_bounds__(kThreads) k_light_rows(const LightArgs a) {
     }
 }
 
-__global__ void k_light_flags(const int64_t* __restrict__ outj_x, int64_t n_x, int64_t lim, uint8_t* light) {
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n_x; x += (int64_t)gridDim.x * blockDim.x)
-        light[x] = outj_x[x] <= lim ? 1 : 0;
+// ------------------------------------------------------------- medium rows
+// An x with more join tuples than a light row but at most kMidMax, on a wide
+// z range: its SPA would be a |Z|-bit bitmap (several shared-memory tiles)
+// scanned word by word to extract a few thousand pairs. One CTA instead
+// gathers the row's join tuples' z ids into shared memory, distributes them to
+// buckets of 4,096 consecutive z ids (a counting sort on the high bits), and
+// deduplicates each bucket with a 128-word bitmap owned by one warp, whose set
+// bits come out in z order. The cost follows the row's tuples and its z
+// range's bucket count, not |Z| bits.
+constexpr int kMidMax = 8192;            // join tuples of a medium row at most
+constexpr int kMidBucketBits = 12;       // 4,096 z per bucket
+constexpr int kMidMaxBuckets = 1024;     // z ranges up to 4,194,304
+constexpr size_t kMidSmem = (size_t)kWarps * 128 * 4 + (size_t)kMidMax * 4 + (size_t)kMidMax * 2 +
+                            (size_t)(3 * kMidMaxBuckets + 1) * 4;
+
+template <bool kEmit>
+__global__ void __launch_bounds__(kThreads) k_mid_rows(const LightArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t* wbm = smem;                                                        // [kWarps][128] bucket bitmaps
+    int32_t* zs = reinterpret_cast<int32_t*>(wbm + kWarps * 128);                // [kMidMax] z ids
+    uint16_t* low = reinterpret_cast<uint16_t*>(zs + kMidMax);                   // [kMidMax] low bits, by bucket
+    int32_t* hist = reinterpret_cast<int32_t*>(low + kMidMax);                   // [buckets] items, then distinct
+    int32_t* bstart = hist + kMidMaxBuckets;                                     // [buckets + 1]
+    int32_t* cursor = bstart + kMidMaxBuckets + 1;                               // [buckets]
+    __shared__ int32_t s_len[kTileChunk], s_off[kTileChunk];
+    __shared__ uint32_t s_s0[kTileChunk];
+    __shared__ int32_t s_sc[kWarps + 1];
+    __shared__ int64_t s_scan[kWarps + 1];
+
+    const int64_t xr = a.rows[blockIdx.x], x = a.x_begin + xr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
+    // 1. the row's join tuples' z ids, entry after entry
+    int n = 0;
+    for (int64_t c0 = r0; c0 < r1; c0 += kTileChunk) {
+        const int nc = (int)min64(kTileChunk, r1 - c0);
+        int len[2];
+        uint32_t first[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = 2 * tid + k;
+            len[k] = 0;
+            first[k] = 0u;
+            if (i < nc) {
+                const int32_t y = a.r_col[c0 + i];
+                const int64_t s0 = a.ss_rowptr[y];
+                len[k] = (int)(a.ss_rowptr[y + 1] - s0);
+                first[k] = (uint32_t)s0;
+            }
+        }
+        int tot;
+        const int ex = block_exclusive_scan<int, kThreads>(len[0] + len[1], &tot, s_sc);
+        s_len[2 * tid] = len[0];
+        s_len[2 * tid + 1] = len[1];
+        s_off[2 * tid] = n + ex;
+        s_off[2 * tid + 1] = n + ex + len[0];
+        s_s0[2 * tid] = first[0];
+        s_s0[2 * tid + 1] = first[1];
+        __syncthreads();
+        for (int i = warp; i < nc; i += kWarps) {
+            const int l = s_len[i], o = s_off[i];
+            const int32_t* src = a.ss_col + s_s0[i];
+            for (int q = lane; q < l; q += 32)
+                if (o + q < kMidMax) zs[o + q] = __ldg(src + q);
+        }
+        n += tot;
+        __syncthreads();
+    }
+    n = min(n, kMidMax);
+    // 2. counting sort of the ids on their bucket (high bits); only the low
+    // bits are kept, by bucket
+    const int nb = (int)((a.n_z + (1 << kMidBucketBits) - 1) >> kMidBucketBits);
+    for (int b = tid; b < nb; b += kThreads) hist[b] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += kThreads) atomicAdd(&hist[zs[i] >> kMidBucketBits], 1);
+    __syncthreads();
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += kThreads) {
+        const int b = b0 + tid;
+        const int v = b < nb ? hist[b] : 0;
+        int tot;
+        const int ex = block_exclusive_scan<int, kThreads>(v, &tot, s_sc);
+        if (b < nb) bstart[b] = cursor[b] = carry + ex;
+        carry += tot;
+    }
+    if (tid == 0) bstart[nb] = n;
+    __syncthreads();
+    for (int i = tid; i < n; i += kThreads) {
+        const int32_t z = zs[i];
+        const int p = atomicAdd(&cursor[z >> kMidBucketBits], 1);
+        low[p] = (uint16_t)(z & ((1 << kMidBucketBits) - 1));
+    }
+    __syncthreads();
+    // 3. every bucket through one warp's 128-word bitmap; its distinct ids go
+    // back to zs at the bucket's start, ascending, and their number to hist
+    uint32_t* mb = wbm + warp * 128;
+    for (int b = warp; b < nb; b += kWarps) {
+        const int i0 = bstart[b], i1 = bstart[b + 1];
+        if (i1 == i0) {
+            if (lane == 0) hist[b] = 0;
+            continue;
+        }
+        *reinterpret_cast<uint4*>(mb + 4 * lane) = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
+        for (int i = i0 + lane; i < i1; i += 32) {
+            const int l = low[i];
+            atomicOr(&mb[l >> 5], 1u << (l & 31));
+        }
+        __syncwarp();
+        const uint4 q = *reinterpret_cast<const uint4*>(mb + 4 * lane);
+        const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+        const int c = __popc(q.x) + __popc(q.y) + __popc(q.z) + __popc(q.w);
+        const int incl = warp_inclusive_scan(c);
+        int pos = i0 + incl - c;
+        const int32_t zb = b << kMidBucketBits;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t v = wv[k];
+            while (v) {
+                const int bit = __ffs(v) - 1;
+                v &= v - 1;
+                zs[pos++] = zb + ((4 * lane + k) << 5) + bit;
+            }
+        }
+        if (lane == 31) hist[b] = incl;
+        __syncwarp();
+    }
+    __syncthreads();
+    if (!kEmit) {
+        int64_t c = 0;
+        for (int b = tid; b < nb; b += kThreads) c += hist[b];
+        c = block_sum<int64_t, kThreads>(c, s_scan);
+        if (tid == 0) a.cnt[xr] = c;
+        return;
+    }
+    // 4. each bucket's distinct z values at its place in the row's output
+    const int64_t o = a.off[xr];
+    fill_range(a.out_x, o, a.off[xr + 1], a.dict_x[x], a.vec_ok);
+    carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += kThreads) {
+        const int b = b0 + tid;
+        const int v = b < nb ? hist[b] : 0;
+        int tot;
+        const int ex = block_exclusive_scan<int, kThreads>(v, &tot, s_sc);
+        if (b < nb) cursor[b] = carry + ex;
+        carry += tot;
+    }
+    __syncthreads();
+    for (int b = warp; b < nb; b += kWarps) {
+        const int d = hist[b], src = bstart[b];
+        const int64_t dst = o + cursor[b];
+        for (int i = lane; i < d; i += 32) a.out_z[dst + i] = __ldg(a.dict_z + zs[src + i]);
+    }
+}
+
+// Row classes: 1 light (at most lim join tuples), 2 medium (at most mid_lim),
+// 0 the rest (bitmap rows).
+__global__ void k_light_flags(const int64_t* __restrict__ outj_x, int64_t n_x, int64_t lim, int64_t mid_lim,
+                              uint8_t* light) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n_x; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = outj_x[x];
+        light[x] = j <= lim ? 1 : j <= mid_lim ? 2 : 0;
+    }
 }
 
 __global__ void k_light_range(const uint8_t* __restrict__ light, int64_t x_begin, int64_t rows, int want,
@@ -1798,7 +1960,7 @@ __global__ void k_count_flags(const uint8_t* __restrict__ f, int64_t n, unsigned
     __shared__ unsigned long long s_warp[kThreads / 32 + 1];
     unsigned long long c = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        c += f[i];
+        c += f[i] != 0;
     c = block_sum<unsigned long long, kThreads>(c, s_warp);
     if (threadIdx.x == 0 && c) atomicAdd(total, c);
 }
@@ -1814,7 +1976,10 @@ static const uint8_t* ensure_light(const Ctx& ctx, Plan& p, cudaStream_t s) {
         const int64_t lim = ctx.opt.light_row_max < 0 ? kLightMax : std::min<int64_t>(ctx.opt.light_row_max, kLightMax);
         if (lim > 0 && p.n_inst == 1 && p.n_zd_total == 0 && p.info.n_z >= kLightMinZ && p.info.n_x > 0) {
             p.light.alloc((size_t)p.info.n_x, s);
-            k_light_flags<<<blocks_for(p.info.n_x), kThreads, 0, s>>>(p.outj_x.as<int64_t>(), p.info.n_x, lim,
+            // medium rows need a bucket count within kMidMaxBuckets
+            int64_t mid = ctx.opt.mid_row_max < 0 ? kMidMax : std::min<int64_t>(ctx.opt.mid_row_max, kMidMax);
+            if (p.info.n_z > ((int64_t)kMidMaxBuckets << kMidBucketBits) || mid < lim) mid = lim;
+            k_light_flags<<<blocks_for(p.info.n_x), kThreads, 0, s>>>(p.outj_x.as<int64_t>(), p.info.n_x, lim, mid,
                                                                      p.light.as<uint8_t>());
             DIM3_LAUNCHED();
             DevBuf tot;
@@ -1851,14 +2016,11 @@ static int64_t list_rows(const uint8_t* light, int64_t x_begin, int64_t rows, in
 }
 
 // the light rows of [x_begin, x_begin + rows): counting (cnt) or emitting (off)
+// The light rows (warp sorts) and the medium rows (bucketed bitmaps) of
+// [x_begin, x_begin + rows): counting (cnt) or emitting (off).
 static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* cnt, const int64_t* off,
                          int32_t* out_x, int32_t* out_z, cudaStream_t s) {
-    DevBuf list;
-    const int64_t n = list_rows(p.light.as<uint8_t>(), x_begin, rows, 1, list, s);
-    if (n == 0) return;
     LightArgs la{};
-    la.rows = list.as<int32_t>();
-    la.n = n;
     la.x_begin = x_begin;
     la.r_rowptr = p.r_rowptr.as<int64_t>();
     la.r_col = p.r_col.as<int32_t>();
@@ -1870,10 +2032,36 @@ static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* 
     la.off = off;
     la.out_x = out_x;
     la.out_z = out_z;
-    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kWarps), 152 * 8));
-    if (off) k_light_rows<true><<<g, kThreads, 0, s>>>(la);
-    else k_light_rows<false><<<g, kThreads, 0, s>>>(la);
-    DIM3_LAUNCHED();
+    la.n_z = p.info.n_z;
+    la.vec_ok = (reinterpret_cast<uintptr_t>(out_x) & 15u) == 0;
+    DevBuf list;
+    const int64_t n = list_rows(p.light.as<uint8_t>(), x_begin, rows, 1, list, s);
+    if (n > 0) {
+        la.rows = list.as<int32_t>();
+        la.n = n;
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kWarps), 152 * 8));
+        if (off) k_light_rows<true><<<g, kThreads, 0, s>>>(la);
+        else k_light_rows<false><<<g, kThreads, 0, s>>>(la);
+        DIM3_LAUNCHED();
+    }
+    DevBuf mlist;
+    const int64_t m = list_rows(p.light.as<uint8_t>(), x_begin, rows, 2, mlist, s);
+    if (m > 0) {
+        DIM3_REQUIRE(m < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long");
+        static bool done[64] = {false};
+        int dev = 0;
+        DIM3_CUDA(cudaGetDevice(&dev));
+        if (!done[dev & 63]) {
+            DIM3_CUDA(cudaFuncSetAttribute(k_mid_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmem));
+            DIM3_CUDA(cudaFuncSetAttribute(k_mid_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmem));
+            done[dev & 63] = true;
+        }
+        la.rows = mlist.as<int32_t>();
+        la.n = m;
+        if (off) k_mid_rows<true><<<(unsigned)m, kThreads, kMidSmem, s>>>(la);
+        else k_mid_rows<false><<<(unsigned)m, kThreads, kMidSmem, s>>>(la);
+        DIM3_LAUNCHED();
+    }
 }
 
 static void launch_rows(const Ctx& ctx, const XRowArgs& a, int kind, bool emit, cudaStream_t s) {

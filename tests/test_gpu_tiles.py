@@ -121,3 +121,35 @@ def test_tiles_plan_range_row_counts_and_capacity(light, cases):
             assert ei.value.status == dim3.DIM3_ERR_CAPACITY and str(ox.size) in str(ei.value)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("mid", [-1, 0, 1500, 3000])
+@pytest.mark.parametrize("light", [-1, 200])
+def test_medium_rows(mid, light, cases):
+    """Rows between the light bound and the medium bound deduplicate by
+    buckets of 4,096 z (counting sort on the high bits, one warp bitmap per
+    bucket) beside light rows and bitmap rows, on tiled and untiled z ranges,
+    one call and plan x ranges."""
+    for tw in (0, 1024):
+        c = ctx_with({dim3.OPT_MID_ROW_MAX: mid, dim3.OPT_LIGHT_ROW_MAX: light, dim3.OPT_TILE_WORDS: tw})
+        try:
+            for inst, ox, oz in cases:
+                x, z = c.join_project(*inst_dev(inst))
+                assert np.array_equal(host(x), ox) and np.array_equal(host(z), oz), (inst.name, tw)
+                plan = c.partition(*inst_dev(inst))
+                n_x = plan.info["n_x"]
+                parts = [plan.join_project(a, b) for a, b in ((0, n_x // 2), (n_x // 2, n_x))]
+                plan.close()
+                assert np.array_equal(np.concatenate([host(p[0]) for p in parts]), ox)
+                assert np.array_equal(np.concatenate([host(p[1]) for p in parts]), oz)
+        finally:
+            c.close()
+
+
+def test_medium_row_option_off_matches():
+    c = dim3.Context(0)
+    try:
+        c.set_option(dim3.OPT_MID_ROW_MAX, 0)
+        c.set_option(dim3.OPT_MID_ROW_MAX, -1)
+    finally:
+        c.close()
