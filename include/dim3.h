@@ -143,12 +143,9 @@ typedef enum {
                                    than 393,216 z and of Join-Count's packed counters; 0 (default): the
                                    fewest tiles of at most 12,288 (bitmap) / 7,168 (counters) words */
     DIM3_OPT_DENSE_TILE_N = 11, /* tensor-core DenseEC: dense z per CTA tile, 128 or 256; 0 (default): 256 */
-    DIM3_OPT_EMIT_PIPELINE = 12,/* single-pass emission with two x rows per CTA: 1 = persistent CTAs that
+    DIM3_OPT_EMIT_PIPELINE = 12 /* single-pass emission with two x rows per CTA: 1 = persistent CTAs that
                                    build the next row group while the previous one's offset resolves;
                                    0 (default) = one group per CTA */
-    DIM3_OPT_MID_ROW_MAX = 13   /* on z ranges where light rows apply: x rows with more join tuples than a
-                                   light row but at most this many (<= 8192) deduplicate by buckets of
-                                   4,096 z instead of the |Z|-bit SPA; <0: 8192 (default), 0: none */
 } dim3_option;
 
 /* Phases timed under DIM3_OPT_TIMING. */

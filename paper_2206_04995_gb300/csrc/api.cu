@@ -202,7 +202,6 @@ int dim3_ctx_set_option(dim3_ctx* ctx, int option, int64_t value) {
             case DIM3_OPT_LIGHT_ROW_MAX: ctx->c.opt.light_row_max = value; break;
             case DIM3_OPT_TIMING: ctx->stats.on = value != 0; break;
             case DIM3_OPT_TWO_PASS: ctx->c.opt.two_pass = value; break;
-            case DIM3_OPT_MID_ROW_MAX: ctx->c.opt.mid_row_max = value; break;
             case DIM3_OPT_EMIT_PIPELINE:
                 DIM3_REQUIRE(value == 0 || value == 1, DIM3_ERR_ARG, "emit pipeline must be 0 or 1");
                 ctx->c.opt.emit_pipe = value;

@@ -87,8 +87,6 @@ struct Options {
     int64_t tile_words = 0;     // z-tiled rows: bitmap words per tile (0: automatic)
     int64_t dense_tile_n = 0;   // tensor-core DenseEC: dense z per CTA tile (128 or 256; 0: 256)
     int64_t emit_pipe = 0;      // single pass, two rows per CTA: persistent pipelined kernel (1) or not (0)
-    int64_t mid_row_max = -1;   // x rows with at most this many join tuples (above the light ones) use bucketed
-                                // bitmaps on wide z ranges; <0: default, 0: none
     // f1 constants (Section 2.6), seconds: t_map per input row, t_randRW per
     // join tuple of the hybrid path, t_hash per join tuple of the classical path
     double f1c[3] = {kF1TMap, kF1TRand, kF1THash};
@@ -157,10 +155,8 @@ struct Plan {
     DevBuf cache_dbits; // dense bits of the cached range
     DevBuf cache_dcnt;  // dense counts of the cached range
     // z-tiled single instance: the cached range's (row, tile) units
-    DevBuf cache_units;     // int32 [cache_n_list]: rows run per tile (null: every row)
-    DevBuf cache_tcnt;      // int32 [cache_n_list * cache_tiles]: pairs per unit
+    DevBuf cache_units;     // int32 [cache_n_list]: rows run over the z tiles (null: every row)
     int64_t cache_n_list = 0, cache_tile_bits = 0;
-    int cache_tiles = 0;
     int64_t max_mx = -1;  // largest |R[x]| (the bound of a pair's count), -1 until computed
 };
 

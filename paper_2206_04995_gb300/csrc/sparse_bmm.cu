@@ -74,12 +74,10 @@ struct XRowArgs {
     int32_t* out_z;
     int32_t* out_c;
     int vec_ok;
-    // z-tiled single instance (k_tile_rows): units = (listed row, z tile)
+    // z-tiled single instance (k_tiled_rows): one CTA per listed row, n_tiles z tiles each
     const int32_t* unit_rows;  // row numbers (x - x_begin) of the rows to run, or null (rows 0 .. n_list-1)
     int64_t n_list;            // rows in the list
     int n_tiles;               // z tiles per row
-    int32_t* tcnt;             // counting pass out: pairs of every unit [n_list * n_tiles]
-    const int32_t* tcnt_in;    // emitting pass: the counting pass's unit pairs
     // k_xrow_emit_g over a batch: groups of up to G rows of one instance,
     // (first row, rows) each; null = consecutive groups of G rows
     const int2* groups;
@@ -198,24 +196,42 @@ __device__ __forceinline__ int64_t popc_words(const uint32_t* bm, int n) {
 }
 
 // flush_warp for a stage of z ids: dst[t] = dict_z[st[t]] for t in [sh, sh + cnt).
+// Two 16-byte pieces per lane and round: their eight gathers are issued
+// before either store, so a round costs one dictionary latency.
 __device__ __forceinline__ void flush_warp_ids(int32_t* dst, const int32_t* st, int sh, int cnt,
                                                const int32_t* __restrict__ dict_z, bool vec_ok) {
     const int end = sh + cnt;
     const int nv = (end + 3) >> 2;
     const int lane = threadIdx.x & 31;
+    if (vec_ok) {
+        // whole pieces [v0, v1): v0 = first piece at or after sh, v1 = last full piece
+        const int v0 = (sh + 3) >> 2, v1 = end >> 2;
+        for (int v = v0 + lane; v < v1; v += 64) {
+            const bool two = v + 32 < v1;
+            const int4 ia = *reinterpret_cast<const int4*>(st + 4 * v);
+            const int4 ib = two ? *reinterpret_cast<const int4*>(st + 4 * (v + 32)) : ia;
+            const int4 a = make_int4(__ldg(dict_z + ia.x), __ldg(dict_z + ia.y), __ldg(dict_z + ia.z),
+                                     __ldg(dict_z + ia.w));
+            const int4 b = make_int4(__ldg(dict_z + ib.x), __ldg(dict_z + ib.y), __ldg(dict_z + ib.z),
+                                     __ldg(dict_z + ib.w));
+            __stcs(reinterpret_cast<int4*>(dst + 4 * v), a);
+            if (two) __stcs(reinterpret_cast<int4*>(dst + 4 * (v + 32)), b);
+        }
+        // the partial pieces at both ends (at most three entries each)
+        if (lane < 8) {
+            const int t = lane < 4 ? sh + lane : 4 * v1 + (lane - 4);
+            const bool head = lane < 4 && t < min(end, 4 * v0);
+            const bool tail = lane >= 4 && t < end && v1 >= v0;
+            if (head || tail) __stcs(dst + t, __ldg(dict_z + st[t]));
+        }
+        return;
+    }
     for (int v = lane; v < nv; v += 32) {
         const int s = v << 2;
-        if (vec_ok && s >= sh && s + 4 <= end) {
-            const int4 id = *reinterpret_cast<const int4*>(st + s);
-            const int4 val = make_int4(__ldg(dict_z + id.x), __ldg(dict_z + id.y), __ldg(dict_z + id.z),
-                                       __ldg(dict_z + id.w));
-            __stcs(reinterpret_cast<int4*>(dst + s), val);
-        } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int t = s + j;
-                if (t >= sh && t < end) __stcs(dst + t, __ldg(dict_z + st[t]));
-            }
+        for (int j = 0; j < 4; ++j) {
+            const int t = s + j;
+            if (t >= sh && t < end) __stcs(dst + t, __ldg(dict_z + st[t]));
         }
     }
 }
@@ -284,15 +300,18 @@ __device__ __forceinline__ void compact_run(const XRowArgs& a, const uint32_t* b
                 sh = (int)(wpos & 3);
                 sc = 0;
             }
+            // one step per set bit of the lane's four words (the warp takes
+            // as many steps as its fullest lane)
             int pos = sh + sc + incl4 - c4;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t v = wv[k];
-                while (v) {
-                    const int b = __ffs(v) - 1;
-                    v &= v - 1;
-                    st[pos++] = (int32_t)(zt0 + ((int64_t)(wl + k) << 5) + b);
+            int k = 0;
+            uint32_t v = wv[0];
+            for (int i = 0; i < c4; ++i) {
+                while (v == 0u) {
+                    ++k;
+                    v = k == 1 ? wv[1] : k == 2 ? wv[2] : wv[3];
                 }
+                st[pos++] = (int32_t)(zt0 + ((int64_t)(wl + k) << 5) + __ffs(v) - 1);
+                v &= v - 1;
             }
             sc += total_c;
             continue;
@@ -1150,18 +1169,20 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
 
 // ------------------------------------------------------------- tiled rows
 // A single instance whose z range spans several shared-memory tiles: one CTA
-// per (x row, z tile) unit, so the tiles of a row run side by side and every
-// CTA holds one tile's SPA bitmap. The bitmap is built from the row's join
-// tuples that fall in the tile: the tile boundaries of every S_sparse row are
-// precomputed (tile_ptr), so each R entry y of the row names one segment of
-// S_sparse[y]. Segments of at least 32 tuples (in power-law graphs nearly all
-// join tuples lie in them: the neighbours of a vertex are biased towards
-// hubs) are cut into pieces of up to 256 tuples, and the warps take the pieces
-// in turn, each lane loading every 32nd tuple of a piece (coalesced, eight
-// independent loads in flight). Shorter segments are walked by the thread that
-// read their entry. The counting pass stores each unit's pairs; the emitting
-// pass writes unit (x, t) after the units (x, t' < t) of its row and after all
-// earlier rows.
+// per x row sweeps the row's z tiles, holding one tile's SPA bitmap at a
+// time. The bitmap is built from the row's join tuples that fall in the tile:
+// the tile boundaries of every S_sparse row are precomputed (tile_ptr), so
+// each R entry y of the row names one segment of S_sparse[y]. Segments of at
+// least 32 tuples (in power-law graphs nearly all join tuples lie in them:
+// the neighbours of a vertex are biased towards hubs) are cut into pieces of
+// up to 256 tuples, and the warps take the pieces in turn, each lane loading
+// every 32nd tuple of a piece (coalesced, eight independent loads in flight).
+// Shorter segments are walked by the thread that read their entry. (Laying
+// all segments end to end and giving every thread eight consecutive tuples
+// balances the threads but makes the loads uncoalesced: measured slower on
+// both the power-law graph and Zipf tables.) The counting pass stores each
+// row's pairs; the emitting pass writes them at the row's offset, tile after
+// tile.
 constexpr int kTileChunk = 2 * kThreads;  // R entries of a row per round (two per thread)
 constexpr int kPiece = 256;               // tuples per warp work item
 constexpr int kLongSeg = 32;              // segments from this length on go to the warps
@@ -1258,88 +1279,195 @@ __device__ __forceinline__ void visit_chunk(const XRowArgs& a, int64_t c0, int n
     }
 }
 
+// Set bits of a 16-byte bitmap word.
+__device__ __forceinline__ int popc4(const uint4 v) {
+    return __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+}
+
+// Block-wide flush of a stage of z ids: dst[t] = dict_z[st[t]] for t in
+// [sh, sh + cnt), with 16-byte stores where dst + 0 is 16-byte aligned.
+__device__ __forceinline__ void flush_block_ids(int32_t* dst, const int32_t* st, int sh, int cnt,
+                                                const int32_t* __restrict__ dict_z, bool vec_ok) {
+    const int end = sh + cnt;
+    const int nv = (end + 3) >> 2;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        const int s = v << 2;
+        if (vec_ok && s >= sh && s + 4 <= end) {
+            const int4 id = *reinterpret_cast<const int4*>(st + s);
+            const int4 val = make_int4(__ldg(dict_z + id.x), __ldg(dict_z + id.y), __ldg(dict_z + id.z),
+                                       __ldg(dict_z + id.w));
+            __stcs(reinterpret_cast<int4*>(dst + s), val);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int t = s + j;
+                if (t >= sh && t < end) __stcs(dst + t, __ldg(dict_z + st[t]));
+            }
+        }
+    }
+}
+
+// 16-byte bitmap words per thread in the scan of a tile of tw4 of them: a
+// contiguous run each, of odd length, so that the eight threads of one
+// 128-byte phase of a 16-byte shared load start in distinct bank groups.
+__device__ __forceinline__ int wide_run(int tw4) { return ((tw4 + kThreads - 1) / kThreads) | 1; }
+
+// One CTA per x row, sweeping the row's z tiles in order with one tile's SPA
+// bitmap (the tiles' pairs are consecutive in the output, so x is filled
+// once and the offset runs on from tile to tile). Each tile's bitmap is built
+// from the row's join tuples in that tile (visit_chunk over the tile starts
+// of the S_sparse rows, wide S rows OR-ed in word by word, DenseEC bits).
+// Then every thread takes a contiguous run of 16-byte bitmap words, counts
+// its set bits, and one block scan places them: the counting pass only adds
+// and zeroes; the emitting pass, when the tile's pairs fit the stage, writes
+// the z ids of its bits into the stage in z order while zeroing its words
+// (the next tile starts clean), and the block flushes the stage as z values
+// with 16-byte stores. A denser tile is compacted warp run by warp run
+// (compact_run) and cleared afterwards. The scan costs a few instructions
+// per 128 z, whichever bits are set.
 template <bool kEmit>
-__global__ void __launch_bounds__(kThreads) k_tile_rows(const XRowArgs a) {
+__global__ void __launch_bounds__(kThreads) k_tiled_rows(const XRowArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
-    int32_t* stage = reinterpret_cast<int32_t*>(smem);           // emit: kWarps x a.stage_ints
-    uint32_t* bm = smem + (kEmit ? kWarps * a.stage_ints : 0);  // tile words
+    const int stage_cap = kEmit ? kWarps * a.stage_ints : 0;
+    int32_t* stage = reinterpret_cast<int32_t*>(smem);
+    uint32_t* bm = smem + stage_cap;
+    uint4* b4 = reinterpret_cast<uint4*>(bm);
     __shared__ ChunkSmem cs;
     __shared__ int32_t s_wide[kTileChunk];   // bitmap rows of the chunk's wide S rows
-    __shared__ int32_t s_wc[kWarps];
     __shared__ int64_t s_scan[kWarps + 1];
+    __shared__ int s_sc[kWarps + 1];
     __shared__ int s_nwide[2];  // wide rows of the current chunk; the two alternate between chunks
 
-    const int64_t unit = blockIdx.x;
-    const int T = a.n_tiles;
-    const int64_t li = unit / T;
-    const int t = (int)(unit - li * T);
+    const int64_t li = blockIdx.x;
     if (li >= a.n_list) return;
     const int64_t xr = a.unit_rows ? (int64_t)a.unit_rows[li] : li;
     const int64_t x = a.x_begin + xr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t zt0 = (int64_t)t * a.tile_bits, zt1 = min64(zt0 + a.tile_bits, a.n_z);
-    const int tw = (int)((zt1 - zt0 + 31) >> 5);
-    if (kEmit && a.tcnt_in[unit] == 0) return;  // nothing of this row in this tile
+    int64_t o = 0;
+    if (kEmit) {
+        o = a.off[xr];
+        const int64_t o_end = a.off[xr + 1];
+        if (o_end == o) return;
+        fill_range(a.out_x, o, o_end, a.dict_x[x], a.vec_ok);
+    }
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
-    clear_words(bm, tw);
+    clear_words(bm, (int)(((a.tile_bits + 127) >> 7) << 2));
     if (tid == 0) s_nwide[0] = 0;
     __syncthreads();
-    for (int64_t c0 = r0, ck = 0; c0 < r1; c0 += kTileChunk, ++ck) {
-        const int nc = (int)min64(kTileChunk, r1 - c0);
-        int* nwide = &s_nwide[ck & 1];
-        if (tid == 0) s_nwide[(ck + 1) & 1] = 0;  // the next chunk's counter (the previous chunk's is done)
-        visit_chunk(a, c0, nc, t, cs, s_wide, nwide, [&](int32_t zid) {
-            const int z = (int)(zid - zt0);
-            atomicOr(&bm[z >> 5], 1u << (z & 31));
-        });
-        // wide S rows of the chunk: OR their bitmap words over the tile
-        const int nw = *nwide;
-        if (nw > 0) {
-            const uint32_t* bits = a.ss_bits + (zt0 >> 5);
-            for (int w = tid; w < tw; w += kThreads) {
-                uint32_t acc = 0u;
-                for (int i = 0; i < nw; ++i) acc |= __ldg(bits + a.bm_off[s_wide[i]] + w);
-                if (acc) atomicOr(&bm[w], acc);
+    int64_t total = 0;
+    // Every tile starts with a clean bitmap and s_nwide[0] = 0: both are
+    // restored before the last block barrier of the previous tile.
+    for (int t = 0; t < a.n_tiles; ++t) {
+        const int64_t zt0 = (int64_t)t * a.tile_bits, zt1 = min64(zt0 + a.tile_bits, a.n_z);
+        const int tw = (int)((zt1 - zt0 + 31) >> 5), tw4 = (tw + 3) >> 2;
+        for (int64_t c0 = r0, ck = 0; c0 < r1; c0 += kTileChunk, ++ck) {
+            const int nc = (int)min64(kTileChunk, r1 - c0);
+            int* nwide = &s_nwide[ck & 1];
+            if (tid == 0) s_nwide[(ck + 1) & 1] = 0;  // the next chunk's counter (the previous chunk's is done)
+            visit_chunk(a, c0, nc, t, cs, s_wide, nwide, [&](int32_t zid) {
+                const int z = (int)(zid - zt0);
+                atomicOr(&bm[z >> 5], 1u << (z & 31));
+            });
+            // wide S rows of the chunk: OR their bitmap words over the tile
+            const int nw = *nwide;
+            if (nw > 0) {
+                const uint32_t* bits = a.ss_bits + (zt0 >> 5);
+                for (int w = tid; w < tw; w += kThreads) {
+                    uint32_t acc = 0u;
+                    for (int i = 0; i < nw; ++i) acc |= __ldg(bits + a.bm_off[s_wide[i]] + w);
+                    if (acc) atomicOr(&bm[w], acc);
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
-    }
-    if (a.n_zd > 0) {
-        // DenseEC result of x over the dense index (see k_xrow_bits)
-        const uint32_t* drow = a.d_bits + xr * a.zdw;
-        for (int64_t d = tid; d < a.n_zd; d += kThreads) {
-            if ((drow[d >> 5] >> (d & 31)) & 1u) {
-                int32_t z = a.zd_list[d];
-                if (z >= zt0 && z < zt1) {
-                    z -= (int32_t)zt0;
-                    atomicOr(&bm[z >> 5], 1u << (z & 31));
+        if (a.n_zd > 0) {
+            // DenseEC result of x over the dense index (see k_xrow_bits)
+            const uint32_t* drow = a.d_bits + xr * a.zdw;
+            for (int64_t d = tid; d < a.n_zd; d += kThreads) {
+                if ((drow[d >> 5] >> (d & 31)) & 1u) {
+                    int32_t z = a.zd_list[d];
+                    if (z >= zt0 && z < zt1) {
+                        z -= (int32_t)zt0;
+                        atomicOr(&bm[z >> 5], 1u << (z & 31));
+                    }
                 }
             }
         }
+        __syncthreads();
+        if (tid == 0) s_nwide[0] = 0;  // the build is done with it; the next barrier publishes it
+        const int q = wide_run(tw4);
+        const int u0 = min(tid * q, tw4), u1 = min(u0 + q, tw4);
+        int c = 0;
+        uint64_t nz = 0;  // emitting pass: the nonzero words of this thread's run (at most 52)
+        for (int u = u0; u < u1; ++u) {
+            const uint4 v = b4[u];
+            c += popc4(v);
+            if (kEmit) {
+                const uint32_t m = (uint32_t)(v.x != 0u) | ((uint32_t)(v.y != 0u) << 1) |
+                                   ((uint32_t)(v.z != 0u) << 2) | ((uint32_t)(v.w != 0u) << 3);
+                nz |= (uint64_t)m << (4 * (u - u0));
+            } else {
+                b4[u] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        if (!kEmit) {
+            total += block_sum<int64_t, kThreads>((int64_t)c, s_scan);
+            continue;
+        }
+        // warp w's pairs follow warps 0 .. w-1 of the tile
+        const int incl = warp_inclusive_scan(c);
+        if (lane == 31) s_sc[warp] = incl;
+        __syncthreads();
+        int base = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const int n = s_sc[w];
+            base += w < warp ? n : 0;
+            tot += n;
+        }
+        if (tot == 0) continue;  // nothing set: the bitmap is clean
+        const int64_t wpos = o + base;
+        const int mine = __shfl_sync(kFull, incl, 31);
+        const int sh = (int)(wpos & 3);
+        int32_t* st = stage + warp * a.stage_ints;
+        const bool lane_runs = sh + mine <= a.stage_ints;
+        if (lane_runs) {
+            // every lane writes the z ids of its run's bits in one flat loop
+            // of c steps (one per set bit; a nonzero word is read and zeroed
+            // when the previous one runs out), so the warp takes as many
+            // steps as its fullest lane, not one per word
+            int pos = sh + incl - c;
+            __syncwarp();  // the warp's previous flush has read the stage
+            uint32_t cur = 0u;
+            int32_t zb = 0;
+            for (int i = 0; i < c; ++i) {
+                if (cur == 0u) {
+                    const int w = 4 * u0 + __ffsll((long long)nz) - 1;
+                    nz &= nz - 1;
+                    cur = bm[w];
+                    bm[w] = 0u;
+                    zb = (int32_t)(zt0 + ((int64_t)w << 5));
+                }
+                st[pos++] = zb + __ffs(cur) - 1;
+                cur &= cur - 1;
+            }
+        } else if (mine > 0) {
+            // a dense run: group by group (compact_run), then zeroed
+            const int groups = (tw + 31) >> 5;
+            const int g0 = min(groups, warp * 4 * q), g1 = min(groups, (warp + 1) * 4 * q);
+            compact_run(a, bm, tw, g0, g1, mine, zt0, wpos, st);
+            for (int u = u0; u < u1; ++u) b4[u] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        // every word is zero again before any warp builds the next tile; the
+        // staged ids are flushed while the other warps go on building
+        __syncthreads();
+        if (lane_runs && mine > 0) {
+            __syncwarp();
+            flush_warp_ids(a.out_z + (wpos - sh), st, sh, mine, a.dict_z, a.vec_ok);
+        }
+        o += tot;
     }
-    __syncthreads();
-    if (!kEmit) {
-        const int64_t c = block_sum<int64_t, kThreads>(popc_words(bm, tw), s_scan);
-        if (tid == 0) a.tcnt[unit] = (int32_t)c;
-        return;
-    }
-    int64_t o = a.off[xr];
-    for (int u = 0; u < t; ++u) o += a.tcnt_in[li * T + u];
-    fill_range(a.out_x, o, o + a.tcnt_in[unit], a.dict_x[x], a.vec_ok);
-    const int groups = (tw + 31) >> 5;
-    const int gpw = (groups + kWarps - 1) / kWarps;
-    const int g0 = warp * gpw, g1 = min(groups, g0 + gpw);
-    int mine = 0;
-    for (int g = g0; g < g1; ++g) {
-        const int w = (g << 5) + lane;
-        mine += w < tw ? __popc(bm[w]) : 0;
-    }
-    mine = warp_sum(mine);
-    if (lane == 0) s_wc[warp] = mine;
-    __syncthreads();
-    int64_t wpos = o;
-    for (int w = 0; w < warp; ++w) wpos += s_wc[w];
-    compact_run(a, bm, tw, g0, g1, mine, zt0, wpos, stage + warp * a.stage_ints);
+    if (!kEmit && tid == 0) a.cnt[xr] = total;
 }
 
 // ------------------------------------------------- Join-Count, packed
@@ -1486,16 +1614,6 @@ __global__ void k_max_row(const int64_t* __restrict__ rowptr, int64_t n, unsigne
     }
 }
 
-// cnt[row] = pairs of the row's units, for the listed rows
-__global__ void k_tile_sum(const int32_t* __restrict__ tcnt, const int32_t* __restrict__ rows, int64_t n_list, int T,
-                           int64_t* cnt) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_list; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t c = 0;
-        for (int t = 0; t < T; ++t) c += tcnt[i * T + t];
-        cnt[rows ? rows[i] : i] = c;
-    }
-}
-
 // ----------------------------------------------------------------- host side
 static size_t bits_smem(int64_t tile_bits, bool emit, int stage_ints) {
     return (emit ? (size_t)kWarps * stage_ints * 4 : 0) + (size_t)(tile_bits / 32) * 4;
@@ -1513,20 +1631,20 @@ static void setup_attrs(const Ctx& ctx) {
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
-    DIM3_CUDA(cudaFuncSetAttribute(k_tile_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
-    DIM3_CUDA(cudaFuncSetAttribute(k_tile_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_tiled_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_tiled_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     done[d] = true;
 }
 
 // Project rows of a single instance whose z range needs several bitmap tiles
-// (of at most kMaxTileWords words, or of the option's size) run as (row,
-// tile) units (k_tile_rows).
+// (of at most kMaxTileWords words, or of the option's size) run one CTA per
+// row over the tiles (k_tiled_rows).
 static bool use_tiles(const Ctx& ctx, const Plan& p, int kind) {
     const int64_t lim = ctx.opt.tile_words > 0 ? std::min<int64_t>(ctx.opt.tile_words, kMaxTileWords) : kMaxTileWords;
     return kind == 0 && p.n_inst == 1 && p.zw > lim;
 }
 
-// Bitmap words per tile of k_tile_rows: the option if set, else the fewest
+// Bitmap words per tile of k_tiled_rows: the option if set, else the fewest
 // tiles of at most kMaxTileWords words, of equal size (a multiple of 32 words).
 static int64_t tile_words_for(const Ctx& ctx, const Plan& p) {
     if (ctx.opt.tile_words > 0) return std::min<int64_t>(ctx.opt.tile_words, kMaxTileWords);
@@ -1695,8 +1813,6 @@ struct LightArgs {
     const int64_t* off;   // emitting pass: row offsets
     int32_t* out_x;
     int32_t* out_z;
-    int64_t n_z;          // medium rows: the z range (bucket count)
-    int vec_ok;           // medium rows: out_x 16-byte aligned at 16-byte offsets
 };
 
 template <bool kEmit>
@@ -1775,169 +1891,10 @@ __global__ void __launch_bounds__(kThreads) k_light_rows(const LightArgs a) {
     }
 }
 
-// ------------------------------------------------------------- medium rows
-// An x with more join tuples than a light row but at most kMidMax, on a wide
-// z range: its SPA would be a |Z|-bit bitmap (several shared-memory tiles)
-// scanned word by word to extract a few thousand pairs. One CTA instead
-// gathers the row's join tuples' z ids into shared memory, distributes them to
-// buckets of 4,096 consecutive z ids (a counting sort on the high bits), and
-// deduplicates each bucket with a 128-word bitmap owned by one warp, whose set
-// bits come out in z order. The cost follows the row's tuples and its z
-// range's bucket count, not |Z| bits.
-constexpr int kMidMax = 8192;            // join tuples of a medium row at most
-constexpr int kMidBucketBits = 12;       // 4,096 z per bucket
-constexpr int kMidMaxBuckets = 1024;     // z ranges up to 4,194,304
-constexpr size_t kMidSmem = (size_t)kWarps * 128 * 4 + (size_t)kMidMax * 4 + (size_t)kMidMax * 2 +
-                            (size_t)(3 * kMidMaxBuckets + 1) * 4;
-
-template <bool kEmit>
-__global__ void __launch_bounds__(kThreads) k_mid_rows(const LightArgs a) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t* wbm = smem;                                                        // [kWarps][128] bucket bitmaps
-    int32_t* zs = reinterpret_cast<int32_t*>(wbm + kWarps * 128);                // [kMidMax] z ids
-    uint16_t* low = reinterpret_cast<uint16_t*>(zs + kMidMax);                   // [kMidMax] low bits, by bucket
-    int32_t* hist = reinterpret_cast<int32_t*>(low + kMidMax);                   // [buckets] items, then distinct
-    int32_t* bstart = hist + kMidMaxBuckets;                                     // [buckets + 1]
-    int32_t* cursor = bstart + kMidMaxBuckets + 1;                               // [buckets]
-    __shared__ int32_t s_len[kTileChunk], s_off[kTileChunk];
-    __shared__ uint32_t s_s0[kTileChunk];
-    __shared__ int32_t s_sc[kWarps + 1];
-    __shared__ int64_t s_scan[kWarps + 1];
-
-    const int64_t xr = a.rows[blockIdx.x], x = a.x_begin + xr;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
-    // 1. the row's join tuples' z ids, entry after entry
-    int n = 0;
-    for (int64_t c0 = r0; c0 < r1; c0 += kTileChunk) {
-        const int nc = (int)min64(kTileChunk, r1 - c0);
-        int len[2];
-        uint32_t first[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int i = 2 * tid + k;
-            len[k] = 0;
-            first[k] = 0u;
-            if (i < nc) {
-                const int32_t y = a.r_col[c0 + i];
-                const int64_t s0 = a.ss_rowptr[y];
-                len[k] = (int)(a.ss_rowptr[y + 1] - s0);
-                first[k] = (uint32_t)s0;
-            }
-        }
-        int tot;
-        const int ex = block_exclusive_scan<int, kThreads>(len[0] + len[1], &tot, s_sc);
-        s_len[2 * tid] = len[0];
-        s_len[2 * tid + 1] = len[1];
-        s_off[2 * tid] = n + ex;
-        s_off[2 * tid + 1] = n + ex + len[0];
-        s_s0[2 * tid] = first[0];
-        s_s0[2 * tid + 1] = first[1];
-        __syncthreads();
-        for (int i = warp; i < nc; i += kWarps) {
-            const int l = s_len[i], o = s_off[i];
-            const int32_t* src = a.ss_col + s_s0[i];
-            for (int q = lane; q < l; q += 32)
-                if (o + q < kMidMax) zs[o + q] = __ldg(src + q);
-        }
-        n += tot;
-        __syncthreads();
-    }
-    n = min(n, kMidMax);
-    // 2. counting sort of the ids on their bucket (high bits); only the low
-    // bits are kept, by bucket
-    const int nb = (int)((a.n_z + (1 << kMidBucketBits) - 1) >> kMidBucketBits);
-    for (int b = tid; b < nb; b += kThreads) hist[b] = 0;
-    __syncthreads();
-    for (int i = tid; i < n; i += kThreads) atomicAdd(&hist[zs[i] >> kMidBucketBits], 1);
-    __syncthreads();
-    int carry = 0;
-    for (int b0 = 0; b0 < nb; b0 += kThreads) {
-        const int b = b0 + tid;
-        const int v = b < nb ? hist[b] : 0;
-        int tot;
-        const int ex = block_exclusive_scan<int, kThreads>(v, &tot, s_sc);
-        if (b < nb) bstart[b] = cursor[b] = carry + ex;
-        carry += tot;
-    }
-    if (tid == 0) bstart[nb] = n;
-    __syncthreads();
-    for (int i = tid; i < n; i += kThreads) {
-        const int32_t z = zs[i];
-        const int p = atomicAdd(&cursor[z >> kMidBucketBits], 1);
-        low[p] = (uint16_t)(z & ((1 << kMidBucketBits) - 1));
-    }
-    __syncthreads();
-    // 3. every bucket through one warp's 128-word bitmap; its distinct ids go
-    // back to zs at the bucket's start, ascending, and their number to hist
-    uint32_t* mb = wbm + warp * 128;
-    for (int b = warp; b < nb; b += kWarps) {
-        const int i0 = bstart[b], i1 = bstart[b + 1];
-        if (i1 == i0) {
-            if (lane == 0) hist[b] = 0;
-            continue;
-        }
-        *reinterpret_cast<uint4*>(mb + 4 * lane) = make_uint4(0u, 0u, 0u, 0u);
-        __syncwarp();
-        for (int i = i0 + lane; i < i1; i += 32) {
-            const int l = low[i];
-            atomicOr(&mb[l >> 5], 1u << (l & 31));
-        }
-        __syncwarp();
-        const uint4 q = *reinterpret_cast<const uint4*>(mb + 4 * lane);
-        const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
-        const int c = __popc(q.x) + __popc(q.y) + __popc(q.z) + __popc(q.w);
-        const int incl = warp_inclusive_scan(c);
-        int pos = i0 + incl - c;
-        const int32_t zb = b << kMidBucketBits;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t v = wv[k];
-            while (v) {
-                const int bit = __ffs(v) - 1;
-                v &= v - 1;
-                zs[pos++] = zb + ((4 * lane + k) << 5) + bit;
-            }
-        }
-        if (lane == 31) hist[b] = incl;
-        __syncwarp();
-    }
-    __syncthreads();
-    if (!kEmit) {
-        int64_t c = 0;
-        for (int b = tid; b < nb; b += kThreads) c += hist[b];
-        c = block_sum<int64_t, kThreads>(c, s_scan);
-        if (tid == 0) a.cnt[xr] = c;
-        return;
-    }
-    // 4. each bucket's distinct z values at its place in the row's output
-    const int64_t o = a.off[xr];
-    fill_range(a.out_x, o, a.off[xr + 1], a.dict_x[x], a.vec_ok);
-    carry = 0;
-    for (int b0 = 0; b0 < nb; b0 += kThreads) {
-        const int b = b0 + tid;
-        const int v = b < nb ? hist[b] : 0;
-        int tot;
-        const int ex = block_exclusive_scan<int, kThreads>(v, &tot, s_sc);
-        if (b < nb) cursor[b] = carry + ex;
-        carry += tot;
-    }
-    __syncthreads();
-    for (int b = warp; b < nb; b += kWarps) {
-        const int d = hist[b], src = bstart[b];
-        const int64_t dst = o + cursor[b];
-        for (int i = lane; i < d; i += 32) a.out_z[dst + i] = __ldg(a.dict_z + zs[src + i]);
-    }
-}
-
-// Row classes: 1 light (at most lim join tuples), 2 medium (at most mid_lim),
-// 0 the rest (bitmap rows).
-__global__ void k_light_flags(const int64_t* __restrict__ outj_x, int64_t n_x, int64_t lim, int64_t mid_lim,
-                              uint8_t* light) {
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n_x; x += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = outj_x[x];
-        light[x] = j <= lim ? 1 : j <= mid_lim ? 2 : 0;
-    }
+// Row classes: 1 light (at most lim join tuples), 0 the rest (bitmap rows).
+__global__ void k_light_flags(const int64_t* __restrict__ outj_x, int64_t n_x, int64_t lim, uint8_t* light) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n_x; x += (int64_t)gridDim.x * blockDim.x)
+        light[x] = outj_x[x] <= lim ? 1 : 0;
 }
 
 __global__ void k_light_range(const uint8_t* __restrict__ light, int64_t x_begin, int64_t rows, int want,
@@ -1976,10 +1933,7 @@ static const uint8_t* ensure_light(const Ctx& ctx, Plan& p, cudaStream_t s) {
         const int64_t lim = ctx.opt.light_row_max < 0 ? kLightMax : std::min<int64_t>(ctx.opt.light_row_max, kLightMax);
         if (lim > 0 && p.n_inst == 1 && p.n_zd_total == 0 && p.info.n_z >= kLightMinZ && p.info.n_x > 0) {
             p.light.alloc((size_t)p.info.n_x, s);
-            // medium rows need a bucket count within kMidMaxBuckets
-            int64_t mid = ctx.opt.mid_row_max < 0 ? kMidMax : std::min<int64_t>(ctx.opt.mid_row_max, kMidMax);
-            if (p.info.n_z > ((int64_t)kMidMaxBuckets << kMidBucketBits) || mid < lim) mid = lim;
-            k_light_flags<<<blocks_for(p.info.n_x), kThreads, 0, s>>>(p.outj_x.as<int64_t>(), p.info.n_x, lim, mid,
+            k_light_flags<<<blocks_for(p.info.n_x), kThreads, 0, s>>>(p.outj_x.as<int64_t>(), p.info.n_x, lim,
                                                                      p.light.as<uint8_t>());
             DIM3_LAUNCHED();
             DevBuf tot;
@@ -2015,9 +1969,8 @@ static int64_t list_rows(const uint8_t* light, int64_t x_begin, int64_t rows, in
     return n;
 }
 
-// the light rows of [x_begin, x_begin + rows): counting (cnt) or emitting (off)
-// The light rows (warp sorts) and the medium rows (bucketed bitmaps) of
-// [x_begin, x_begin + rows): counting (cnt) or emitting (off).
+// The light rows (warp sorts) of [x_begin, x_begin + rows): counting (cnt)
+// or emitting (off).
 static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* cnt, const int64_t* off,
                          int32_t* out_x, int32_t* out_z, cudaStream_t s) {
     LightArgs la{};
@@ -2032,8 +1985,6 @@ static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* 
     la.off = off;
     la.out_x = out_x;
     la.out_z = out_z;
-    la.n_z = p.info.n_z;
-    la.vec_ok = (reinterpret_cast<uintptr_t>(out_x) & 15u) == 0;
     DevBuf list;
     const int64_t n = list_rows(p.light.as<uint8_t>(), x_begin, rows, 1, list, s);
     if (n > 0) {
@@ -2042,24 +1993,6 @@ static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* 
         const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kWarps), 152 * 8));
         if (off) k_light_rows<true><<<g, kThreads, 0, s>>>(la);
         else k_light_rows<false><<<g, kThreads, 0, s>>>(la);
-        DIM3_LAUNCHED();
-    }
-    DevBuf mlist;
-    const int64_t m = list_rows(p.light.as<uint8_t>(), x_begin, rows, 2, mlist, s);
-    if (m > 0) {
-        DIM3_REQUIRE(m < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long");
-        static bool done[64] = {false};
-        int dev = 0;
-        DIM3_CUDA(cudaGetDevice(&dev));
-        if (!done[dev & 63]) {
-            DIM3_CUDA(cudaFuncSetAttribute(k_mid_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmem));
-            DIM3_CUDA(cudaFuncSetAttribute(k_mid_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmem));
-            done[dev & 63] = true;
-        }
-        la.rows = mlist.as<int32_t>();
-        la.n = m;
-        if (off) k_mid_rows<true><<<(unsigned)m, kThreads, kMidSmem, s>>>(la);
-        else k_mid_rows<false><<<(unsigned)m, kThreads, kMidSmem, s>>>(la);
         DIM3_LAUNCHED();
     }
 }
@@ -2187,20 +2120,19 @@ static void launch_cnt(const Ctx& ctx, const XRowArgs& a, int cb, bool emit, cud
     DIM3_LAUNCHED();
 }
 
-// One (row, tile) unit per CTA: counting (a.tcnt) or emitting (a.tcnt_in).
-static void launch_tiles(const Ctx& ctx, const XRowArgs& a, bool emit, cudaStream_t s) {
-    const int64_t units = a.n_list * a.n_tiles;
-    if (units <= 0) return;
-    DIM3_REQUIRE(units < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long for its z tiles");
+// One CTA per listed row over its z tiles: counting (a.cnt) or emitting (a.off).
+static void launch_wide(const Ctx& ctx, const XRowArgs& a, bool emit, cudaStream_t s) {
+    if (a.n_list <= 0) return;
+    DIM3_REQUIRE(a.n_list < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long");
     setup_attrs(ctx);
     PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
     const size_t sm = bits_smem(a.tile_bits, emit, a.stage_ints);
-    if (emit) k_tile_rows<true><<<(unsigned)units, kThreads, sm, s>>>(a);
-    else k_tile_rows<false><<<(unsigned)units, kThreads, sm, s>>>(a);
+    if (emit) k_tiled_rows<true><<<(unsigned)a.n_list, kThreads, sm, s>>>(a);
+    else k_tiled_rows<false><<<(unsigned)a.n_list, kThreads, sm, s>>>(a);
     DIM3_LAUNCHED();
 }
 
-// make_args with k_tile_rows's tile size and tile starts (built once per size).
+// make_args with k_tiled_rows's tile size and tile starts (built once per size).
 static XRowArgs tile_args(Plan& p, int64_t x_begin, int64_t rows, int64_t tile_bits, cudaStream_t s) {
     XRowArgs a = make_args(p, x_begin, rows, 0);
     a.tile_bits = tile_bits;
@@ -2235,9 +2167,7 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
     cnt.alloc((size_t)std::max<int64_t>(rows, 1) * 8, s);
     p.cache_off.alloc((size_t)(rows + 1) * 8, s);
     p.cache_units.release();
-    p.cache_tcnt.release();
     p.cache_n_list = 0;
-    p.cache_tiles = 0;
     if (rows > 0) {
         if (p.info.n_z <= 0 || p.info.n_r_kept == 0) {
             DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
@@ -2252,21 +2182,14 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
             const uint8_t* light = ensure_light(ctx, p, s);
             a.n_list = light ? list_rows(light, x_begin, rows, 0, p.cache_units, s) : rows;
             a.unit_rows = p.cache_units.as<int32_t>();
-            p.cache_tcnt.alloc((size_t)std::max<int64_t>(a.n_list * a.n_tiles, 1) * 4, s);
-            a.tcnt = p.cache_tcnt.as<int32_t>();
+            a.cnt = cnt.as<int64_t>();
             DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
-            launch_tiles(ctx, a, false, s);
-            if (a.n_list > 0) {
-                k_tile_sum<<<blocks_for(a.n_list), kThreads, 0, s>>>(a.tcnt, a.unit_rows, a.n_list, a.n_tiles,
-                                                                    cnt.as<int64_t>());
-                DIM3_LAUNCHED();
-            }
+            launch_wide(ctx, a, false, s);
             if (light) {
                 PhaseScope phase(ctx.stats, PH_COUNT, s);
                 launch_light(p, x_begin, rows, cnt.as<int64_t>(), nullptr, nullptr, nullptr, s);
             }
             p.cache_n_list = a.n_list;
-            p.cache_tiles = a.n_tiles;
             p.cache_tile_bits = a.tile_bits;
         } else {
             XRowArgs a = prep_args(p, x_begin, rows, kind, s);
@@ -2428,8 +2351,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
         set_stage(ctx, p, a, total);
         a.unit_rows = p.cache_units.as<int32_t>();
         a.n_list = p.cache_n_list;
-        a.tcnt_in = p.cache_tcnt.as<int32_t>();
-        launch_tiles(ctx, a, true, s);
+        launch_wide(ctx, a, true, s);
         if (p.light_n > 0) {
             PhaseScope phase(ctx.stats, PH_EMIT, s);
             launch_light(p, x_begin, rows, nullptr, a.off, out_x, out_z, s);

@@ -35,7 +35,6 @@ OPT_PATH = 9
 OPT_TILE_WORDS = 10
 OPT_DENSE_TILE_N = 11
 OPT_EMIT_PIPELINE = 12
-OPT_MID_ROW_MAX = 13
 PATH_AUTO, PATH_HYBRID, PATH_CLASSICAL = 0, 1, 2
 PHASES = {"map": 0, "partition": 1, "dense_ec": 2, "sparse_count": 3, "sparse_emit": 4, "dense_tc": 5}
 

@@ -123,15 +123,12 @@ def test_tiles_plan_range_row_counts_and_capacity(light, cases):
         c.close()
 
 
-@pytest.mark.parametrize("mid", [-1, 0, 1500, 3000])
-@pytest.mark.parametrize("light", [-1, 200])
-def test_medium_rows(mid, light, cases):
-    """Rows between the light bound and the medium bound deduplicate by
-    buckets of 4,096 z (counting sort on the high bits, one warp bitmap per
-    bucket) beside light rows and bitmap rows, on tiled and untiled z ranges,
-    one call and plan x ranges."""
+@pytest.mark.parametrize("light", [-1, 0, 200])
+def test_light_and_bitmap_rows_on_tiles(light, cases):
+    """Light rows (warp sorts) beside bitmap rows swept over z tiles, on tiled
+    and untiled z ranges, one call and plan x ranges."""
     for tw in (0, 1024):
-        c = ctx_with({dim3.OPT_MID_ROW_MAX: mid, dim3.OPT_LIGHT_ROW_MAX: light, dim3.OPT_TILE_WORDS: tw})
+        c = ctx_with({dim3.OPT_LIGHT_ROW_MAX: light, dim3.OPT_TILE_WORDS: tw})
         try:
             for inst, ox, oz in cases:
                 x, z = c.join_project(*inst_dev(inst))
@@ -144,12 +141,3 @@ def test_medium_rows(mid, light, cases):
                 assert np.array_equal(np.concatenate([host(p[1]) for p in parts]), oz)
         finally:
             c.close()
-
-
-def test_medium_row_option_off_matches():
-    c = dim3.Context(0)
-    try:
-        c.set_option(dim3.OPT_MID_ROW_MAX, 0)
-        c.set_option(dim3.OPT_MID_ROW_MAX, -1)
-    finally:
-        c.close()
