@@ -496,6 +496,7 @@ def main():
         sub = {"batch256": run_batch(args, rank, world, local_rank, sub=True),
                "chung_lu_1m_4m": onecall_record("chung_lu_1m_4m", local_rank),
                "chung_lu_uncapped_x0.25": onecall_record("chung_lu_uncapped_x0.25", local_rank),
+               "dense_16k": onecall_record("dense_16k", local_rank),
                "serve2000": serve_record(args, local_rank)}
 
     if rank == 0:
@@ -599,8 +600,8 @@ def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, 
     return {"pairs_per_s": out_p * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps, "steps": steps,
             "out_p": out_p, "out_j": info["out_j"], "n_x": info["n_x"], "n_z": info["n_z"],
             "n_z_dense": info["n_z_dense"], "phase_ms": {k: round(v[0] / steps, 4) for k, v in tm.items() if v[1]},
-            "roofline": {"bound": "hbm", "kernel": "emitting pass (k_tile_rows<emit> + k_light_rows<emit>, or "
-                         "k_xrow_emit_g)", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
+            "roofline": {"bound": "hbm", "kernel": "emitting pass (k_place_rows after staging, or k_tiled_rows<emit> "
+                         "+ k_light_rows<emit>, or k_xrow_emit_g)", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm"] if achieved else None, "peak_source": peaks["source"],
                          "alg_bytes_per_launch": alg_bytes, "launch_ms": emit_s * 1e3},
             "dense_roofline": dense,

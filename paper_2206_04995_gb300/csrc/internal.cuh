@@ -157,6 +157,12 @@ struct Plan {
     // z-tiled single instance: the cached range's (row, tile) units
     DevBuf cache_units;     // int32 [cache_n_list]: rows run over the z tiles (null: every row)
     int64_t cache_n_list = 0, cache_tile_bits = 0;
+    // z-tiled single instance, counted for an emitting call: every row's z
+    // values, deduplicated and ascending, at cache_slot[r] of cache_vals (a
+    // slot of min(|OUT_J| of the row, |Z|) entries rounded up to a multiple
+    // of four); the emitting pass then only places them (null: not staged)
+    DevBuf cache_vals;      // int32 [cache_slot[rows]]
+    DevBuf cache_slot;      // int64 [rows + 1]
     int64_t max_mx = -1;  // largest |R[x]| (the bound of a pair's count), -1 until computed
 };
 

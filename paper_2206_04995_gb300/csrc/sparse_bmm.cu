@@ -27,6 +27,10 @@
 namespace dimcube {
 
 constexpr int kWarps = kThreads / 32;
+// Passes of the row kernels over wide z ranges (k_tiled_rows, k_light_rows):
+// count each row's pairs; emit them at the row offsets; or stage each row's
+// z values at its slot of a buffer (and count them) for k_place_rows.
+constexpr int kCountRows = 0, kEmitRows = 1, kStageRows = 2;
 constexpr int kWarpStage = 1040;        // staged output values per warp (1024 + alignment shift, 16-byte multiple)
 constexpr int kWarpStageIds = 528;      // staged z ids per warp in the one-row kernel (512 + shift)
 constexpr int kWarpStageQ = 272;        // staged values per warp, quarter groups (256 + shift)
@@ -75,6 +79,7 @@ struct XRowArgs {
     int32_t* out_c;
     int vec_ok;
     // z-tiled single instance (k_tiled_rows): one CTA per listed row, n_tiles z tiles each
+    const int64_t* slot;       // staging pass: each row's slot in the staging buffer (a.out_z)
     const int32_t* unit_rows;  // row numbers (x - x_begin) of the rows to run, or null (rows 0 .. n_list-1)
     int64_t n_list;            // rows in the list
     int n_tiles;               // z tiles per row
@@ -1325,10 +1330,11 @@ __device__ __forceinline__ int wide_run(int tw4) { return ((tw4 + kThreads - 1) 
 // with 16-byte stores. A denser tile is compacted warp run by warp run
 // (compact_run) and cleared afterwards. The scan costs a few instructions
 // per 128 z, whichever bits are set.
-template <bool kEmit>
+template <int kMode>
 __global__ void __launch_bounds__(kThreads) k_tiled_rows(const XRowArgs a) {
+    constexpr bool kWrite = kMode != kCountRows;  // emitting or staging: z values are written
     extern __shared__ __align__(16) uint32_t smem[];
-    const int stage_cap = kEmit ? kWarps * a.stage_ints : 0;
+    const int stage_cap = kWrite ? kWarps * a.stage_ints : 0;
     int32_t* stage = reinterpret_cast<int32_t*>(smem);
     uint32_t* bm = smem + stage_cap;
     uint4* b4 = reinterpret_cast<uint4*>(bm);
@@ -1343,12 +1349,16 @@ __global__ void __launch_bounds__(kThreads) k_tiled_rows(const XRowArgs a) {
     const int64_t xr = a.unit_rows ? (int64_t)a.unit_rows[li] : li;
     const int64_t x = a.x_begin + xr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // emitting: the row's pairs go to out_z at its offset (x filled once);
+    // staging: its z values go to a.out_z (the staging buffer) at its slot
     int64_t o = 0;
-    if (kEmit) {
+    if (kMode == kEmitRows) {
         o = a.off[xr];
         const int64_t o_end = a.off[xr + 1];
         if (o_end == o) return;
         fill_range(a.out_x, o, o_end, a.dict_x[x], a.vec_ok);
+    } else if (kMode == kStageRows) {
+        o = a.slot[xr];
     }
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
     clear_words(bm, (int)(((a.tile_bits + 127) >> 7) << 2));
@@ -1402,7 +1412,7 @@ __global__ void __launch_bounds__(kThreads) k_tiled_rows(const XRowArgs a) {
         for (int u = u0; u < u1; ++u) {
             const uint4 v = b4[u];
             c += popc4(v);
-            if (kEmit) {
+            if (kWrite) {
                 const uint32_t m = (uint32_t)(v.x != 0u) | ((uint32_t)(v.y != 0u) << 1) |
                                    ((uint32_t)(v.z != 0u) << 2) | ((uint32_t)(v.w != 0u) << 3);
                 nz |= (uint64_t)m << (4 * (u - u0));
@@ -1410,7 +1420,7 @@ __global__ void __launch_bounds__(kThreads) k_tiled_rows(const XRowArgs a) {
                 b4[u] = make_uint4(0u, 0u, 0u, 0u);
             }
         }
-        if (!kEmit) {
+        if (!kWrite) {
             total += block_sum<int64_t, kThreads>((int64_t)c, s_scan);
             continue;
         }
@@ -1466,8 +1476,9 @@ __global__ void __launch_bounds__(kThreads) k_tiled_rows(const XRowArgs a) {
             flush_warp_ids(a.out_z + (wpos - sh), st, sh, mine, a.dict_z, a.vec_ok);
         }
         o += tot;
+        total += tot;
     }
-    if (!kEmit && tid == 0) a.cnt[xr] = total;
+    if (kMode != kEmitRows && tid == 0) a.cnt[xr] = total;
 }
 
 // ------------------------------------------------- Join-Count, packed
@@ -1631,8 +1642,9 @@ static void setup_attrs(const Ctx& ctx) {
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
     DIM3_CUDA(cudaFuncSetAttribute(k_xrow_counts<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cnt_max));
-    DIM3_CUDA(cudaFuncSetAttribute(k_tiled_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
-    DIM3_CUDA(cudaFuncSetAttribute(k_tiled_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_tiled_rows<kCountRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_tiled_rows<kEmitRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
+    DIM3_CUDA(cudaFuncSetAttribute(k_tiled_rows<kStageRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, bits_max));
     done[d] = true;
 }
 
@@ -1809,13 +1821,15 @@ struct LightArgs {
     const int32_t* ss_col;
     const int32_t* dict_x;
     const int32_t* dict_z;
-    int64_t* cnt;         // counting pass out
+    int64_t* cnt;         // counting and staging passes out
     const int64_t* off;   // emitting pass: row offsets
     int32_t* out_x;
     int32_t* out_z;
+    const int64_t* slot;  // staging pass: each row's slot in vals
+    int32_t* vals;
 };
 
-template <bool kEmit>
+template <int kMode>
 __global__ void __launch_bounds__(kThreads) k_light_rows(const LightArgs a) {
     __shared__ int32_t s_buf[kWarps][kLightMax];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1872,21 +1886,24 @@ __global__ void __launch_bounds__(kThreads) k_light_rows(const LightArgs a) {
                 __syncwarp();
             }
         }
-        int64_t o = kEmit ? a.off[xr] : 0;
+        // emitting: pairs at the row's offset; staging: z values at its slot
+        int64_t o = kMode == kEmitRows ? a.off[xr] : kMode == kStageRows ? a.slot[xr] : 0;
         int run = 0;
         for (int base = 0; base < n; base += 32) {
             const int t = base + lane;
             const int32_t v = t < n ? buf[t] : 0;
             const bool first = t < n && (t == 0 || buf[t - 1] != v);
             const unsigned bal = __ballot_sync(kFull, first);
-            if (kEmit && first) {
+            if (kMode == kEmitRows && first) {
                 const int64_t at = o + run + __popc(bal & lt);
                 a.out_x[at] = a.dict_x[x];
                 a.out_z[at] = a.dict_z[v];
+            } else if (kMode == kStageRows && first) {
+                a.vals[o + run + __popc(bal & lt)] = a.dict_z[v];
             }
             run += __popc(bal);
         }
-        if (!kEmit && lane == 0) a.cnt[xr] = run;
+        if (kMode != kEmitRows && lane == 0) a.cnt[xr] = run;
         __syncwarp();
     }
 }
@@ -1969,10 +1986,10 @@ static int64_t list_rows(const uint8_t* light, int64_t x_begin, int64_t rows, in
     return n;
 }
 
-// The light rows (warp sorts) of [x_begin, x_begin + rows): counting (cnt)
-// or emitting (off).
-static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* cnt, const int64_t* off,
-                         int32_t* out_x, int32_t* out_z, cudaStream_t s) {
+// The light rows (warp sorts) of [x_begin, x_begin + rows): counting (cnt),
+// emitting (off, out_x, out_z) or staging (cnt, slot, vals).
+static void launch_light(const Plan& p, int mode, int64_t x_begin, int64_t rows, int64_t* cnt, const int64_t* off,
+                         int32_t* out_x, int32_t* out_z, const int64_t* slot, int32_t* vals, cudaStream_t s) {
     LightArgs la{};
     la.x_begin = x_begin;
     la.r_rowptr = p.r_rowptr.as<int64_t>();
@@ -1985,14 +2002,17 @@ static void launch_light(const Plan& p, int64_t x_begin, int64_t rows, int64_t* 
     la.off = off;
     la.out_x = out_x;
     la.out_z = out_z;
+    la.slot = slot;
+    la.vals = vals;
     DevBuf list;
     const int64_t n = list_rows(p.light.as<uint8_t>(), x_begin, rows, 1, list, s);
     if (n > 0) {
         la.rows = list.as<int32_t>();
         la.n = n;
         const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kWarps), 152 * 8));
-        if (off) k_light_rows<true><<<g, kThreads, 0, s>>>(la);
-        else k_light_rows<false><<<g, kThreads, 0, s>>>(la);
+        if (mode == kEmitRows) k_light_rows<kEmitRows><<<g, kThreads, 0, s>>>(la);
+        else if (mode == kStageRows) k_light_rows<kStageRows><<<g, kThreads, 0, s>>>(la);
+        else k_light_rows<kCountRows><<<g, kThreads, 0, s>>>(la);
         DIM3_LAUNCHED();
     }
 }
@@ -2120,16 +2140,54 @@ static void launch_cnt(const Ctx& ctx, const XRowArgs& a, int cb, bool emit, cud
     DIM3_LAUNCHED();
 }
 
-// One CTA per listed row over its z tiles: counting (a.cnt) or emitting (a.off).
-static void launch_wide(const Ctx& ctx, const XRowArgs& a, bool emit, cudaStream_t s) {
+// One CTA per listed row over its z tiles: counting (a.cnt), emitting
+// (a.off) or staging (a.slot, a.cnt; a.out_z is the staging buffer).
+static void launch_wide(const Ctx& ctx, const XRowArgs& a, int mode, cudaStream_t s) {
     if (a.n_list <= 0) return;
     DIM3_REQUIRE(a.n_list < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long");
     setup_attrs(ctx);
-    PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
-    const size_t sm = bits_smem(a.tile_bits, emit, a.stage_ints);
-    if (emit) k_tiled_rows<true><<<(unsigned)a.n_list, kThreads, sm, s>>>(a);
-    else k_tiled_rows<false><<<(unsigned)a.n_list, kThreads, sm, s>>>(a);
+    PhaseScope phase(ctx.stats, mode == kEmitRows ? PH_EMIT : PH_COUNT, s);
+    const size_t sm = bits_smem(a.tile_bits, mode != kCountRows, a.stage_ints);
+    if (mode == kEmitRows) k_tiled_rows<kEmitRows><<<(unsigned)a.n_list, kThreads, sm, s>>>(a);
+    else if (mode == kStageRows) k_tiled_rows<kStageRows><<<(unsigned)a.n_list, kThreads, sm, s>>>(a);
+    else k_tiled_rows<kCountRows><<<(unsigned)a.n_list, kThreads, sm, s>>>(a);
     DIM3_LAUNCHED();
+}
+
+// Staged rows to their places: row r's z values from vals[slot[r] ..] to
+// out_z[off[r] .. off[r + 1]) (16-byte stores where the output is aligned),
+// x = dict_x[x_begin + r] beside them. One CTA per row, rows in turn.
+__global__ void __launch_bounds__(kThreads) k_place_rows(const int64_t* __restrict__ off,
+                                                         const int64_t* __restrict__ slot,
+                                                         const int32_t* __restrict__ vals, int64_t rows,
+                                                         int64_t x_begin, const int32_t* __restrict__ dict_x,
+                                                         int32_t* out_x, int32_t* out_z, int vec_ok) {
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t o0 = off[r], o1 = off[r + 1];
+        if (o0 == o1) continue;
+        const int64_t d = slot[r] - o0;  // vals index of output position o: o + d
+        fill_range(out_x, o0, o1, dict_x[x_begin + r], vec_ok);
+        if (!vec_ok) {
+            for (int64_t o = o0 + threadIdx.x; o < o1; o += blockDim.x) __stcs(out_z + o, __ldcs(vals + o + d));
+            continue;
+        }
+        const int64_t a = min64(o1, (o0 + 3) & ~int64_t(3)), b = max64(a, o1 & ~int64_t(3));
+        for (int64_t o = o0 + threadIdx.x; o < a; o += blockDim.x) __stcs(out_z + o, __ldcs(vals + o + d));
+        for (int64_t o = a + 4 * (int64_t)threadIdx.x; o < b; o += 4 * (int64_t)blockDim.x) {
+            const int32_t* v = vals + o + d;
+            __stcs(reinterpret_cast<int4*>(out_z + o), make_int4(__ldcs(v), __ldcs(v + 1), __ldcs(v + 2), __ldcs(v + 3)));
+        }
+        for (int64_t o = b + threadIdx.x; o < o1; o += blockDim.x) __stcs(out_z + o, __ldcs(vals + o + d));
+    }
+}
+
+// slot length of row r: min(|OUT_J| of x_begin + r + extra, n_z), rounded
+// up to a multiple of four (16-byte aligned slots); extra covers pairs that
+// are no join tuples of the plan (a partial result cache's columns)
+__global__ void k_slot_len(const int64_t* __restrict__ outj_x, int64_t x_begin, int64_t rows, int64_t extra,
+                           int64_t n_z, int64_t* len) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
+        len[r] = (min64(outj_x[x_begin + r] + extra, n_z) + 3) & ~int64_t(3);
 }
 
 // make_args with k_tiled_rows's tile size and tile starts (built once per size).
@@ -2145,13 +2203,44 @@ static XRowArgs tile_args(Plan& p, int64_t x_begin, int64_t rows, int64_t tile_b
 
 // Dense results and per-row counts of a range, cached on the plan so that a
 // count query followed by the emitting call does the counting pass once.
-static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int kind, cudaStream_t s) {
+// Slots of a staging pass over rows [x_begin, x_begin + rows) of a z-tiled
+// plan (p.cache_slot, p.cache_vals): each row gets min(its |OUT_J| plus the
+// partial result cache's columns, |Z|) entries, a bound of its pairs. Returns false (and allocates nothing) when
+// the buffer would take more than a quarter of the free device memory.
+static bool stage_slots(Plan& p, int64_t x_begin, int64_t rows, cudaStream_t s) {
+    p.cache_slot.alloc((size_t)(rows + 1) * 8, s);
+    {
+        DevBuf len;
+        len.alloc((size_t)rows * 8, s);
+        k_slot_len<<<blocks_for(rows), kThreads, 0, s>>>(p.outj_x.as<int64_t>(), x_begin, rows, p.n_zc,
+                                                         p.info.n_z, len.as<int64_t>());
+        DIM3_LAUNCHED();
+        exclusive_scan_i64(len.as<int64_t>(), p.cache_slot.as<int64_t>(), rows, s);
+    }
+    const int64_t n = read_i64(p.cache_slot.as<int64_t>() + rows, s);
+    size_t free_b = 0, total_b = 0;
+    DIM3_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if ((double)n * 4.0 > 0.25 * (double)free_b) {
+        p.cache_slot.release();
+        return false;
+    }
+    p.cache_vals.alloc((size_t)std::max<int64_t>(n, 4) * 4, s);
+    return true;
+}
+
+// The counting pass of a range (row offsets in p.cache_off, dense results).
+// With `stage` (an emitting call follows) a z-tiled plan also keeps every
+// row's z values (p.cache_vals), so that the emitting pass only places them.
+static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int kind, cudaStream_t s,
+                          bool stage = false) {
     if (p.cache_begin == x_begin && p.cache_end == x_end && p.cache_kind == kind) return;
     p.cache_begin = p.cache_end = -1;
     p.cache_kind = -1;
     const int64_t rows = x_end - x_begin;
     p.cache_dbits.release();
     p.cache_dcnt.release();
+    p.cache_vals.release();
+    p.cache_slot.release();
     DIM3_REQUIRE(kind == 0 || p.n_zc == 0, DIM3_ERR_UNSUPPORTED,
                  "Join-Count on a plan with a partial result cache (the cache holds pairs, not counts)");
     if (p.n_zd_total > 0 && rows > 0) {
@@ -2184,10 +2273,18 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
             a.unit_rows = p.cache_units.as<int32_t>();
             a.cnt = cnt.as<int64_t>();
             DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
-            launch_wide(ctx, a, false, s);
+            const int mode = stage && stage_slots(p, x_begin, rows, s) ? kStageRows : kCountRows;
+            if (mode == kStageRows) {
+                a.slot = p.cache_slot.as<int64_t>();
+                a.out_z = p.cache_vals.as<int32_t>();
+                a.vec_ok = 1;
+                set_stage(ctx, p, a, p.info.out_j);
+            }
+            launch_wide(ctx, a, mode, s);
             if (light) {
                 PhaseScope phase(ctx.stats, PH_COUNT, s);
-                launch_light(p, x_begin, rows, cnt.as<int64_t>(), nullptr, nullptr, nullptr, s);
+                launch_light(p, mode, x_begin, rows, cnt.as<int64_t>(), nullptr, nullptr, nullptr,
+                             p.cache_slot.as<int64_t>(), p.cache_vals.as<int32_t>(), s);
             }
             p.cache_n_list = a.n_list;
             p.cache_tile_bits = a.tile_bits;
@@ -2200,7 +2297,8 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
             launch_rows(ctx, a, kind, false, s);
             if (a.light) {
                 PhaseScope phase(ctx.stats, PH_COUNT, s);
-                launch_light(p, x_begin, rows, cnt.as<int64_t>(), nullptr, nullptr, nullptr, s);
+                launch_light(p, kCountRows, x_begin, rows, cnt.as<int64_t>(), nullptr, nullptr, nullptr, nullptr,
+                             nullptr, s);
             }
         }
     }
@@ -2322,7 +2420,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
         p.info.n_r_kept > 0 && !use_tiles(ctx, p, 0) && p.zw <= kMaxTileWords && !ctx.opt.two_pass &&
         !ensure_light(ctx, p, s))
         return plan_join_single_pass(ctx, p, x_begin, x_end, out_x, out_z, capacity, count, s);
-    ensure_counts(ctx, p, x_begin, x_end, kind, s);
+    ensure_counts(ctx, p, x_begin, x_end, kind, s, true);
     const int64_t rows = x_end - x_begin;
     const int64_t total = read_i64(p.cache_off.as<int64_t>() + rows, s);
     if (count) *count = total;
@@ -2340,6 +2438,15 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
         a.vec_ok = ((reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z) |
                      reinterpret_cast<uintptr_t>(out_cnt)) & 15u) == 0;
         launch_cnt(ctx, a, cb, true, s);
+    } else if (total > 0 && use_tiles(ctx, p, kind) && p.cache_vals.p) {
+        // staged by the counting pass: place every row's z values
+        DIM3_REQUIRE(out_x && out_z, DIM3_ERR_ARG, "null output buffer");
+        PhaseScope phase(ctx.stats, PH_EMIT, s);
+        const int vec_ok = ((reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z)) & 15u) == 0;
+        k_place_rows<<<(unsigned)std::min<int64_t>(rows, (int64_t)ctx.sm_count * 16), kThreads, 0, s>>>(
+            p.cache_off.as<int64_t>(), p.cache_slot.as<int64_t>(), p.cache_vals.as<int32_t>(), rows, x_begin,
+            p.dict_x.as<int32_t>(), out_x, out_z, vec_ok);
+        DIM3_LAUNCHED();
     } else if (total > 0 && use_tiles(ctx, p, kind)) {
         DIM3_REQUIRE(out_x && out_z, DIM3_ERR_ARG, "null output buffer");
         XRowArgs a = tile_args(p, x_begin, rows, p.cache_tile_bits, s);
@@ -2351,10 +2458,10 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
         set_stage(ctx, p, a, total);
         a.unit_rows = p.cache_units.as<int32_t>();
         a.n_list = p.cache_n_list;
-        launch_wide(ctx, a, true, s);
+        launch_wide(ctx, a, kEmitRows, s);
         if (p.light_n > 0) {
             PhaseScope phase(ctx.stats, PH_EMIT, s);
-            launch_light(p, x_begin, rows, nullptr, a.off, out_x, out_z, s);
+            launch_light(p, kEmitRows, x_begin, rows, nullptr, a.off, out_x, out_z, nullptr, nullptr, s);
         }
     } else if (total > 0) {
         DIM3_REQUIRE(out_x && out_z && (kind == 0 || out_cnt), DIM3_ERR_ARG, "null output buffer");
@@ -2381,7 +2488,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
         launch_rows(ctx, a, kind, true, s);
         if (a.light) {
             PhaseScope phase(ctx.stats, PH_EMIT, s);
-            launch_light(p, x_begin, rows, nullptr, a.off, out_x, out_z, s);
+            launch_light(p, kEmitRows, x_begin, rows, nullptr, a.off, out_x, out_z, nullptr, nullptr, s);
         }
     }
     DIM3_CUDA(cudaStreamSynchronize(s));
