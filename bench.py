@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--dense-variant", type=int, default=None, help="0 auto, 1 tensor core, 2 popc, 3 probe")
     ap.add_argument("--opt", action="append", default=[],
                     help="library option KEY=VALUE (dim3_option number), e.g. 6=1 for one x row per emitting CTA")
+    ap.add_argument("--batch-insts", type=int, default=256,
+                    help="batch256: instances drawn (fewer for small profiling runs; the first ones of the stream)")
     ap.add_argument("--serve-queries", type=int, default=2000)
     ap.add_argument("--serve-max-tuples", type=int, default=2_000_000)
     ap.add_argument("--serve-workers", type=int, default=2)
@@ -466,7 +468,9 @@ def main():
         alg_bytes = (12 if args.count else 8) * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
         achieved = alg_bytes / emit_s / 1e9
         traffic, tinfo = traffic_for(args.workload) if not args.count else (None, {"kernel": "k_xrow_counts<emit>"})
-        kname = (tinfo or {}).get("kernel", "k_xrow_emit_g / k_xrow_bits<emit>")
+        tiled = args.workload == "chung_lu_1m_4m" and not args.count
+        kname = (tinfo or {}).get("kernel", "k_place_rows (rows staged by k_tiled_rows<stage> + k_light_rows<stage>)"
+                                  if tiled else "k_xrow_emit_g / k_xrow_bits<emit>")
         roofline = {"bound": "hbm", "kernel": f"{kname} (SparseBMM+union+compaction)",
                     "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s", "frac": achieved / peaks["hbm"],
                     "peak_source": peaks["source"], "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
@@ -516,6 +520,8 @@ def main():
             "roofline": roofline,
             "phase_ms": phases,
             "partition_roofline": partition_roofline(info, phases, peaks["hbm"]),
+            "sparse_roofline": (sparse_passes_roofline(tm, args.steps, roofline["alg_bytes_per_launch"], peaks)
+                                if roofline["bound"] == "hbm" else None),
             "wall_s": t_wall,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -604,10 +610,24 @@ def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, 
                          "+ k_light_rows<emit>, or k_xrow_emit_g)", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm"] if achieved else None, "peak_source": peaks["source"],
                          "alg_bytes_per_launch": alg_bytes, "launch_ms": emit_s * 1e3},
+            # the whole SparseBMM + compaction (counting or staging pass plus
+            # emitting pass) against the same algorithmic bytes
+            "sparse_roofline": sparse_passes_roofline(tm, steps, alg_bytes, peaks),
             "dense_roofline": dense,
             "partition_roofline": partition_roofline(info, {k: v[0] / steps for k, v in tm.items() if v[1]},
                                                      peaks["hbm"]),
             "tuner": tuned, "l2": "flushed between steps"}
+
+
+def sparse_passes_roofline(tm, steps: int, alg_bytes: float, peaks):
+    """HBM fraction of both SparseBMM passes together (counting or staging
+    pass + emitting pass), per step."""
+    ms = (tm["sparse_count"][0] + tm["sparse_emit"][0]) / steps
+    if ms <= 0:
+        return None
+    gbs = alg_bytes / (ms / 1e3) / 1e9
+    return {"kernels": "k_tiled_rows<stage> + k_light_rows<stage> + k_place_rows, or count + emit",
+            "alg_bytes": alg_bytes, "ms": ms, "achieved_gbs": gbs, "frac": gbs / peaks["hbm"]}
 
 
 def serve_record(args, local_rank: int):
@@ -642,7 +662,7 @@ def run_batch(args, rank, world, local_rank, sub=False):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    insts = gen.config4_batch(seed=3 + 1000 * rank)
+    insts = gen.config4_batch(seed=3 + 1000 * rank, n_inst=args.batch_insts)
     cols = [[torch.from_numpy(np.ascontiguousarray(a, np.int32)).to(dev)
              for a in (i.r_key, i.r_val, i.s_key, i.s_val)] for i in insts]
     ctx = dim3.Context(local_rank)

@@ -331,12 +331,14 @@ __device__ __forceinline__ void compact_run(const XRowArgs& a, const uint32_t* b
             wpos += sc;
             sc = 0;
         }
-        const int per = a.stage_ints >= kWarpStage ? 1 : 2;  // whole groups fit a large stage
+        // whole groups fit a large stage, half groups (512 pairs) the
+        // 528-entry one, quarter groups (256 pairs) the 272-entry one
+        const int per = a.stage_ints >= kWarpStage ? 1 : a.stage_ints >= kWarpStageIds ? 2 : 4;
         for (int h = gc * per; h < min(gc + 4, g1) * per; ++h) {
             const int g = h / per;
             const int w = (g << 5) + lane;
-            const bool mine_half = per == 1 || (lane >> 4) == (h & 1);
-            const uint32_t word = (mine_half && w < tw) ? bm[w] : 0u;
+            const bool mine_part = per == 1 || lane / (32 / per) == h % per;
+            const uint32_t word = (mine_part && w < tw) ? bm[w] : 0u;
             const int c = __popc(word);
             const int incl = warp_inclusive_scan(c);
             const int total_g = __shfl_sync(kFull, incl, 31);
@@ -1490,9 +1492,9 @@ __global__ void __launch_bounds__(kThreads) k_tiled_rows(const XRowArgs a) {
 // threads on short ones) and add 1 << (CB * slot) with one shared atomic;
 // DenseEC's counts are added the same way. Every warp then owns a run of the
 // tile's counter words: it counts their nonzero counters and, in the
-// emitting pass, writes (z, count) of each in z order through a per-warp
-// stage -- no block barrier between a warp's groups.
-constexpr int kCntStageP = 264;             // staged (z id, count) per warp: 2 x 128 + the alignment shift
+// emitting pass, writes (z, count) of each in z order straight to the output
+// (one z per lane, ballot compaction) -- no block barrier between a warp's
+// blocks and no staging.
 constexpr int64_t kMaxPackedWords = 7168;   // counter words per tile (28 KiB)
 
 template <int CB>
@@ -1509,9 +1511,7 @@ __global__ void __launch_bounds__(kThreads) k_cnt_rows(const XRowArgs a) {
     constexpr int LCPW = CB == 8 ? 2 : CB == 16 ? 1 : 0;
     constexpr uint32_t CMASK = CB == 32 ? 0xFFFFFFFFu : ((1u << CB) - 1u);
     extern __shared__ __align__(16) uint32_t smem[];
-    int32_t* st_z = reinterpret_cast<int32_t*>(smem);            // emit: kWarps x kCntStageP z ids
-    int32_t* st_c = st_z + (kEmit ? kWarps * kCntStageP : 0);     // emit: kWarps x kCntStageP counts
-    uint32_t* ctr = reinterpret_cast<uint32_t*>(st_c + (kEmit ? kWarps * kCntStageP : 0));
+    uint32_t* ctr = smem;  // the tile's packed counters
     __shared__ ChunkSmem cs;
     __shared__ int32_t s_wc[kWarps];
     __shared__ int64_t s_scan[kWarps + 1];
@@ -1520,6 +1520,7 @@ __global__ void __launch_bounds__(kThreads) k_cnt_rows(const XRowArgs a) {
     if (xr >= a.n_rows) return;
     const int64_t x = a.x_begin + xr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = lanemask_lt();
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
     int64_t out_pos = 0, total = 0;
     if (kEmit) {
@@ -1568,42 +1569,33 @@ __global__ void __launch_bounds__(kThreads) k_cnt_rows(const XRowArgs a) {
             if (w < warp) wpos += s_wc[w];
             tile_total += s_wc[w];
         }
-        int32_t* sz = st_z + warp * kCntStageP;
-        int32_t* sc_ = st_c + warp * kCntStageP;
-        int sh = (int)(wpos & 3), sc = 0;
+        // Round of 32 counter words (32 * CPW z), lane l holding word l:
+        // blocks of 32 consecutive z, each lane taking one z (its word shuffled
+        // in), the nonzero ones compacted by a ballot and written straight to
+        // the output -- z values read coalesced from the dictionary, stores to
+        // consecutive positions; blocks whose words are all zero are skipped.
+        constexpr int WPB = 32 / CPW;  // counter words per 32-z block
+        constexpr unsigned BMASK = WPB == 32 ? 0xFFFFFFFFu : ((1u << WPB) - 1u);
         for (int wb = w0; wb < w1; wb += 32) {
             const int w = wb + lane;
             const uint32_t word = w < w1 ? ctr[w] : 0u;
-            uint32_t m = nonzero_slots<CB>(word);
-            const int c = __popc(m);
-            const int incl = warp_inclusive_scan(c);
-            const int tot = __shfl_sync(kFull, incl, 31);
-            if (tot == 0) continue;
-            if (sh + sc + tot > kCntStageP) {
-                __syncwarp();
-                flush_warp_ids(a.out_z + (wpos - sh), sz, sh, sc, a.dict_z, a.vec_ok);
-                flush_warp(a.out_c + (wpos - sh), sc_, sh, sc, a.vec_ok);
-                __syncwarp();
-                wpos += sc;
-                sh = (int)(wpos & 3);
-                sc = 0;
+            const unsigned nzw = __ballot_sync(kFull, word != 0u);
+            if (nzw == 0u) continue;
+#pragma unroll
+            for (int j = 0; j < CPW; ++j) {
+                if (((nzw >> (j * WPB)) & BMASK) == 0u) continue;
+                const uint32_t wv = __shfl_sync(kFull, word, j * WPB + lane / CPW);
+                const uint32_t c = (wv >> (CB * (lane % CPW))) & CMASK;
+                const unsigned m = __ballot_sync(kFull, c != 0u);
+                if (c != 0u) {
+                    const int64_t pos = wpos + __popc(m & lt);
+                    const int64_t z = zt0 + (int64_t)(wb + j * WPB) * CPW + lane;
+                    __stcs(a.out_z + pos, __ldg(a.dict_z + z));
+                    __stcs(a.out_c + pos, (int32_t)c);
+                }
+                wpos += __popc(m);
             }
-            int pos = sh + sc + incl - c;
-            while (m) {
-                const int slot = __ffs(m) - 1;
-                m &= m - 1;
-                sz[pos] = (int32_t)(zt0 + (int64_t)w * CPW + slot);
-                sc_[pos] = (int32_t)((word >> (CB * slot)) & CMASK);
-                ++pos;
-            }
-            sc += tot;
         }
-        __syncwarp();
-        if (sc) {
-            flush_warp_ids(a.out_z + (wpos - sh), sz, sh, sc, a.dict_z, a.vec_ok);
-            flush_warp(a.out_c + (wpos - sh), sc_, sh, sc, a.vec_ok);
-        }
-        __syncwarp();
         out_pos += tile_total;
         __syncthreads();
     }
@@ -2114,7 +2106,7 @@ static void launch_cnt(const Ctx& ctx, const XRowArgs& a, int cb, bool emit, cud
     if (a.n_rows <= 0 || a.n_z <= 0) return;
     static bool done[64] = {false};
     if (!done[ctx.device & 63]) {
-        const int mx = (int)((size_t)2 * kWarps * kCntStageP * 4 + (size_t)12288 * 4);  // the largest tile option
+        const int mx = (int)((size_t)12288 * 4);  // the largest tile option
         DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         DIM3_CUDA(cudaFuncSetAttribute(k_cnt_rows<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -2126,7 +2118,7 @@ static void launch_cnt(const Ctx& ctx, const XRowArgs& a, int cb, bool emit, cud
     DIM3_REQUIRE(a.n_rows < (int64_t(1) << 31), DIM3_ERR_OVERFLOW, "x range too long");
     PhaseScope phase(ctx.stats, emit ? PH_EMIT : PH_COUNT, s);
     const size_t words = (size_t)ceil_div(a.tile_bits, 32 / cb);
-    const size_t sm = (emit ? (size_t)2 * kWarps * kCntStageP * 4 : 0) + words * 4;
+    const size_t sm = words * 4;
     const unsigned g = (unsigned)a.n_rows;
 #define DIM3_CNT_LAUNCH(CB)                                                 \
     do {                                                                    \
@@ -2173,9 +2165,26 @@ __global__ void __launch_bounds__(kThreads) k_place_rows(const int64_t* __restri
         }
         const int64_t a = min64(o1, (o0 + 3) & ~int64_t(3)), b = max64(a, o1 & ~int64_t(3));
         for (int64_t o = o0 + threadIdx.x; o < a; o += blockDim.x) __stcs(out_z + o, __ldcs(vals + o + d));
-        for (int64_t o = a + 4 * (int64_t)threadIdx.x; o < b; o += 4 * (int64_t)blockDim.x) {
+        // 16-byte pieces [a, b), two per thread and round with all their loads
+        // issued first; 16-byte loads too when source and output share their
+        // alignment (d a multiple of four)
+        const bool same = (d & 3) == 0;
+        const int64_t step = 4 * (int64_t)blockDim.x;
+        for (int64_t o = a + 4 * (int64_t)threadIdx.x; o < b; o += 2 * step) {
+            const int64_t o2 = o + step;
+            const bool two = o2 < b;
             const int32_t* v = vals + o + d;
-            __stcs(reinterpret_cast<int4*>(out_z + o), make_int4(__ldcs(v), __ldcs(v + 1), __ldcs(v + 2), __ldcs(v + 3)));
+            const int32_t* w = vals + (two ? o2 : o) + d;
+            int4 p, q;
+            if (same) {
+                p = __ldcs(reinterpret_cast<const int4*>(v));
+                q = __ldcs(reinterpret_cast<const int4*>(w));
+            } else {
+                p = make_int4(__ldcs(v), __ldcs(v + 1), __ldcs(v + 2), __ldcs(v + 3));
+                q = make_int4(__ldcs(w), __ldcs(w + 1), __ldcs(w + 2), __ldcs(w + 3));
+            }
+            __stcs(reinterpret_cast<int4*>(out_z + o), p);
+            if (two) __stcs(reinterpret_cast<int4*>(out_z + o2), q);
         }
         for (int64_t o = b + threadIdx.x; o < o1; o += blockDim.x) __stcs(out_z + o, __ldcs(vals + o + d));
     }
