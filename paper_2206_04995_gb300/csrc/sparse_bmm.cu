@@ -1960,6 +1960,14 @@ static const uint8_t* ensure_light(const Ctx& ctx, Plan& p, cudaStream_t s) {
     return p.light_n > 0 ? p.light.as<uint8_t>() : nullptr;
 }
 
+// Join-Project rows of a single instance that k_tiled_rows sweeps (one CTA
+// per row, the counting pass staging z values for the emitting call): a z
+// range wider than one tile, or light rows beside the others (the staging
+// pass then sorts the light rows once instead of in both passes).
+static bool row_sweep(const Ctx& ctx, Plan& p, int kind, cudaStream_t s) {
+    return use_tiles(ctx, p, kind) || (kind == 0 && p.n_inst == 1 && ensure_light(ctx, p, s) != nullptr);
+}
+
 // Row numbers r of [x_begin, x_begin + rows) whose light flag equals `want`
 // (flags null: every row is heavy) into `list`; returns their number.
 static int64_t list_rows(const uint8_t* light, int64_t x_begin, int64_t rows, int want, DevBuf& list,
@@ -2274,7 +2282,7 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
             a.d_cnt = p.cache_dcnt.as<int32_t>();
             a.cnt = cnt.as<int64_t>();
             launch_cnt(ctx, a, counter_bits(p, s), false, s);
-        } else if (use_tiles(ctx, p, kind)) {
+        } else if (row_sweep(ctx, p, kind, s)) {
             XRowArgs a = tile_args(p, x_begin, rows, tile_words_for(ctx, p) * 32, s);
             a.d_bits = p.cache_dbits.as<uint32_t>();
             const uint8_t* light = ensure_light(ctx, p, s);
@@ -2426,7 +2434,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
     check_range(p, x_begin, x_end);
     const bool cached = p.cache_begin == x_begin && p.cache_end == x_end && p.cache_kind == kind;
     if (!cached && kind == 0 && capacity > 0 && out_x && out_z && x_end > x_begin && p.info.n_z > 0 &&
-        p.info.n_r_kept > 0 && !use_tiles(ctx, p, 0) && p.zw <= kMaxTileWords && !ctx.opt.two_pass &&
+        p.info.n_r_kept > 0 && !row_sweep(ctx, p, 0, s) && p.zw <= kMaxTileWords && !ctx.opt.two_pass &&
         !ensure_light(ctx, p, s))
         return plan_join_single_pass(ctx, p, x_begin, x_end, out_x, out_z, capacity, count, s);
     ensure_counts(ctx, p, x_begin, x_end, kind, s, true);
@@ -2447,7 +2455,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
         a.vec_ok = ((reinterpret_cast<uintptr_t>(out_x) | reinterpret_cast<uintptr_t>(out_z) |
                      reinterpret_cast<uintptr_t>(out_cnt)) & 15u) == 0;
         launch_cnt(ctx, a, cb, true, s);
-    } else if (total > 0 && use_tiles(ctx, p, kind) && p.cache_vals.p) {
+    } else if (total > 0 && row_sweep(ctx, p, kind, s) && p.cache_vals.p) {
         // staged by the counting pass: place every row's z values
         DIM3_REQUIRE(out_x && out_z, DIM3_ERR_ARG, "null output buffer");
         PhaseScope phase(ctx.stats, PH_EMIT, s);
@@ -2456,7 +2464,7 @@ int64_t plan_join(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_end, int k
             p.cache_off.as<int64_t>(), p.cache_slot.as<int64_t>(), p.cache_vals.as<int32_t>(), rows, x_begin,
             p.dict_x.as<int32_t>(), out_x, out_z, vec_ok);
         DIM3_LAUNCHED();
-    } else if (total > 0 && use_tiles(ctx, p, kind)) {
+    } else if (total > 0 && row_sweep(ctx, p, kind, s)) {
         DIM3_REQUIRE(out_x && out_z, DIM3_ERR_ARG, "null output buffer");
         XRowArgs a = tile_args(p, x_begin, rows, p.cache_tile_bits, s);
         a.d_bits = p.cache_dbits.as<uint32_t>();
