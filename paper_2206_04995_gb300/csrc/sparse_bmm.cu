@@ -1190,7 +1190,8 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
 // both the power-law graph and Zipf tables.) The counting pass stores each
 // row's pairs; the emitting pass writes them at the row's offset, tile after
 // tile.
-constexpr int kTileChunk = 2 * kThreads;  // R entries of a row per round (two per thread)
+constexpr int kTileChunk = kThreads;      // R entries of a row per round
+constexpr int kEPT = kTileChunk / kThreads;  // entries per thread and round
 constexpr int kPiece = 256;               // tuples per warp work item
 constexpr int kLongSeg = 32;              // segments from this length on go to the warps
 
@@ -1214,11 +1215,11 @@ template <class Visit>
 __device__ __forceinline__ void visit_chunk(const XRowArgs& a, int64_t c0, int nc, int t, ChunkSmem& sm,
                                             int32_t* wide, int* nwide, Visit visit) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int len[2];
-    uint32_t first[2];
+    int len[kEPT];
+    uint32_t first[kEPT];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int i = 2 * tid + k;
+    for (int k = 0; k < kEPT; ++k) {
+        const int i = kEPT * tid + k;
         len[k] = 0;
         first[k] = 0u;
         if (i < nc) {
@@ -1241,16 +1242,21 @@ __device__ __forceinline__ void visit_chunk(const XRowArgs& a, int64_t c0, int n
             }
         }
     }
-    const int pc0 = len[0] >= kLongSeg ? (len[0] + kPiece - 1) / kPiece : 0;
-    const int pc1 = len[1] >= kLongSeg ? (len[1] + kPiece - 1) / kPiece : 0;
+    int pc[kEPT], pcs = 0;
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        pc[k] = len[k] >= kLongSeg ? (len[k] + kPiece - 1) / kPiece : 0;
+        pcs += pc[k];
+    }
     int n_pieces;
-    const int ex = block_exclusive_scan<int, kThreads>(pc0 + pc1, &n_pieces, sm.sc);
-    sm.pc[2 * tid] = ex;
-    sm.pc[2 * tid + 1] = ex + pc0;
-    sm.s0[2 * tid] = first[0];
-    sm.s0[2 * tid + 1] = first[1];
-    sm.len[2 * tid] = len[0];
-    sm.len[2 * tid + 1] = len[1];
+    int ex = block_exclusive_scan<int, kThreads>(pcs, &n_pieces, sm.sc);
+#pragma unroll
+    for (int k = 0; k < kEPT; ++k) {
+        sm.pc[kEPT * tid + k] = ex;
+        ex += pc[k];
+        sm.s0[kEPT * tid + k] = first[k];
+        sm.len[kEPT * tid + k] = len[k];
+    }
     __syncthreads();
     // long segments: piece p of the chunk goes to warp p mod kWarps
     for (int p = warp; p < n_pieces; p += kWarps) {
@@ -1271,7 +1277,7 @@ __device__ __forceinline__ void visit_chunk(const XRowArgs& a, int64_t c0, int n
     }
     // short segments: the thread that read the entry walks it
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kEPT; ++k) {
         if (len[k] > 0 && len[k] < kLongSeg) {
             const int32_t* src = a.ss_col + first[k];
             for (int q0 = 0; q0 < len[k]; q0 += 4) {
