@@ -501,6 +501,10 @@ def main():
                "chung_lu_1m_4m": onecall_record("chung_lu_1m_4m", local_rank),
                "chung_lu_uncapped_x0.25": onecall_record("chung_lu_uncapped_x0.25", local_rank),
                "dense_16k": onecall_record("dense_16k", local_rank),
+               # every z dense on the tensor cores (the tuner's choice above is
+               # all sparse on GB300): DenseEC's own roofline, same exact result
+               "dense_16k_tc": onecall_record("dense_16k", local_rank, tune_it=False,
+                                              opts={dim3.OPT_THETA_Z: 0, dim3.OPT_DENSE_VARIANT: dim3.DENSE_TC}),
                "serve2000": serve_record(args, local_rank)}
 
     if rank == 0:
@@ -548,10 +552,12 @@ def partition_roofline(info: dict, phase_ms: dict, peak_gbs: float) -> dict:
     return {"alg_bytes": alg, "ms": ms, "achieved_gbs": gbs, "frac": gbs / peak_gbs if gbs else None}
 
 
-def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, tune_it: bool = True):
+def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, tune_it: bool = True,
+                   opts: dict | None = None):
     """A compact record of one workload through the one-call path
-    (dim3_join_project into caller buffers), tuned first: pairs/s, phases and
-    the emitting pass's HBM roofline."""
+    (dim3_join_project into caller buffers), tuned first (or with the given
+    context options instead): pairs/s, phases and the emitting pass's HBM
+    roofline (and the tensor-core DenseEC's when it ran)."""
     import torch
 
     import paper_2206_04995_gb300 as dim3
@@ -561,7 +567,9 @@ def onecall_record(name: str, local_rank: int, steps: int = 5, warmup: int = 3, 
     cols = device_columns(torch, [inst.r_key, inst.r_val, inst.s_key, inst.s_val], dev)
     ctx = dim3.Context(local_rank)
     tuned = None
-    if tune_it:
+    for k, v in (opts or {}).items():
+        ctx.set_option(k, v)
+    if tune_it and not opts:
         from paper_2206_04995_gb300 import tune
 
         tuned = tune.summary(tune.tune(ctx, cols, use_cache=False))
