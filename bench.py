@@ -749,7 +749,11 @@ def run_batch(args, rank, world, local_rank, sub=False):
     emit_s = emit_ms / 1e3 / max(emit_n, 1)
     alg_bytes = 8 * out_p + 4 * info["n_r_kept"] + 4 * info["n_s_sparse"]
     achieved = alg_bytes / emit_s / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_xrow_bits<emit> over all instances", "achieved": achieved,
+    # the emitting kernel over all instances: k_xrow_emit_g<G> with G rows of
+    # one instance per CTA (the tuner's choice), or k_xrow_bits<emit> with one
+    G = (tuned or {}).get("emit_rows") or next((int(kv.split("=")[1]) for kv in args.opt if kv.split("=")[0] == "6"), 0) or 2
+    kname = f"k_xrow_emit_g<{G}> over all instances" if G > 1 else "k_xrow_bits<emit> over all instances"
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved,
                 "peak": peaks["hbm"], "unit": "GB/s", "frac": achieved / peaks["hbm"],
                 "peak_source": peaks["source"], "traffic": None, "alg_bytes_per_launch": alg_bytes,
                 "launch_ms": emit_s * 1e3}
