@@ -1190,12 +1190,11 @@ __global__ void __launch_bounds__(kThreads) k_xrow_counts(const XRowArgs a) {
 // both the power-law graph and Zipf tables.) The counting pass stores each
 // row's pairs; the emitting pass writes them at the row's offset, tile after
 // tile.
-constexpr int kTileChunk = kThreads;      // R entries of a row per round
-constexpr int kEPT = kTileChunk / kThreads;  // entries per thread and round
+constexpr int kTileChunk = kThreads;      // R entries of a row per round (one per thread)
 constexpr int kPiece = 256;               // tuples per warp work item
 constexpr int kLongSeg = 32;              // segments from this length on go to the warps
 
-// Shared memory of visit_chunk.
+// Shared memory of visit_segments.
 struct ChunkSmem {
     uint32_t s0[kTileChunk];   // first tuple of the entry's segment in ss_col
     int32_t len[kTileChunk];   // its length
@@ -1203,60 +1202,22 @@ struct ChunkSmem {
     int32_t sc[kWarps + 1];
 };
 
-// Calls visit(z) for every join tuple (y in R entries [c0, c0 + nc), z in
-// S_sparse[y]) -- only the z of tile t when tile_ptr is set. Entries whose y
-// is held as a bitmap row are skipped when `wide` is set and their bitmap
-// rows appended to wide[*nwide++] instead. Long segments are cut into pieces
-// of kPiece tuples taken by the warps in turn (coalesced, kPiece / 32
-// independent loads per lane); short ones are walked by the thread that read
-// the entry. Contains __syncthreads: call from every thread; the caller
-// synchronises before sm is reused.
+// Calls visit(z) for every z of the chunk's segments: thread i holds entry
+// i's segment (first tuple in ss_col and length, 0 for none), nc entries.
+// Long segments are cut into pieces of kPiece tuples taken by the warps in
+// turn (coalesced, kPiece / 32 independent loads per lane); short ones are
+// walked by the thread that holds them. Contains __syncthreads: call from
+// every thread; the caller synchronises before sm is reused.
 template <class Visit>
-__device__ __forceinline__ void visit_chunk(const XRowArgs& a, int64_t c0, int nc, int t, ChunkSmem& sm,
-                                            int32_t* wide, int* nwide, Visit visit) {
+__device__ __forceinline__ void visit_segments(const XRowArgs& a, int nc, int len, uint32_t first, ChunkSmem& sm,
+                                               Visit visit) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int len[kEPT];
-    uint32_t first[kEPT];
-#pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        const int i = kEPT * tid + k;
-        len[k] = 0;
-        first[k] = 0u;
-        if (i < nc) {
-            const int32_t y = a.r_col[c0 + i];
-            const int32_t b = wide ? a.bm_row_of_y[y] : -1;
-            if (b >= 0) {
-                wide[atomicAdd(nwide, 1)] = b;
-            } else {
-                int64_t s0, s1;
-                if (a.tile_ptr) {
-                    const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + t;
-                    s0 = tp[0];
-                    s1 = tp[1];
-                } else {
-                    s0 = a.ss_rowptr[y];
-                    s1 = a.ss_rowptr[y + 1];
-                }
-                len[k] = (int)(s1 - s0);
-                first[k] = (uint32_t)s0;
-            }
-        }
-    }
-    int pc[kEPT], pcs = 0;
-#pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        pc[k] = len[k] >= kLongSeg ? (len[k] + kPiece - 1) / kPiece : 0;
-        pcs += pc[k];
-    }
+    const int pc = len >= kLongSeg ? (len + kPiece - 1) / kPiece : 0;
     int n_pieces;
-    int ex = block_exclusive_scan<int, kThreads>(pcs, &n_pieces, sm.sc);
-#pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        sm.pc[kEPT * tid + k] = ex;
-        ex += pc[k];
-        sm.s0[kEPT * tid + k] = first[k];
-        sm.len[kEPT * tid + k] = len[k];
-    }
+    const int ex = block_exclusive_scan<int, kThreads>(pc, &n_pieces, sm.sc);
+    sm.pc[tid] = ex;
+    sm.s0[tid] = first;
+    sm.len[tid] = len;
     __syncthreads();
     // long segments: piece p of the chunk goes to warp p mod kWarps
     for (int p = warp; p < n_pieces; p += kWarps) {
@@ -1275,21 +1236,51 @@ __device__ __forceinline__ void visit_chunk(const XRowArgs& a, int64_t c0, int n
         for (int u = 0; u < kPiece / 32; ++u)
             if (zz[u] >= 0) visit(zz[u]);
     }
-    // short segments: the thread that read the entry walks it
+    // short segments: the thread that holds the entry walks it
+    if (len > 0 && len < kLongSeg) {
+        const int32_t* src = a.ss_col + first;
+        for (int q0 = 0; q0 < len; q0 += 4) {
+            int32_t zz[4];
 #pragma unroll
-    for (int k = 0; k < kEPT; ++k) {
-        if (len[k] > 0 && len[k] < kLongSeg) {
-            const int32_t* src = a.ss_col + first[k];
-            for (int q0 = 0; q0 < len[k]; q0 += 4) {
-                int32_t zz[4];
+            for (int u = 0; u < 4; ++u) zz[u] = q0 + u < len ? __ldg(src + q0 + u) : -1;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) zz[u] = q0 + u < len[k] ? __ldg(src + q0 + u) : -1;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (zz[u] >= 0) visit(zz[u]);
-            }
+            for (int u = 0; u < 4; ++u)
+                if (zz[u] >= 0) visit(zz[u]);
         }
     }
+}
+
+// Calls visit(z) for every join tuple (y in R entries [c0, c0 + nc), z in
+// S_sparse[y]) -- only the z of tile t when tile_ptr is set; one entry per
+// thread (nc <= kTileChunk). Entries whose y is held as a bitmap row are
+// skipped when `wide` is set and their bitmap rows appended to
+// wide[*nwide++] instead. Contains __syncthreads (see visit_segments).
+template <class Visit>
+__device__ __forceinline__ void visit_chunk(const XRowArgs& a, int64_t c0, int nc, int t, ChunkSmem& sm,
+                                            int32_t* wide, int* nwide, Visit visit) {
+    const int tid = threadIdx.x;
+    int len = 0;
+    uint32_t first = 0u;
+    if (tid < nc) {
+        const int32_t y = a.r_col[c0 + tid];
+        const int32_t b = wide ? a.bm_row_of_y[y] : -1;
+        if (b >= 0) {
+            wide[atomicAdd(nwide, 1)] = b;
+        } else {
+            int64_t s0, s1;
+            if (a.tile_ptr) {
+                const int64_t* tp = a.tile_ptr + (int64_t)y * a.tile_cols + t;
+                s0 = tp[0];
+                s1 = tp[1];
+            } else {
+                s0 = a.ss_rowptr[y];
+                s1 = a.ss_rowptr[y + 1];
+            }
+            len = (int)(s1 - s0);
+            first = (uint32_t)s0;
+        }
+    }
+    visit_segments(a, nc, len, first, sm, visit);
 }
 
 // Set bits of a 16-byte bitmap word.
@@ -1369,16 +1360,52 @@ __global__ void __launch_bounds__(kThreads) k_tiled_rows(const XRowArgs a) {
         o = a.slot[xr];
     }
     const int64_t r0 = a.r_rowptr[x], r1 = a.r_rowptr[x + 1];
+    // A row of at most kTileChunk R entries (the common case) keeps them in
+    // registers over its tiles: thread i holds entry i's y, the bitmap row of
+    // a wide y (else -1) and the bounds of its segment in the current tile,
+    // the next tile's end loaded while the current tile is processed.
+    const bool one = r1 - r0 <= kTileChunk;
+    int32_t my_y = -1, my_b = -1;
+    int64_t seg0 = 0, seg1 = 0;
+    if (one && tid < r1 - r0) {
+        my_y = a.r_col[r0 + tid];
+        my_b = a.bm_row_of_y[my_y];
+        if (my_b < 0) {
+            const int64_t* tp = a.tile_ptr + (int64_t)my_y * a.tile_cols;
+            seg0 = tp[0];
+            seg1 = tp[1];
+        }
+    }
     clear_words(bm, (int)(((a.tile_bits + 127) >> 7) << 2));
-    if (tid == 0) s_nwide[0] = 0;
+    if (tid == 0) s_nwide[0] = s_nwide[1] = 0;
     __syncthreads();
+    if (one && my_b >= 0) s_wide[atomicAdd(&s_nwide[1], 1)] = my_b;  // final after the next barrier
     int64_t total = 0;
     // Every tile starts with a clean bitmap and s_nwide[0] = 0: both are
     // restored before the last block barrier of the previous tile.
     for (int t = 0; t < a.n_tiles; ++t) {
         const int64_t zt0 = (int64_t)t * a.tile_bits, zt1 = min64(zt0 + a.tile_bits, a.n_z);
         const int tw = (int)((zt1 - zt0 + 31) >> 5), tw4 = (tw + 3) >> 2;
-        for (int64_t c0 = r0, ck = 0; c0 < r1; c0 += kTileChunk, ++ck) {
+        if (one) {
+            const bool seg = my_y >= 0 && my_b < 0;
+            const int64_t nxt = seg && t + 1 < a.n_tiles ? a.tile_ptr[(int64_t)my_y * a.tile_cols + t + 2] : seg1;
+            visit_segments(a, (int)(r1 - r0), seg ? (int)(seg1 - seg0) : 0, (uint32_t)seg0, cs, [&](int32_t zid) {
+                const int z = (int)(zid - zt0);
+                atomicOr(&bm[z >> 5], 1u << (z & 31));
+            });
+            const int nw = s_nwide[1];  // the row's wide S rows: OR their bitmap words over the tile
+            if (nw > 0) {
+                const uint32_t* bits = a.ss_bits + (zt0 >> 5);
+                for (int w = tid; w < tw; w += kThreads) {
+                    uint32_t acc = 0u;
+                    for (int i = 0; i < nw; ++i) acc |= __ldg(bits + a.bm_off[s_wide[i]] + w);
+                    if (acc) atomicOr(&bm[w], acc);
+                }
+            }
+            seg0 = seg1;
+            seg1 = nxt;
+        }
+        for (int64_t c0 = r0, ck = 0; !one && c0 < r1; c0 += kTileChunk, ++ck) {
             const int nc = (int)min64(kTileChunk, r1 - c0);
             int* nwide = &s_nwide[ck & 1];
             if (tid == 0) s_nwide[(ck + 1) & 1] = 0;  // the next chunk's counter (the previous chunk's is done)
