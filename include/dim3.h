@@ -475,7 +475,13 @@ DIM3_API int dim3_plan_row_counts(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begi
  * output buffers are unspecified (a single-pass emission may have written a
  * prefix). capacity = 0 (or null buffers) only sizes the range: it runs a
  * counting pass that the plan keeps, so the next call for the same range
- * emits without counting again.
+ * emits without counting again. Memory: on a single instance whose z range
+ * spans several shared-memory tiles, or whose light rows are sorted, that
+ * counting pass also keeps every row's z values for the emitting pass (a
+ * staging buffer of 4 bytes per min(join tuples of the row, |Z|) entry,
+ * taken only when it fits a quarter of the free device memory, else the
+ * emitting pass recomputes), released with the plan or by the next range's
+ * count; dim3_plan_row_counts never stages.
  * x_begin = 0, x_end = n_x covers everything. Synchronises the stream.
  */
 DIM3_API int dim3_plan_join_project(dim3_ctx *ctx, dim3_plan *plan, int64_t x_begin, int64_t x_end,

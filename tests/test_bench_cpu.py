@@ -99,3 +99,15 @@ def test_host_region_info_finds_the_mapping():
     info = bench.host_region_info(a.ctypes.data)
     assert info["anon_huge_bytes"] is not None and info["anon_huge_bytes"] >= 0
     assert info["numa_pages"] is None or sum(info["numa_pages"].values()) >= 1
+
+
+def test_sparse_passes_roofline_sums_both_passes():
+    """The SparseBMM roofline of a step counts the counting (or staging) pass
+    and the emitting pass together, per step, against the HBM peak."""
+    tm = {"sparse_count": (40.0, 4), "sparse_emit": (10.0, 4)}
+    peaks = {"hbm": 5000.0}
+    r = bench.sparse_passes_roofline(tm, 2, 1e9, peaks)
+    assert r["ms"] == 25.0
+    assert abs(r["achieved_gbs"] - 1e9 / 0.025 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved_gbs"] / 5000.0) < 1e-12
+    assert bench.sparse_passes_roofline({"sparse_count": (0.0, 0), "sparse_emit": (0.0, 0)}, 1, 1e9, peaks) is None
