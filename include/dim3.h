@@ -133,7 +133,8 @@ typedef enum {
     DIM3_OPT_LIGHT_ROW_MAX = 4, /* x rows with at most this many join tuples dedup in shared memory by sort; <0: default */
     DIM3_OPT_TIMING = 5,        /* nonzero: record CUDA events around each phase (dim3_ctx_timing) */
     DIM3_OPT_EMIT_ROWS = 6,     /* x rows per CTA in the emitting SparseBMM pass: 1, 2, 4; 0: automatic */
-    DIM3_OPT_TWO_PASS = 7,      /* nonzero: always count before emitting (no single-pass look-back) */
+    DIM3_OPT_TWO_PASS = 7,      /* nonzero: always count before emitting (no single-pass look-back, no
+                                   staged z values: the emitting pass rebuilds the bitmaps) */
     DIM3_OPT_ID_CHUNK_MAX = 8,  /* emitting pass: a 4096-z chunk of one x row holding at most this many
                                    pairs is written through staged z ids, a denser one group by group;
                                    0: always group by group; <0: default (512); at most 1024 */

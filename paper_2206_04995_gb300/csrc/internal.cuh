@@ -154,7 +154,8 @@ struct Plan {
     DevBuf cache_off;  // int64 [rows + 1]
     DevBuf cache_dbits; // dense bits of the cached range
     DevBuf cache_dcnt;  // dense counts of the cached range
-    // z-tiled single instance: the cached range's (row, tile) units
+    // z-tiled single instance (or light rows beside bitmap rows): the rows the
+    // cached range sweeps over the z tiles
     DevBuf cache_units;     // int32 [cache_n_list]: rows run over the z tiles (null: every row)
     int64_t cache_n_list = 0, cache_tile_bits = 0;
     // z-tiled single instance, counted for an emitting call: every row's z

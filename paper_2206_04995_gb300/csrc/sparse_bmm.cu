@@ -2323,7 +2323,7 @@ static void ensure_counts(const Ctx& ctx, Plan& p, int64_t x_begin, int64_t x_en
             a.unit_rows = p.cache_units.as<int32_t>();
             a.cnt = cnt.as<int64_t>();
             DIM3_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)rows * 8, s));
-            const int mode = stage && stage_slots(p, x_begin, rows, s) ? kStageRows : kCountRows;
+            const int mode = stage && !ctx.opt.two_pass && stage_slots(p, x_begin, rows, s) ? kStageRows : kCountRows;
             if (mode == kStageRows) {
                 a.slot = p.cache_slot.as<int64_t>();
                 a.out_z = p.cache_vals.as<int32_t>();

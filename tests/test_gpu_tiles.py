@@ -1,8 +1,10 @@
-"""SparseBMM over z ranges wider than one shared-memory bitmap: every x row
-runs as (row, z tile) units, counted first and emitted after. Small tiles
-are forced with DIM3_OPT_TILE_WORDS so that inputs the oracle finishes in
-seconds span many tiles, with ragged last tiles and tile sizes that are not
-whole 1024-z groups; the full-size power-law workload (three tiles of the
+"""SparseBMM over z ranges wider than one shared-memory bitmap: one CTA per
+x row sweeps the z tiles; the counting pass stages every row's z values and
+the emitting pass places them (without staging -- DIM3_OPT_TWO_PASS, or
+after a plain row count -- the emitting pass rebuilds the tiles). Small
+tiles are forced with DIM3_OPT_TILE_WORDS so that inputs the oracle finishes
+in seconds span many tiles, with ragged last tiles and tile sizes that are
+not whole 1024-z groups; the full-size power-law workload (three tiles of the
 default size) is covered in test_gpu_full.py. All integer: exact equality
 with the oracle."""
 
@@ -141,3 +143,22 @@ def test_light_and_bitmap_rows_on_tiles(light, cases):
                 assert np.array_equal(np.concatenate([host(p[1]) for p in parts]), oz)
         finally:
             c.close()
+
+
+@pytest.mark.parametrize("two_pass", [0, 1])
+@pytest.mark.parametrize("light", [-1, 0])
+def test_staged_and_rebuilt_emission_agree(two_pass, light, cases):
+    """One call with the rows' z values staged by the counting pass (default)
+    or rebuilt by the emitting pass (DIM3_OPT_TWO_PASS), into aligned and
+    4-byte-offset output buffers: the same exact pairs."""
+    c = ctx_with({dim3.OPT_TILE_WORDS: 1500, dim3.OPT_LIGHT_ROW_MAX: light, dim3.OPT_TWO_PASS: two_pass})
+    try:
+        for inst, ox, oz in cases:
+            cols = inst_dev(inst)
+            for shift in (0, 1):
+                bx = torch.empty(ox.size + shift, dtype=torch.int32, device="cuda")
+                bz = torch.empty(ox.size + shift, dtype=torch.int32, device="cuda")
+                x, z = c.join_project(*cols, out_x=bx[shift:], out_z=bz[shift:])
+                assert np.array_equal(host(x), ox) and np.array_equal(host(z), oz), (inst.name, shift)
+    finally:
+        c.close()
