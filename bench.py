@@ -1206,7 +1206,8 @@ def pinned_host_empty(torch, n, node=None):
 
 def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
     """Same metric through the public call with HOST buffers: pinned host
-    inputs copied in, the join (``join_call``), both output columns copied out.
+    inputs copied in, the join (``join_call``), both output columns copied out
+    (side by side on two streams when the host columns are page-locked).
     The output columns are placed on the NUMA node of the CPUs local to the
     GPU when sysfs names one. A further, separately timed step records each
     copy's time and rate, and the record says where the host pages landed."""
@@ -1240,7 +1241,10 @@ def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
     h2d = sum(h.numel() * 4 for h in h_in)
     d2h = 2 * out_p * 4
 
-    def one(ev=None):
+    side = torch.cuda.Stream(dev) if pin else None
+    joined, copied = torch.cuda.Event(), torch.cuda.Event()
+
+    def one(ev=None, overlap=True):
         if ev:
             ev[0].record()
         for d, h in zip(d_in, h_in):
@@ -1250,10 +1254,21 @@ def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
         x, z = join_call(d_cols, d_x, d_z)
         if ev:
             ev[2].record()
-        h_x.copy_(x, non_blocking=pin)
-        if ev:
-            ev[3].record()
-        h_z.copy_(z, non_blocking=pin)
+        if overlap and side is not None:
+            # the two output columns leave side by side: x on this stream, z
+            # on a second one that waits for the join and is waited for
+            joined.record()
+            side.wait_event(joined)
+            with torch.cuda.stream(side):
+                h_z.copy_(z, non_blocking=True)
+                copied.record(side)
+            h_x.copy_(x, non_blocking=True)
+            torch.cuda.current_stream().wait_event(copied)
+        else:
+            h_x.copy_(x, non_blocking=pin)
+            if ev:
+                ev[3].record()
+            h_z.copy_(z, non_blocking=pin)
         if ev:
             ev[4].record()
 
@@ -1268,12 +1283,19 @@ def run_e2e(torch, host_cols, join_call, dev, out_p, steps):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
-    # one more step with an event between every part
+    # two more steps with events between the parts: the columns copied side by
+    # side as timed, then one after the other for each column's own rate
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     one(ev)
     torch.cuda.synchronize()
-    part = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
-    parts = {"h2d_ms": part[0], "join_ms": part[1], "d2h_x_ms": part[2], "d2h_z_ms": part[3],
+    both = ev[2].elapsed_time(ev[4])
+    part = [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])]
+    one(ev, overlap=False)
+    torch.cuda.synchronize()
+    part += [ev[2].elapsed_time(ev[3]), ev[3].elapsed_time(ev[4])]
+    parts = {"h2d_ms": part[0], "join_ms": part[1], "d2h_both_ms": both,
+             "d2h_both_gbs": 2 * out_p * 4 / max(both, 1e-6) / 1e6,
+             "d2h_x_ms": part[2], "d2h_z_ms": part[3],
              "h2d_gbs": h2d / max(part[0], 1e-6) / 1e6, "d2h_x_gbs": out_p * 4 / max(part[2], 1e-6) / 1e6,
              "d2h_z_gbs": out_p * 4 / max(part[3], 1e-6) / 1e6}
     del d_in, d_x, d_z
